@@ -1,0 +1,229 @@
+/*
+ * qkc.h -- C-ABI of the GB300 arithmetic-circuit engine for noisy variational
+ * quantum circuits (Huang, Holtzen, Millstein, Van den Broeck, Martonosi,
+ * "Logical Abstractions for Noisy Variational Quantum Algorithm Simulation",
+ * ASPLOS 2021).
+ *
+ * The engine follows the paper's statement of the problem (Sec. 1, Sec. 3.2,
+ * Sec. 3.3): a noisy circuit is compiled once into an arithmetic circuit (AC),
+ * and the AC is then queried many times with new gate parameters and new
+ * evidence -- amplitudes and probabilities by an upward pass (Sec. 3.3.1,
+ * Table 5), every partial derivative by a downward pass (Sec. 3.3.2), and
+ * samples of the output distribution.
+ *
+ * Conventions for every call below.
+ *  - Pointers whose name ends in _dev are device memory owned by the caller
+ *    (for example PyTorch tensors); the library never frees them.  Pointers
+ *    without that suffix are host memory.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls that
+ *    take a stream are asynchronous on it and write no host memory; the
+ *    caller synchronises before reading results.
+ *  - Every call returns a qkc_status; on failure a message is kept per host
+ *    thread and returned by qkc_last_error().  No call aborts or traps.
+ *  - An AC handle is not thread safe: calls on one handle must be issued from
+ *    one host thread (or serialised by the caller) and on one stream at a time,
+ *    because the handle owns its scratch buffers.
+ *  - Outcome bit order: qubit 0 is the most significant bit of an outcome index.
+ */
+#ifndef QKC_H
+#define QKC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QKC_OK = 0,
+    QKC_ERR_ARG = 1,         /* a size, pointer or code is out of range               */
+    QKC_ERR_FORMAT = 2,      /* a compiled-AC byte buffer is malformed                 */
+    QKC_ERR_NOMEM = 3,       /* host or device allocation failed                      */
+    QKC_ERR_CUDA = 4,        /* a CUDA runtime call failed (message has the name)      */
+    QKC_ERR_TIMEOUT = 5,     /* a bounded wait ran out                                */
+    QKC_ERR_UNSUPPORTED = 6, /* the query needs another AC kind                        */
+    QKC_ERR_TOO_LARGE = 7    /* the AC would exceed the compiler's node budget         */
+} qkc_status;
+
+/* ------------------------------------------------------------------ circuits
+ * One circuit operation (24 bytes).  `kind` codes:
+ *   gates     H=0 X=1 Y=2 Z=3 RX=4 RY=5 RZ=6 CNOT=7 (q0 control, q1 target) CZ=8
+ *   channels  DEP1=16 (symmetric depolarising, Kraus sqrt(1-p) I, sqrt(p/3) X, Y, Z)
+ *             DEP2=17 (two-qubit depolarising on q0,q1: sqrt(1-p) I(x)I and
+ *                      sqrt(p/15) for each of the 15 other Pauli products)
+ *             AD=18   (amplitude damping, p = gamma)
+ *             PD=19   (phase damping, p = gamma; the paper's Sec. 2.2 Kraus pair,
+ *                      with the sign of Table 3b on the damping operator)
+ *             PF=20   (phase flip: sqrt(1-p) I, sqrt(p) Z)
+ *             BF=21   (bit flip:   sqrt(1-p) I, sqrt(p) X)
+ * RX/RY/RZ(theta) = exp(-i theta P/2) with theta = angles[angle].  q1 = -1 for
+ * one-qubit operations.  Noise strengths are fixed at compile time.
+ */
+typedef struct {
+    int32_t kind;
+    int32_t q0;
+    int32_t q1;
+    int32_t angle;
+    double p;
+} qkc_op;
+
+enum { QKC_AC_AMPLITUDE = 0, QKC_AC_DENSITY = 1 };
+enum { QKC_ORDER_AUTO = 0, QKC_ORDER_MINFILL = 1, QKC_ORDER_MINWEIGHT = 2, QKC_ORDER_CREATION = 3 };
+
+/*
+ * qkc_compile -- noisy circuit -> Bayesian network -> arithmetic circuit.
+ *
+ * Sec. 3.1 (conditional amplitude tables, Tables 3a-3c: the table of a gate is
+ * the transpose of its unitary; multi-qubit gates must be monomial so only the
+ * target gets a new node; a noise channel gets a random-variable node), Sec. 3.2
+ * (knowledge compilation, with the simplifications of Table 4: known initial
+ * states substituted, 0/1 parameters folded into the structure, every other
+ * parameter kept as a leaf, intermediate qubit states summed out).  The
+ * compiler used here is symbolic variable elimination with a min-fill order
+ * (the paper names variable elimination as its first approach, Sec. 3.2)
+ * instead of CNF + c2d.
+ *
+ * kind QKC_AC_AMPLITUDE: the paper's AC.  Its network polynomial is
+ *   f(lambda) = sum_{x,r} prod lambda_{x_j} prod lambda_{r_k} A(x, r)
+ * over output qubits x and noise random variables r (Table 5).
+ * kind QKC_AC_DENSITY: the AC of the doubled network (ket copy with the tables
+ * above, bra copy with their complex conjugates, noise variables and output
+ * variables shared by both copies), whose polynomial is
+ *   f(lambda) = sum_x prod_j lambda_{x_j} <x| rho |x>,
+ * so partial evidence gives marginal probabilities exactly (this construction
+ * is this library's reading of Sec. 3.3; the paper itself enumerates r).
+ *
+ * `order` is one of QKC_ORDER_*; `max_nodes` bounds the AC (0 = 2^31-1), above
+ * it QKC_ERR_TOO_LARGE.  On success *out_bytes is a malloc'd buffer in the
+ * compiled-AC format below; release it with qkc_free_bytes.
+ */
+qkc_status qkc_compile(const qkc_op *ops, int32_t n_ops, int32_t n_qubits, int32_t n_angles,
+                       int32_t kind, int32_t order, int64_t max_nodes,
+                       uint8_t **out_bytes, uint64_t *out_len);
+void qkc_free_bytes(uint8_t *bytes);
+
+/*
+ * Compiled-AC byte format (little endian, version 1).  Header of 16 uint32:
+ *   [0] magic 0x43414B51 ("QKAC")  [1] version = 1  [2] kind  [3] n_qubits
+ *   [4] n_angles  [5] n_vars  [6] n_nodes  [7] n_edges  [8] n_levels
+ *   [9] n_leaves  [10] root  [11] n_ind  [12..15] 0
+ * then these arrays, each starting on an 8-byte boundary:
+ *   var_card[n_vars] u32      cardinality of each indicator variable
+ *   var_tag[n_vars]  i32      qubit index of an output variable, or -1-k for
+ *                             the noise variable of the k-th channel
+ *   level_off[n_levels+1] u32 nodes of level L are [level_off[L], level_off[L+1])
+ *   op[n_nodes] u8            0 IND, 1 PARAM, 2 CONST, 3 ADD, 4 MUL
+ *   child_off[n_nodes+1] u32  children of node i are child[child_off[i] ..]
+ *   child[n_edges] u32        every child has a lower level than its parent
+ *   leaf_a[n_leaves] i32      IND: variable; PARAM: angle slot; CONST: -1
+ *   leaf_b[n_leaves] i32      IND: value; PARAM: function (0 cos(t/2),
+ *                             1 sin(t/2), 2 exp(-i t/2), 3 exp(+i t/2)); CONST: 0
+ *   leaf_coef[n_leaves][2] f64 PARAM: complex coefficient c (leaf = c g(t));
+ *                             CONST: the value; IND: (1, 0)
+ * Level 0 holds exactly the leaves.  Nodes 0 .. n_ind-1 are the indicator
+ * leaves lambda_{v=k} in (variable, value) order, one per value of every
+ * variable.  MUL nodes have exactly two children; ADD nodes two or more.
+ */
+
+/* ------------------------------------------------------------------ engine */
+typedef struct qkc_ctx qkc_ctx; /* opaque: one CUDA device */
+typedef struct qkc_ac qkc_ac;   /* opaque: one AC resident on the device + scratch */
+
+typedef struct {
+    int32_t kind, n_qubits, n_angles, n_vars, n_ind, precision;
+    int64_t n_nodes, n_edges, n_levels, n_leaves, max_level_width;
+    int64_t device_bytes;       /* structure bytes resident on the device   */
+    int64_t reserved_columns;   /* columns the scratch currently holds      */
+} qkc_ac_info;
+
+/* Bind a context to CUDA device `device`. */
+qkc_status qkc_ctx_create(int device, qkc_ctx **out);
+void qkc_ctx_destroy(qkc_ctx *ctx);
+
+/*
+ * qkc_load_ac -- copy a compiled AC (host bytes, caller keeps them) to the
+ * device of `ctx` (Sec. 3.2.2: compile once, reuse across simulations).
+ * precision 32: node values complex FP32 with a power-of-two scale per
+ * (level, column); 64: complex FP64.  Blocks until the copy is done.
+ */
+qkc_status qkc_load_ac(qkc_ctx *ctx, const uint8_t *bytes, uint64_t len, int32_t precision,
+                       qkc_ac **out);
+void qkc_free_ac(qkc_ac *ac);
+qkc_status qkc_get_info(const qkc_ac *ac, qkc_ac_info *out);
+
+/*
+ * qkc_reserve -- size the AC's device scratch for up to `max_vectors` parameter
+ * vectors and `max_columns` evaluation columns (grows, never shrinks).  Calls
+ * that need more scratch than reserved grow it themselves, which synchronises
+ * the device; reserve first to keep them asynchronous.
+ */
+qkc_status qkc_reserve(qkc_ac *ac, int64_t max_vectors, int64_t max_columns);
+
+/*
+ * qkc_set_params -- bind gate parameters (Sec. 3.2.1, Table 4: parameters are
+ * weight variables resolved at simulation time).  angles_dev is [n_vectors]
+ * [n_angles] float64, row-major.  Every PARAM leaf gets c g(angle) per vector.
+ */
+qkc_status qkc_set_params(qkc_ac *ac, const double *angles_dev, int64_t n_vectors, void *stream);
+
+/*
+ * Evidence (Sec. 3.3.1: indicators are 1 for the observed value and 0 for the
+ * others; unobserved variables have every indicator at 1).  evidence_dev is
+ * [n_cols][n_vars] int8: -1 free, k >= 0 observed value k, -2 Pauli-Z sign
+ * (binary variables only: lambda_0 = 1, lambda_1 = -1, so the density AC
+ * returns <Z...Z> on those qubits).  col_vec_dev [n_cols] int32 names the
+ * parameter vector of each column (< n_vectors of the last qkc_set_params).
+ *
+ * qkc_evaluate -- upward pass (Sec. 3.3.1): out_dev[c] = f(lambda_c) as
+ * (re, im) float64, [n_cols][2].
+ */
+qkc_status qkc_evaluate(qkc_ac *ac, const int32_t *col_vec_dev, const int8_t *evidence_dev,
+                        int64_t n_cols, double *out_dev, void *stream);
+
+/*
+ * qkc_marginals -- upward then downward pass (Sec. 3.3.2, the differential
+ * approach the paper cites): marg_dev[c][i] = d f / d lambda_i for every
+ * indicator leaf i (n_ind of them, (variable, value) order) as (re, im)
+ * float64, [n_cols][n_ind][2].  Because f is multilinear in the indicators,
+ * for a density AC this is P(e without X_j, X_j = v) for every qubit j and
+ * value v.  root_dev (nullable) receives f, [n_cols][2].
+ */
+qkc_status qkc_marginals(qkc_ac *ac, const int32_t *col_vec_dev, const int8_t *evidence_dev,
+                         int64_t n_cols, double *root_dev, double *marg_dev, void *stream);
+
+/*
+ * qkc_gradient -- weighted expectation and its gradient in the gate angles.
+ * For every vector v:  value_dev[v] = sum_{c: col_vec[c]=v} w_c Re f(lambda_c)
+ * and grad_dev[v][k] = d value_dev[v] / d angle_k, with w = weight_dev [n_cols]
+ * float64.  With one column per Z-string term and w_c its coefficient this is
+ * <H> and its gradient.  The derivative is the downward pass taken to the
+ * PARAM leaves, chained with d leaf / d angle (holomorphic chain rule).
+ * value_dev [n_vectors], grad_dev [n_vectors][n_angles] float64.
+ */
+qkc_status qkc_gradient(qkc_ac *ac, const int32_t *col_vec_dev, const int8_t *evidence_dev,
+                        const double *weight_dev, int64_t n_cols, int64_t n_vectors,
+                        double *value_dev, double *grad_dev, void *stream);
+
+/*
+ * qkc_sample -- exact qubit-by-qubit conditional sampling of the output
+ * distribution (Sec. 3.3.2 gives the sampling task; the paper's own sampler
+ * is Gibbs MCMC, this one is the exact chain rule it compares against,
+ * "ideal sampling").  Needs a DENSITY AC.
+ * For vector v, sample s, qubit j: u = (SplitMix64_k(seeds[v]) >> 11) 2^-53
+ * with k = s*n_qubits + j + 1 (the k-th output of a SplitMix64 stream);
+ * p0 = P(x_<j, X_j = 0), P = P(x_<j); x_j = 1 iff u * P >= p0, in float64.
+ * Samples of one vector that share a prefix share one evaluation.
+ * bits_dev [n_vectors][max_shots] uint64: outcome index of each sample
+ * (entries s >= shots[v] are left untouched).  shots_dev [n_vectors] int32.
+ */
+qkc_status qkc_sample(qkc_ac *ac, const uint64_t *seeds_dev, const int32_t *shots_dev,
+                      int64_t n_vectors, int64_t max_shots, uint64_t *bits_dev, void *stream);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *qkc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QKC_H */

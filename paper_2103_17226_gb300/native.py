@@ -1,0 +1,264 @@
+"""Thin ctypes binding of libqkc (include/qkc.h): argument marshalling only.
+
+Every function here has the name of the C entry point without its `qkc_`
+prefix and forwards to it; all computation runs in the library's CUDA kernels
+(or, for `compile` and `plan`, in its host compiler).  Device buffers are
+PyTorch tensors, streams are PyTorch's current stream.  There is no fallback:
+if the library is missing, loading fails with an error that says so.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+from .inputs import OP_DTYPE
+
+_LIB_PATH = Path(__file__).resolve().parent / "_build" / "libqkc.so"
+_lib = None
+
+QKC_AC_AMPLITUDE = 0
+QKC_AC_DENSITY = 1
+STATUS = {0: "QKC_OK", 1: "QKC_ERR_ARG", 2: "QKC_ERR_FORMAT", 3: "QKC_ERR_NOMEM", 4: "QKC_ERR_CUDA",
+          5: "QKC_ERR_TIMEOUT", 6: "QKC_ERR_UNSUPPORTED", 7: "QKC_ERR_TOO_LARGE"}
+
+
+class QKCError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class ACInfo(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n_qubits", ctypes.c_int32), ("n_angles", ctypes.c_int32),
+                ("n_vars", ctypes.c_int32), ("n_ind", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("n_nodes", ctypes.c_int64), ("n_edges", ctypes.c_int64), ("n_levels", ctypes.c_int64),
+                ("n_leaves", ctypes.c_int64), ("max_level_width", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("reserved_columns", ctypes.c_int64)]
+
+
+def lib():
+    """The loaded libqkc (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not _LIB_PATH.exists():
+        raise RuntimeError(f"libqkc is not built ({_LIB_PATH} missing): run __graft_entry__.build() "
+                           "or paper_2103_17226_gb300.build.build_library()")
+    L = ctypes.CDLL(str(_LIB_PATH))
+    P, I32, I64, U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    sig = {
+        "qkc_compile": [P, I32, I32, I32, I32, I32, I64, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(U64)],
+        "qkc_plan": [P, I32, I32, I32, I32, I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+        "qkc_ctx_create": [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)],
+        "qkc_load_ac": [P, P, U64, I32, ctypes.POINTER(ctypes.c_void_p)],
+        "qkc_get_info": [P, ctypes.POINTER(ACInfo)],
+        "qkc_reserve": [P, I64, I64],
+        "qkc_set_params": [P, P, I64, P],
+        "qkc_evaluate": [P, P, P, I64, P, P],
+        "qkc_marginals": [P, P, P, I64, P, P, P],
+        "qkc_gradient": [P, P, P, P, I64, I64, P, P, P],
+        "qkc_sample": [P, P, P, I64, I64, P, P],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.qkc_free_bytes.argtypes = [ctypes.c_void_p]
+    L.qkc_free_bytes.restype = None
+    L.qkc_ctx_destroy.argtypes = [ctypes.c_void_p]
+    L.qkc_ctx_destroy.restype = None
+    L.qkc_free_ac.argtypes = [ctypes.c_void_p]
+    L.qkc_free_ac.restype = None
+    L.qkc_last_error.argtypes = []
+    L.qkc_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(st: int):
+    if st != 0:
+        raise QKCError(st, lib().qkc_last_error().decode())
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0) if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# --------------------------------------------------------------------------- compiler (host)
+def _records(circuit):
+    rec = circuit.as_records()
+    assert rec.dtype == OP_DTYPE
+    return np.ascontiguousarray(rec)
+
+
+def compile(circuit, kind: int = QKC_AC_DENSITY, order: int = 0, max_nodes: int = 0) -> bytes:
+    """qkc_compile: circuit -> compiled-AC bytes."""
+    rec = _records(circuit)
+    out = ctypes.c_void_p()
+    n = ctypes.c_uint64()
+    _check(lib().qkc_compile(rec.ctypes.data_as(ctypes.c_void_p), len(rec), circuit.n_qubits, circuit.n_angles,
+                             kind, order, max_nodes, ctypes.byref(out), ctypes.byref(n)))
+    try:
+        return ctypes.string_at(out, n.value)
+    finally:
+        lib().qkc_free_bytes(out)
+
+
+def plan(circuit, kind: int = QKC_AC_DENSITY, order: int = 0):
+    """qkc_plan: (sum of elimination table sizes, log2 of the largest table) without building."""
+    rec = _records(circuit)
+    a = ctypes.c_double()
+    w = ctypes.c_double()
+    _check(lib().qkc_plan(rec.ctypes.data_as(ctypes.c_void_p), len(rec), circuit.n_qubits, circuit.n_angles,
+                          kind, order, ctypes.byref(a), ctypes.byref(w)))
+    return a.value, w.value
+
+
+def header(ac_bytes: bytes) -> dict:
+    """Header fields of compiled-AC bytes (the format is documented in include/qkc.h)."""
+    h = np.frombuffer(ac_bytes[:64], dtype="<u4")
+    keys = ["magic", "version", "kind", "n_qubits", "n_angles", "n_vars", "n_nodes", "n_edges", "n_levels",
+            "n_leaves", "root", "n_ind"]
+    return {k: int(h[i]) for i, k in enumerate(keys)}
+
+
+# --------------------------------------------------------------------------- engine
+class Context:
+    """qkc_ctx_create / qkc_ctx_destroy."""
+
+    def __init__(self, device: int = 0):
+        self._h = ctypes.c_void_p()
+        _check(lib().qkc_ctx_create(device, ctypes.byref(self._h)))
+        self.device = device
+
+    def close(self):
+        if self._h:
+            lib().qkc_ctx_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class AC:
+    """A compiled AC resident on the device (qkc_load_ac / qkc_free_ac)."""
+
+    def __init__(self, ctx: Context, ac_bytes: bytes, precision: int = 32):
+        self.ctx = ctx
+        self._h = ctypes.c_void_p()
+        buf = ctypes.create_string_buffer(ac_bytes, len(ac_bytes))
+        _check(lib().qkc_load_ac(ctx._h, buf, len(ac_bytes), precision, ctypes.byref(self._h)))
+        self.precision = precision
+        self._info = self.info()
+
+    def info(self) -> dict:
+        i = ACInfo()
+        _check(lib().qkc_get_info(self._h, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in ACInfo._fields_}
+
+    @property
+    def n_qubits(self):
+        return self._info["n_qubits"]
+
+    @property
+    def n_vars(self):
+        return self._info["n_vars"]
+
+    @property
+    def n_ind(self):
+        return self._info["n_ind"]
+
+    @property
+    def n_angles(self):
+        return self._info["n_angles"]
+
+    def close(self):
+        if self._h:
+            lib().qkc_free_ac(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ctx_create(device: int = 0) -> Context:
+    return Context(device)
+
+
+def load_ac(ctx: Context, ac_bytes: bytes, precision: int = 32) -> AC:
+    return AC(ctx, ac_bytes, precision)
+
+
+def reserve(ac: AC, max_vectors: int, max_columns: int):
+    _check(lib().qkc_reserve(ac._h, max_vectors, max_columns))
+
+
+def set_params(ac: AC, angles, stream=None):
+    """angles: float64 CUDA tensor [n_vectors][n_angles] (contiguous)."""
+    assert angles.is_cuda and angles.dtype.is_floating_point and angles.is_contiguous()
+    n_vec = angles.shape[0] if angles.dim() == 2 else 1
+    _check(lib().qkc_set_params(ac._h, _ptr(angles), n_vec, _stream(stream)))
+    ac._angles = angles  # keep alive: the gradient reads it
+
+
+def _cols(col_vec, evidence, ac):
+    assert evidence.is_cuda and evidence.is_contiguous() and evidence.shape[-1] == ac.n_vars
+    n = evidence.shape[0]
+    if col_vec is not None:
+        assert col_vec.is_cuda and col_vec.is_contiguous() and col_vec.shape[0] == n
+    return n
+
+
+def evaluate(ac: AC, col_vec, evidence, out=None, stream=None):
+    """Upward pass: complex f per column, float64 tensor [n_cols][2]."""
+    import torch
+    n = _cols(col_vec, evidence, ac)
+    if out is None:
+        out = torch.empty((n, 2), dtype=torch.float64, device=evidence.device)
+    _check(lib().qkc_evaluate(ac._h, _ptr(col_vec), _ptr(evidence), n, _ptr(out), _stream(stream)))
+    return out
+
+
+def marginals(ac: AC, col_vec, evidence, stream=None):
+    """Upward + downward pass: (root [n][2], d f / d lambda [n][n_ind][2])."""
+    import torch
+    n = _cols(col_vec, evidence, ac)
+    root = torch.empty((n, 2), dtype=torch.float64, device=evidence.device)
+    marg = torch.empty((n, ac.n_ind, 2), dtype=torch.float64, device=evidence.device)
+    _check(lib().qkc_marginals(ac._h, _ptr(col_vec), _ptr(evidence), n, _ptr(root), _ptr(marg), _stream(stream)))
+    return root, marg
+
+
+def gradient(ac: AC, col_vec, evidence, weight, n_vectors: int, stream=None):
+    """(value [n_vectors], grad [n_vectors][n_angles]) of sum_c w_c Re f_c per vector."""
+    import torch
+    n = _cols(col_vec, evidence, ac)
+    value = torch.empty((n_vectors,), dtype=torch.float64, device=evidence.device)
+    grad = torch.empty((n_vectors, max(1, ac.n_angles)), dtype=torch.float64, device=evidence.device)
+    _check(lib().qkc_gradient(ac._h, _ptr(col_vec), _ptr(evidence), _ptr(weight), n, n_vectors, _ptr(value),
+                              _ptr(grad), _stream(stream)))
+    return value, grad[:, :ac.n_angles]
+
+
+def sample(ac: AC, seeds, shots, max_shots: int, out=None, stream=None):
+    """Chain-rule samples: uint64 outcome indices [n_vectors][max_shots] (int64 tensor view)."""
+    import torch
+    n_vec = seeds.shape[0]
+    if out is None:
+        out = torch.zeros((n_vec, max_shots), dtype=torch.int64, device=seeds.device)
+    _check(lib().qkc_sample(ac._h, _ptr(seeds), _ptr(shots), n_vec, max_shots, _ptr(out), _stream(stream)))
+    return out
