@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Benchmark of the batched arithmetic-circuit hot path on one or more GB300s.
+
+Default workload (32-qubit noise-free QAOA p=1 on a seeded random 3-regular graph,
+compiled to a density AC of about 142K nodes, FP32 complex node values): one
+step, per GPU, is a variational iteration over 64 parameter vectors --
+  bind the angles (upward-pass leaves),
+  <C> and its angle gradient for the Max-Cut cost C = sum_edges (1 - Z_i Z_j)/2
+    (48 Z-string evidence columns per vector: upward + downward pass),
+  10000 chain-rule samples per vector (qubit-by-qubit conditional sampling).
+`value` is samples/s over all GPUs (weak scaling: every GPU runs its own 64
+vectors; there is no collective on the data path).
+
+--workload hea16: 16-qubit noisy hardware-efficient ansatz (the largest AC,
+about 2.35M nodes): 256 vectors x 16 Z-string terms, <H> + gradient over 192
+angles; value = gradient columns/s.
+
+--impl reference times the oracle (plain FP64 C evaluator, one host core) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["qaoa32", "hea16"], default="qaoa32")
+    ap.add_argument("--shots", type=int, default=10000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=["step", "uppass"], default="step",
+                    help="uppass: only the upward pass over --columns sampling-prefix columns (profiling case)")
+    ap.add_argument("--columns", type=int, default=2048)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- workloads
+def make_workload(name, shots):
+    from paper_2103_17226_gb300 import inputs as I
+    if name == "qaoa32":
+        c = I.workload("qaoa32_3reg_p1_ideal")
+        edges = I.random_regular_graph(32, 3, seed=5)
+        V = 64
+        angles = I.uniform_angles(V, c.n_angles, seed=5)
+        # Max-Cut cost C = sum_e (1 - Z_i Z_j) / 2: <C> = |E|/2 - 1/2 sum_e <Z_i Z_j>
+        sup = np.zeros((len(edges), 32), dtype=bool)
+        for k, (i, j) in enumerate(edges):
+            sup[k, i] = sup[k, j] = True
+        coef = np.full(len(edges), -0.5)
+        return dict(name="qaoa32_3reg_p1_ideal", circuit=c, V=V, angles=angles, sup=sup, coef=coef, shots=shots,
+                    seeds=I.vector_seeds(V, 5), unit="samples/s", metric="samples/s (chain-rule sampling, "
+                    "with <C> + gradient, of a 32-qubit QAOA density AC)")
+    c = I.workload("hea16_l6")
+    V = 256
+    sup, coef = I.z_string_hamiltonian(16, 16, seed=3)
+    return dict(name="hea16_l6", circuit=c, V=V, angles=I.uniform_angles(V, c.n_angles, seed=3), sup=sup,
+                coef=coef, shots=0, seeds=None, unit="gradient columns/s",
+                metric="gradient columns/s (<H> + d<H>/dangles of a 16-qubit noisy HEA density AC)")
+
+
+def hamiltonian_columns(W):
+    V, T = W["V"], len(W["coef"])
+    ev = np.array([[-2 if b else -1 for b in W["sup"][t]] for _ in range(V) for t in range(T)], dtype=np.int8)
+    cv = np.repeat(np.arange(V, dtype=np.int32), T)
+    w = np.tile(W["coef"], V).astype(np.float64)
+    return ev, cv, w
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                pw.append(float(r[3]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        # samples under load: the upper half by power
+        cut = statistics.median(pw)
+        loaded = [s for s, p in zip(sm, pw) if p >= cut] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(pw)}
+
+
+# ---------------------------------------------------------------- oracle timing (CPU baseline / reference arm)
+def oracle_rate(W, ac_bytes, budget_s=12.0):
+    """Time the oracle as it stands (acref.c, FP64, one host core) on a bounded sample of
+    the workload: the per-vector gradient columns, then samples until the budget."""
+    from oracle import acref as R
+    ref = R.ACRef(ac_bytes)
+    a = W["angles"][0]
+    t0 = time.perf_counter()
+    for t, (s, cf) in enumerate(zip(W["sup"], W["coef"])):
+        ref.gradient(a, [-2 if b else -1 for b in s], cf)
+    t_grad = time.perf_counter() - t0
+    T = len(W["coef"])
+    if W["shots"] == 0:
+        return dict(value=T / t_grad, unit=W["unit"], cores=1, kind="oracle",
+                    sample=f"1 vector x {T} Z-string columns (up + down pass each) on acref.c, FP64, one core")
+    n_s = 0
+    t1 = time.perf_counter()
+    while time.perf_counter() - t1 < max(1.0, budget_s - t_grad) or n_s == 0:
+        ref.sample(a, int(W["seeds"][0]) + n_s, 4)
+        n_s += 4
+    t_s = (time.perf_counter() - t1) / n_s
+    per_vec = t_grad + W["shots"] * t_s
+    return dict(value=W["shots"] / per_vec, unit=W["unit"], cores=1, kind="oracle",
+                sample=(f"1 vector: {T} gradient columns ({t_grad:.2f} s) + {n_s} chain-rule samples "
+                        f"({t_s * 1e3:.1f} ms each) on acref.c, FP64, one core; rate = {W['shots']} samples / "
+                        f"(gradient + {W['shots']} x per-sample time)"))
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2103_17226_gb300.build import build_library
+    build_library()
+    from paper_2103_17226_gb300 import native as N
+    W = make_workload(args.workload, args.shots)
+    b = N.compile(W["circuit"], N.QKC_AC_DENSITY)
+    rates = []
+    for i in range(args.warmup + args.steps):
+        r = oracle_rate(W, b, budget_s=8.0)
+        if i >= args.warmup:
+            rates.append(r)
+    val = statistics.median([r["value"] for r in rates])
+    line = {"impl": "reference", "metric": W["metric"], "value": val, "unit": W["unit"], "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": W["name"]},
+            "cpu_baseline": {"value": val, "unit": W["unit"], "cores": 1, "kind": "oracle",
+                             "sample": rates[-1]["sample"]},
+            "e2e": {"value": val, "unit": W["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2103_17226_gb300.build import build_library
+    build_library()
+    from paper_2103_17226_gb300 import native as N
+
+    W = make_workload(args.workload, args.shots)
+    ac_bytes = N.compile(W["circuit"], N.QKC_AC_DENSITY)
+    ctx = N.Context(local)
+    ac = N.load_ac(ctx, ac_bytes, precision=32)
+    V, S = W["V"], W["shots"]
+    ev, cv, w = hamiltonian_columns(W)
+    n_cols = len(cv)
+    N.reserve(ac, V, max(n_cols, V * max(S, 1)))
+    info = ac.info()
+
+    # device inputs (kernel-only timing) -- a few angle sets, rotated per step
+    angle_sets = [W["angles"] + 0.01 * k for k in range(4)]
+    d_angles = [torch.tensor(a, device=dev) for a in angle_sets]
+    d_ev, d_cv, d_w = torch.tensor(ev, device=dev), torch.tensor(cv, device=dev), torch.tensor(w, device=dev)
+    d_seeds = torch.tensor(W["seeds"].astype(np.int64), device=dev) if S else None
+    d_shots = torch.full((V,), S, dtype=torch.int32, device=dev) if S else None
+    d_bits = torch.empty((V, S), dtype=torch.int64, device=dev) if S else None
+    d_val = torch.empty(V, dtype=torch.float64, device=dev)
+    d_grad = torch.empty((V, W["circuit"].n_angles), dtype=torch.float64, device=dev)
+
+    def step(k, angles=None, ev_t=None, cv_t=None, w_t=None, seeds=None, shots=None):
+        N.set_params(ac, angles if angles is not None else d_angles[k % 4])
+        val, grad = N.gradient(ac, cv_t if cv_t is not None else d_cv, ev_t if ev_t is not None else d_ev,
+                               w_t if w_t is not None else d_w, V)
+        bits = None
+        if S:
+            bits = N.sample(ac, seeds if seeds is not None else d_seeds, shots if shots is not None else d_shots, S,
+                            out=d_bits)
+        return val, grad, bits
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for k in range(args.warmup):
+        step(k)
+    barrier()
+    N.stats_enable(ac, True, 1 << 20)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(args.steps):
+        step(k)
+    e1.record()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    stats = N.get_stats(ac)
+    N.stats_enable(ac, False, 0)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    units_per_step = V * S if S else n_cols
+    value = units_per_step * world * args.steps / (ms_max / 1e3)
+
+    # ---- end to end through the public API: pinned host inputs in, results out, every step
+    h_angles = [torch.tensor(a).pin_memory() for a in angle_sets]
+    h_ev, h_cv, h_w = torch.tensor(ev).pin_memory(), torch.tensor(cv).pin_memory(), torch.tensor(w).pin_memory()
+    h_seeds = torch.tensor(W["seeds"].astype(np.int64)).pin_memory() if S else None
+    h_shots = torch.full((V,), S, dtype=torch.int32).pin_memory() if S else None
+    h_bits = torch.empty((V, S), dtype=torch.int64).pin_memory() if S else None
+    h_val = torch.empty(V, dtype=torch.float64).pin_memory()
+    h_grad = torch.empty((V, W["circuit"].n_angles), dtype=torch.float64).pin_memory()
+    h2d = (h_angles[0].numel() * 8 + h_ev.numel() + h_cv.numel() * 4 + h_w.numel() * 8 +
+           (h_seeds.numel() * 8 + h_shots.numel() * 4 if S else 0))
+    d2h = h_val.numel() * 8 + h_grad.numel() * 8 + (h_bits.numel() * 8 if S else 0)
+
+    def e2e_step(k):
+        a = h_angles[k % 4].to(dev, non_blocking=True)
+        e_ = h_ev.to(dev, non_blocking=True)
+        c_ = h_cv.to(dev, non_blocking=True)
+        w_ = h_w.to(dev, non_blocking=True)
+        sd = h_seeds.to(dev, non_blocking=True) if S else None
+        sh = h_shots.to(dev, non_blocking=True) if S else None
+        val, grad, bits = step(k, a, e_, c_, w_, sd, sh)
+        h_val.copy_(val, non_blocking=True)
+        h_grad.copy_(grad, non_blocking=True)
+        if S:
+            h_bits.copy_(bits, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    for k in range(min(args.warmup, 2)):
+        e2e_step(k)
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        e2e_step(k)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = units_per_step * world * args.steps / float(t.item())
+
+    if rank == 0:
+        peaks = {}
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                peaks = json.load(f)
+        except OSError:
+            pass
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+        up_gbs = stats["up_bytes"] / (stats["up_ms"] * 1e6) if stats["up_ms"] > 0 else None
+        dn_gbs = stats["down_bytes"] / (stats["down_ms"] * 1e6) if stats["down_ms"] > 0 else None
+        dominant = "up_level_f32" if stats["up_ms"] >= stats["down_ms"] else "down_level_f32"
+        ach = up_gbs if dominant == "up_level_f32" else dn_gbs
+        per_launch_bytes = (stats["up_bytes"] / max(1, stats["up_launches"])) if dominant == "up_level_f32" else \
+            (stats["down_bytes"] / max(1, stats["down_launches"]))
+        edge_evals = (info["n_edges"] * (stats["up_columns"] + stats["down_columns"]))
+        line = {
+            "metric": W["metric"], "value": value, "unit": W["unit"], "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": W["name"], "qubits": W["circuit"].n_qubits, "vectors_per_gpu": V, "shots": S,
+                       "hamiltonian_terms": len(W["coef"]), "ac_nodes": info["n_nodes"],
+                       "ac_edges": info["n_edges"], "ac_levels": info["n_levels"],
+                       "precision": "complex FP32 nodes, power-of-two scale per (level, column); FP64 decisions",
+                       "l2": "inputs larger than L2: node buffer = nodes x tile columns x 8 B "
+                             f"({info['n_nodes'] * info['reserved_columns'] * 8 / 1e9:.1f} GB)"},
+            "roofline": {"bound": "hbm", "kernel": dominant, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                         "frac": (ach / hbm) if ach else None, "peak_source": peak_src,
+                         "bytes_per_launch": per_launch_bytes, "traffic": None,
+                         "up_pass_gbs": up_gbs, "down_pass_gbs": dn_gbs},
+            "gpu_launches": stats["launches"],
+            "edge_evals_per_s": edge_evals * world / (ms_max / 1e3),
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": W["unit"], "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = oracle_rate(W, ac_bytes)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_uppass(args):
+    """Small profiling case: the upward pass alone over `--columns` columns whose
+    evidence fixes a random prefix of the qubits (the sampler's column shape)."""
+    import torch
+    from paper_2103_17226_gb300.build import build_library
+    build_library()
+    from paper_2103_17226_gb300 import inputs as I, native as N
+    W = make_workload(args.workload, args.shots)
+    c = W["circuit"]
+    n = c.n_qubits
+    ac = N.load_ac(N.Context(0), N.compile(c, N.QKC_AC_DENSITY), precision=32)
+    rng = I.SplitMix(17)
+    ev = np.full((args.columns, n), -1, dtype=np.int8)
+    for k in range(args.columns):
+        L = rng.randint(n)
+        ev[k, :L] = [rng.randint(2) for _ in range(L)]
+    cv = np.array([k % W["V"] for k in range(args.columns)], dtype=np.int32)
+    d_ev, d_cv = torch.tensor(ev, device="cuda"), torch.tensor(cv, device="cuda")
+    N.set_params(ac, torch.tensor(W["angles"], device="cuda"))
+    N.reserve(ac, W["V"], args.columns)
+    out = N.evaluate(ac, d_cv, d_ev)
+    for _ in range(args.warmup):
+        N.evaluate(ac, d_cv, d_ev, out=out)
+    torch.cuda.synchronize()
+    N.stats_enable(ac, True, 1 << 12)
+    for _ in range(args.steps):
+        N.evaluate(ac, d_cv, d_ev, out=out)
+    st = N.get_stats(ac)
+    print(json.dumps({"mode": "uppass", "workload": W["name"], "columns": args.columns,
+                      "up_ms_per_pass": st["up_ms"] / max(1, st["up_passes"]),
+                      "up_gbs": st["up_bytes"] / (st["up_ms"] * 1e6), "launches": st["launches"]}), flush=True)
+
+
+def main():
+    args = parse()
+    if args.mode == "uppass":
+        run_uppass(args)
+        return
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -104,6 +104,16 @@ qkc_status qkc_compile(const qkc_op *ops, int32_t n_ops, int32_t n_qubits, int32
 void qkc_free_bytes(uint8_t *bytes);
 
 /*
+ * qkc_plan -- the elimination order qkc_compile would use, without building
+ * nodes: *table_entries = sum over eliminated variables of the product of the
+ * cardinalities of the variable and its neighbours (about the node count), and
+ * *max_log2_table = log2 of the largest such table (the order's width in bits).
+ * Lets a caller reject a circuit whose AC would not fit before compiling it.
+ */
+qkc_status qkc_plan(const qkc_op *ops, int32_t n_ops, int32_t n_qubits, int32_t n_angles, int32_t kind,
+                    int32_t order, double *table_entries, double *max_log2_table);
+
+/*
  * Compiled-AC byte format (little endian, version 1).  Header of 16 uint32:
  *   [0] magic 0x43414B51 ("QKAC")  [1] version = 1  [2] kind  [3] n_qubits
  *   [4] n_angles  [5] n_vars  [6] n_nodes  [7] n_edges  [8] n_levels
@@ -219,6 +229,28 @@ qkc_status qkc_gradient(qkc_ac *ac, const int32_t *col_vec_dev, const int8_t *ev
  */
 qkc_status qkc_sample(qkc_ac *ac, const uint64_t *seeds_dev, const int32_t *shots_dev,
                       int64_t n_vectors, int64_t max_shots, uint64_t *bits_dev, void *stream);
+
+/*
+ * Measurement support (no counterpart in the paper).  qkc_stats_enable resets
+ * the counters and, when enable != 0, records a pair of CUDA events around
+ * every chain of level kernels (upward or downward pass of one column tile)
+ * issued by later calls on this AC, with the number of columns that chain
+ * processed, up to max_records chains.  qkc_get_stats waits for the recorded
+ * events and returns the launch count of this library's kernels and, per pass
+ * kind, the summed event time and the algorithmic bytes the level kernels move:
+ * upward  (E + N - leaves) x elem per column (child reads, node writes);
+ * downward (E + E_mul + N - 1) x elem per column (parent adjoints, siblings of
+ * products, node writes); elem = 8 (FP32 complex) or 16 (FP64 complex).
+ */
+typedef struct {
+    int64_t launches, records;
+    int64_t up_passes, up_columns, up_launches;
+    double up_ms, up_bytes;
+    int64_t down_passes, down_columns, down_launches;
+    double down_ms, down_bytes;
+} qkc_stats;
+qkc_status qkc_stats_enable(qkc_ac *ac, int32_t enable, int64_t max_records);
+qkc_status qkc_get_stats(qkc_ac *ac, qkc_stats *out);
 
 /* Message of the last failed call on this host thread ("" if none). */
 const char *qkc_last_error(void);

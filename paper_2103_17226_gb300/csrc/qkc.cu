@@ -624,6 +624,13 @@ __global__ void sample_write(int64_t n_vec, int64_t max_shots, const int32_t *sh
     bits[t] = s_bits[t];
 }
 
+// active column count of one timed pass, for the live roofline (stats mode)
+__global__ void stat_record(const int32_t *n_active, int64_t col0, int64_t ncols, int64_t *dst) {
+    int64_t c = ncols;
+    if (n_active) c = min(ncols, (int64_t)(*n_active) - col0);
+    *dst = c > 0 ? c : 0;
+}
+
 inline unsigned grid_for(int64_t work, int64_t per_block = TPB, int64_t cap = 152LL * 64) {
     int64_t b = (work + per_block - 1) / per_block;
     if (b < 1) b = 1;
@@ -653,6 +660,7 @@ struct qkc_ac {
     uint32_t kind, n_qubits, n_angles, n_vars, N, E, D, n_leaves, root, n_ind, n_param, n_const;
     std::vector<uint32_t> level_off;
     int64_t max_width = 0;
+    int64_t n_mul_edges = 0;  // parent entries that carry a sibling (children of products)
     int64_t struct_bytes = 0;
     // device structure
     uint8_t *d_op = nullptr;
@@ -680,6 +688,15 @@ struct qkc_ac {
     int32_t *d_g_vec[2] = {nullptr, nullptr};
     uint64_t *d_g_prefix[2] = {nullptr, nullptr};
     double *d_g_P[2] = {nullptr, nullptr};
+
+    // stats: launches of this library's kernels, and (when enabled) CUDA events around
+    // every chain of level kernels with the number of columns it processed
+    int64_t launches = 0;
+    bool timing = false;
+    struct Rec { cudaEvent_t e0, e1; int kind; };  // kind 0 upward, 1 downward
+    std::vector<Rec> recs;
+    int64_t *d_statcols = nullptr;
+    int64_t statcap = 0;
 
     DevAC dev() const {
         DevAC d;
@@ -731,10 +748,17 @@ static void free_scratch(qkc_ac *a) {
     a->vec_cap = a->tile = a->root_cap = a->samp_cap = a->grp_cap = 0;
 }
 
+static void drop_records(qkc_ac *a) {
+    for (auto &r : a->recs) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+    a->recs.clear();
+}
+
 extern "C" void qkc_free_ac(qkc_ac *a) {
     if (!a) return;
     cudaSetDevice(a->ctx->device);
     cudaDeviceSynchronize();
+    drop_records(a);
+    cudaFree(a->d_statcols);
     free_scratch(a);
     cudaFree(a->d_op); cudaFree(a->d_child_off); cudaFree(a->d_child); cudaFree(a->d_par_off);
     cudaFree(a->d_par); cudaFree(a->d_node_level); cudaFree(a->d_cl_off); cudaFree(a->d_cl);
@@ -881,6 +905,8 @@ extern "C" qkc_status qkc_load_ac(qkc_ctx *ctx, const uint8_t *bytes, uint64_t l
     a->ctx = ctx; a->prec = precision; a->kind = kind; a->n_qubits = nq; a->n_angles = na; a->n_vars = nv;
     a->N = N; a->E = E; a->D = D; a->n_leaves = nl; a->root = root; a->n_ind = nind; a->n_param = n_param;
     a->n_const = nl - nind - n_param; a->level_off = lo;
+    for (uint32_t i = nl; i < N; ++i)
+        if (op[i] == OP_MUL) a->n_mul_edges += coff[i + 1] - coff[i];
     for (uint32_t l = 0; l < D; ++l) a->max_width = std::max<int64_t>(a->max_width, lo[l + 1] - lo[l]);
     qkc_status st = QKC_OK;
     int64_t &b = a->struct_bytes;
@@ -1004,6 +1030,7 @@ extern "C" qkc_status qkc_set_params(qkc_ac *a, const double *angles, int64_t n_
         else
             bind_params_kernel<double2><<<grid_for(work), TPB, 0, s>>>(a->dev(), angles, n_vec, a->vec_cap,
                                                                        (double2 *)a->d_pv);
+        ++a->launches;
         QKC_LAUNCH_CHECK();
     }
     a->n_vec = n_vec;
@@ -1012,10 +1039,33 @@ extern "C" qkc_status qkc_set_params(qkc_ac *a, const double *angles, int64_t n_
 }
 
 // ---- one upward pass over a column tile [col0, col0 + ncols)
+// Opens a timed record (stats mode): event before the level-kernel chain; the
+// active column count is written by a tiny kernel so device-side counts work.
+static qkc_status rec_begin(qkc_ac *a, int kind, const int32_t *n_active, int64_t col0, int64_t ncols,
+                            cudaStream_t s) {
+    if (!a->timing) return QKC_OK;
+    if ((int64_t)a->recs.size() >= a->statcap) return QKC_OK;  // record buffer full: stop recording
+    qkc_ac::Rec r;
+    r.kind = kind;
+    QKC_CUDA(cudaEventCreate(&r.e0));
+    QKC_CUDA(cudaEventCreate(&r.e1));
+    stat_record<<<1, 1, 0, s>>>(n_active, col0, ncols, a->d_statcols + a->recs.size());
+    ++a->launches;
+    QKC_CUDA(cudaEventRecord(r.e0, s));
+    a->recs.push_back(r);
+    return QKC_OK;
+}
+static qkc_status rec_end(qkc_ac *a, size_t idx, cudaStream_t s) {
+    if (!a->timing || idx >= a->recs.size()) return QKC_OK;
+    QKC_CUDA(cudaEventRecord(a->recs[idx].e1, s));
+    return QKC_OK;
+}
+
 static qkc_status run_up(qkc_ac *a, const EvSrc &es, int64_t col0, int64_t ncols, cudaStream_t s) {
     const int64_t pitch = a->tile;
     const DevAC d = a->dev();
     const int sms = a->ctx->sm_count;
+    qkc_status st;
     if (a->prec == 32) {
         // level 0: leaves (S[0] = 0 and obs[0] reset by the scale kernel, then observed)
         level_scale_kernel<<<(unsigned)((pitch + TPB - 1) / TPB), TPB, 0, s>>>(d, 0, pitch, ncols, a->d_S, a->d_obs);
@@ -1023,6 +1073,9 @@ static qkc_status run_up(qkc_ac *a, const EvSrc &es, int64_t col0, int64_t ncols
             d, es, col0, ncols, pitch, (const float2 *)a->d_pv, a->vec_cap, (float2 *)a->d_V, a->d_obs,
             (int)a->n_leaves);
         QKC_LAUNCH_CHECK();
+        a->launches += 2;
+        const size_t ri = a->recs.size();
+        if ((st = rec_begin(a, 0, es.n_active, col0, ncols, s))) return st;
         for (uint32_t L = 1; L < a->D; ++L) {
             level_scale_kernel<<<(unsigned)((pitch + TPB - 1) / TPB), TPB, 0, s>>>(d, (int)L, pitch, ncols, a->d_S,
                                                                                    a->d_obs);
@@ -1031,16 +1084,23 @@ static qkc_status run_up(qkc_ac *a, const EvSrc &es, int64_t col0, int64_t ncols
             up_level_f32<<<grid_for(items * 32, TPB, (int64_t)sms * 8), TPB, 0, s>>>(d, la, (float2 *)a->d_V, a->d_S,
                                                                                     a->d_obs);
         }
+        a->launches += 2 * (int64_t)(a->D - 1);
+        if ((st = rec_end(a, ri, s))) return st;
         QKC_LAUNCH_CHECK();
     } else {
         bind_leaves_f64<<<grid_for((int64_t)a->n_leaves * pitch), TPB, 0, s>>>(
             d, es, col0, ncols, pitch, (const double2 *)a->d_pv, a->vec_cap, (double2 *)a->d_V, (int)a->n_leaves);
         QKC_LAUNCH_CHECK();
+        a->launches += 1;
+        const size_t ri = a->recs.size();
+        if ((st = rec_begin(a, 0, es.n_active, col0, ncols, s))) return st;
         for (uint32_t L = 1; L < a->D; ++L) {
             LevelArgs la{a->level_off[L], a->level_off[L + 1], (int)L, pitch, ncols, es.n_active, col0};
             const int64_t items = ((int64_t)(la.hi - la.lo + NB - 1) / NB) * ((ncols + 31) / 32);
             up_level_f64<<<grid_for(items * 32, TPB, (int64_t)sms * 8), TPB, 0, s>>>(d, la, (double2 *)a->d_V);
         }
+        a->launches += (int64_t)(a->D - 1);
+        if ((st = rec_end(a, ri, s))) return st;
         QKC_LAUNCH_CHECK();
     }
     return QKC_OK;
@@ -1053,6 +1113,7 @@ static qkc_status run_roots(qkc_ac *a, int64_t col0, int64_t ncols, const int32_
                                    col0, a->d_root);
     else
         root_f64<<<g, TPB, 0, s>>>((const double2 *)a->d_V, a->tile, a->root, ncols, n_active, col0, a->d_root);
+    ++a->launches;
     QKC_LAUNCH_CHECK();
     return QKC_OK;
 }
@@ -1062,6 +1123,10 @@ static qkc_status run_down(qkc_ac *a, int64_t ncols, cudaStream_t s) {
     const DevAC d = a->dev();
     const int sms = a->ctx->sm_count;
     const unsigned g = (unsigned)((ncols + TPB - 1) / TPB);
+    qkc_status st;
+    const size_t ri = a->recs.size();
+    if ((st = rec_begin(a, 1, nullptr, 0, ncols, s))) return st;
+    a->launches += (int64_t)a->D;
     if (a->prec == 32) {
         seed_root<float2><<<g, TPB, 0, s>>>((float2 *)a->d_A, pitch, a->root, ncols);
         for (int L = (int)a->D - 2; L >= 0; --L) {
@@ -1079,6 +1144,7 @@ static qkc_status run_down(qkc_ac *a, int64_t ncols, cudaStream_t s) {
                 d, la, (const double2 *)a->d_V, (double2 *)a->d_A);
         }
     }
+    if ((st = rec_end(a, ri, s))) return st;
     QKC_LAUNCH_CHECK();
     return QKC_OK;
 }
@@ -1098,8 +1164,8 @@ extern "C" qkc_status qkc_evaluate(qkc_ac *a, const int32_t *col_vec, const int8
                                    double *out, void *stream) {
     qkc_status st = check_query(a, col_vec, ev, n_cols, "qkc_evaluate");
     if (st) return st;
-    if (!out) return fail(QKC_ERR_ARG, "qkc_evaluate: out is null");
     if (n_cols == 0) return QKC_OK;
+    if (!out) return fail(QKC_ERR_ARG, "qkc_evaluate: out is null");
     QKC_CUDA(cudaSetDevice(a->ctx->device));
     if ((st = ensure_tile(a, n_cols)) || (st = ensure_roots(a, n_cols))) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1117,8 +1183,8 @@ extern "C" qkc_status qkc_marginals(qkc_ac *a, const int32_t *col_vec, const int
                                     double *root_out, double *marg_out, void *stream) {
     qkc_status st = check_query(a, col_vec, ev, n_cols, "qkc_marginals");
     if (st) return st;
-    if (!marg_out) return fail(QKC_ERR_ARG, "qkc_marginals: marg_out is null");
     if (n_cols == 0) return QKC_OK;
+    if (!marg_out) return fail(QKC_ERR_ARG, "qkc_marginals: marg_out is null");
     QKC_CUDA(cudaSetDevice(a->ctx->device));
     if ((st = ensure_tile(a, n_cols)) || (st = ensure_roots(a, n_cols)) || (st = ensure_adj(a))) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1135,6 +1201,7 @@ extern "C" qkc_status qkc_marginals(qkc_ac *a, const int32_t *col_vec, const int
         else
             gather_marginals<double2><<<grid_for(work), TPB, 0, s>>>((const double2 *)a->d_A, a->tile, (int)a->n_ind,
                                                                     nc, c0, (double2 *)marg_out);
+        ++a->launches;
         QKC_LAUNCH_CHECK();
     }
     if (root_out)
@@ -1170,6 +1237,7 @@ extern "C" qkc_status qkc_gradient(qkc_ac *a, const int32_t *col_vec, const int8
             gradient_accumulate<double2><<<grid_for(work), TPB, 0, s>>>(a->dev(), (const double2 *)a->d_A, a->tile, nc,
                                                                        c0, col_vec, n_vectors, a->last_angles, weight,
                                                                        a->d_root, value, grad);
+        ++a->launches;
         QKC_LAUNCH_CHECK();
     }
     return QKC_OK;
@@ -1232,6 +1300,7 @@ extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t
             if ((st = run_roots(a, c0, nc, nullptr, s))) return st;
         }
         sample_set_total<<<(unsigned)((n_vec + TPB - 1) / TPB), TPB, 0, s>>>(a->d_root, n_vec, a->d_g_P[cur]);
+        a->launches += 2;  // init + totals
         QKC_LAUNCH_CHECK();
     }
     int64_t bound = n_vec;  // host upper bound of the group count
@@ -1256,11 +1325,66 @@ extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t
             gcount, a->d_flag, a->d_pos, a->d_bsum, a->d_g_vec[cur], a->d_g_prefix[cur], a->d_g_P[cur], a->d_root,
             a->d_g_vec[nxt], a->d_g_prefix[nxt], a->d_g_P[nxt], a->d_gcount + nxt);
         sample_remap<<<gs, TPB, 0, s>>>(n_vec, max_shots, shots, a->d_pos, a->d_bsum, a->d_s_group, a->d_s_bits);
+        a->launches += 5;
         QKC_LAUNCH_CHECK();
         cur = nxt;
         bound = std::min<int64_t>(2 * bound, n_samp);
     }
     sample_write<<<gs, TPB, 0, s>>>(n_vec, max_shots, shots, a->d_s_bits, bits);
+    ++a->launches;
     QKC_LAUNCH_CHECK();
+    return QKC_OK;
+}
+
+extern "C" qkc_status qkc_stats_enable(qkc_ac *a, int32_t enable, int64_t max_records) {
+    if (!a || max_records < 0) return fail(QKC_ERR_ARG, "qkc_stats_enable: bad argument");
+    QKC_CUDA(cudaSetDevice(a->ctx->device));
+    QKC_CUDA(cudaDeviceSynchronize());
+    drop_records(a);
+    if (enable && max_records > a->statcap) {
+        cudaFree(a->d_statcols);
+        a->d_statcols = nullptr;
+        a->statcap = 0;
+        QKC_CUDA(cudaMalloc((void **)&a->d_statcols, sizeof(int64_t) * (size_t)max_records));
+        a->statcap = max_records;
+    }
+    a->timing = enable != 0;
+    a->launches = 0;
+    return QKC_OK;
+}
+
+extern "C" qkc_status qkc_get_stats(qkc_ac *a, qkc_stats *o) {
+    if (!a || !o) return fail(QKC_ERR_ARG, "qkc_get_stats: bad argument");
+    QKC_CUDA(cudaSetDevice(a->ctx->device));
+    std::memset(o, 0, sizeof(*o));
+    o->launches = a->launches;
+    if (!a->recs.empty()) {
+        std::vector<int64_t> cols(a->recs.size());
+        QKC_CUDA(cudaMemcpy(cols.data(), a->d_statcols, sizeof(int64_t) * cols.size(), cudaMemcpyDeviceToHost));
+        const double elem = (double)a->elem();
+        for (size_t i = 0; i < a->recs.size(); ++i) {
+            float ms = 0.f;
+            QKC_CUDA(cudaEventSynchronize(a->recs[i].e1));
+            QKC_CUDA(cudaEventElapsedTime(&ms, a->recs[i].e0, a->recs[i].e1));
+            if (a->recs[i].kind == 0) {
+                o->up_passes += 1;
+                o->up_columns += cols[i];
+                o->up_ms += ms;
+                o->up_launches += (int64_t)(a->D - 1);
+                // child reads + node writes of the internal nodes (the algorithmic bytes of the level kernels)
+                o->up_bytes += elem * ((double)a->E + (double)(a->N - a->n_leaves)) * (double)cols[i];
+            } else {
+                o->down_passes += 1;
+                o->down_columns += cols[i];
+                o->down_ms += ms;
+                o->down_launches += (int64_t)(a->D - 1);
+                // per parent entry: the parent's adjoint (+ the sibling value for a product), one write per node
+                double reads = 0.0;
+                reads = (double)a->E + (double)a->n_mul_edges;
+                o->down_bytes += elem * (reads + (double)(a->N - 1)) * (double)cols[i];
+            }
+        }
+    }
+    o->records = (int64_t)a->recs.size();
     return QKC_OK;
 }

@@ -38,6 +38,14 @@ class ACInfo(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("reserved_columns", ctypes.c_int64)]
 
 
+class Stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("records", ctypes.c_int64),
+                ("up_passes", ctypes.c_int64), ("up_columns", ctypes.c_int64), ("up_launches", ctypes.c_int64),
+                ("up_ms", ctypes.c_double), ("up_bytes", ctypes.c_double),
+                ("down_passes", ctypes.c_int64), ("down_columns", ctypes.c_int64), ("down_launches", ctypes.c_int64),
+                ("down_ms", ctypes.c_double), ("down_bytes", ctypes.c_double)]
+
+
 def lib():
     """The loaded libqkc (raises if it has not been built)."""
     global _lib
@@ -60,6 +68,8 @@ def lib():
         "qkc_marginals": [P, P, P, I64, P, P, P],
         "qkc_gradient": [P, P, P, P, I64, I64, P, P, P],
         "qkc_sample": [P, P, P, I64, I64, P, P],
+        "qkc_stats_enable": [P, I32, I64],
+        "qkc_get_stats": [P, ctypes.POINTER(Stats)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -262,3 +272,15 @@ def sample(ac: AC, seeds, shots, max_shots: int, out=None, stream=None):
         out = torch.zeros((n_vec, max_shots), dtype=torch.int64, device=seeds.device)
     _check(lib().qkc_sample(ac._h, _ptr(seeds), _ptr(shots), n_vec, max_shots, _ptr(out), _stream(stream)))
     return out
+
+
+def stats_enable(ac: AC, enable: bool = True, max_records: int = 1 << 16):
+    """qkc_stats_enable: reset counters; record event-timed level-kernel chains."""
+    _check(lib().qkc_stats_enable(ac._h, 1 if enable else 0, max_records))
+
+
+def get_stats(ac: AC) -> dict:
+    """qkc_get_stats: launches, and per pass kind the event time and algorithmic bytes."""
+    st = Stats()
+    _check(lib().qkc_get_stats(ac._h, ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in Stats._fields_}
