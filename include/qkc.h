@@ -231,6 +231,33 @@ qkc_status qkc_sample(qkc_ac *ac, const uint64_t *seeds_dev, const int32_t *shot
                       int64_t n_vectors, int64_t max_shots, uint64_t *bits_dev, void *stream);
 
 /*
+ * qkc_evaluate_static -- the upward pass of qkc_evaluate (same arguments, same
+ * results), but it allocates nothing.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc -- a serving loop that
+ * must never stall on the implicit device synchronisation cudaMalloc/cudaFree
+ * can cause, or a host application whose own memory pool has claimed the
+ * device memory and forbids other allocations.  The caller still passes every
+ * input and output buffer, and the AC's parameters must already be bound by
+ * qkc_set_params (which allocates, once, outside the hot loop).
+ *
+ * Scratch is one file-scope device array of QKC_STATIC_SCRATCH_BYTES (64 MiB),
+ * held by every GPU that loads this library until the process exits.  Columns
+ * are processed in tiles of the largest multiple of 64 that fits it: node
+ * values (8 bytes per node per column in FP32, 16 in FP64) plus, in FP32, two
+ * int32 words per level per column.  An AC that needs more than the array for
+ * a 64-column tile is rejected with QKC_ERR_TOO_LARGE (FP32: about 130K nodes).
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  Every call uses the same array and leaves its contents behind;
+ * nothing a call reads is left over from an earlier call, but calls whose
+ * work overlaps on the GPU (other streams, other host threads, other AC
+ * handles) race on the array: serialise them.
+ */
+#define QKC_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
+qkc_status qkc_evaluate_static(qkc_ac *ac, const int32_t *col_vec_dev, const int8_t *evidence_dev,
+                               int64_t n_cols, double *out_dev, void *stream);
+
+/*
  * Measurement support (no counterpart in the paper).  qkc_stats_enable resets
  * the counters and, when enable != 0, records a pair of CUDA events around
  * every chain of level kernels (upward or downward pass of one column tile)

@@ -26,6 +26,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1386,5 +1387,95 @@ extern "C" qkc_status qkc_get_stats(qkc_ac *a, qkc_stats *o) {
         }
     }
     o->records = (int64_t)a->recs.size();
+    return QKC_OK;
+}
+
+// ------------------------------------------------------------------ upward pass without allocation
+// Scratch for qkc_evaluate_static: node values and the FP32 per-(level, column)
+// scale words of one column tile.  A file-scope device array, so every GPU that
+// loads this library holds QKC_STATIC_SCRATCH_BYTES until the process exits.
+static __device__ __align__(256) unsigned char g_static_scratch[QKC_STATIC_SCRATCH_BYTES];
+
+namespace {
+// Device address of g_static_scratch per device, looked up once per device with
+// that device current.  In host code the array's name is only a host-side
+// stand-in, so kernels must be given this address, never the name.
+std::mutex g_static_mu;
+void *g_static_ptr[128] = {nullptr};
+}  // namespace
+
+static qkc_status static_scratch(int device, void **out) {
+    if (device < 0 || device >= 128) return fail(QKC_ERR_ARG, "qkc_evaluate_static: device %d out of range", device);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(QKC_ERR_CUDA, "qkc_evaluate_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+        g_static_ptr[device] = p;
+    }
+    *out = g_static_ptr[device];
+    return QKC_OK;
+}
+
+extern "C" qkc_status qkc_evaluate_static(qkc_ac *a, const int32_t *col_vec, const int8_t *ev, int64_t n_cols,
+                                          double *out, void *stream) {
+    qkc_status st = check_query(a, col_vec, ev, n_cols, "qkc_evaluate_static");
+    if (st) return st;
+    if (n_cols == 0) return QKC_OK;
+    if (!out) return fail(QKC_ERR_ARG, "qkc_evaluate_static: out is null");
+    QKC_CUDA(cudaSetDevice(a->ctx->device));
+    void *base = nullptr;
+    if ((st = static_scratch(a->ctx->device, &base))) return st;
+    // tile: the largest multiple of 64 columns whose values (+ FP32 scale words) fit the array
+    const int64_t scale_words = a->prec == 32 ? 2LL * a->D * (int64_t)sizeof(int) : 0;
+    const int64_t per_col = (int64_t)a->N * (int64_t)a->elem() + scale_words;
+    int64_t tile = (int64_t)QKC_STATIC_SCRATCH_BYTES / per_col;
+    tile = std::min<int64_t>(tile / 64 * 64, (n_cols + 63) / 64 * 64);
+    if (tile < 64)
+        return fail(QKC_ERR_TOO_LARGE,
+                    "qkc_evaluate_static: this AC needs %lld bytes of scratch for a 64-column tile; the static "
+                    "scratch holds %lld bytes",
+                    (long long)(per_col * 64), (long long)QKC_STATIC_SCRATCH_BYTES);
+    // layout inside the array: values [N][tile], then S [D][tile], then obs [D][tile]
+    char *p = static_cast<char *>(base);
+    void *V = p;
+    int *S = reinterpret_cast<int *>(p + (size_t)a->N * tile * a->elem());
+    int *obs = S + (size_t)a->D * tile;
+    cudaStream_t s = (cudaStream_t)stream;
+    const DevAC d = a->dev();
+    const int sms = a->ctx->sm_count;
+    double2 *o = reinterpret_cast<double2 *>(out);
+    // Every scratch word a tile reads is written earlier in the same tile (leaves, then each
+    // level's scale words, then its values), so nothing left from a previous call is used.
+    for (int64_t c0 = 0; c0 < n_cols; c0 += tile) {
+        const int64_t nc = std::min<int64_t>(tile, n_cols - c0);
+        EvSrc es{ev, nullptr, 0, 0, col_vec, nullptr, std::max<int64_t>(1, a->n_vec)};
+        const unsigned gr = (unsigned)((nc + TPB - 1) / TPB);
+        if (a->prec == 32) {
+            level_scale_kernel<<<(unsigned)((tile + TPB - 1) / TPB), TPB, 0, s>>>(d, 0, tile, nc, S, obs);
+            bind_leaves_f32<<<grid_for((int64_t)a->n_leaves * tile), TPB, 0, s>>>(
+                d, es, c0, nc, tile, (const float2 *)a->d_pv, a->vec_cap, (float2 *)V, obs, (int)a->n_leaves);
+            for (uint32_t L = 1; L < a->D; ++L) {
+                level_scale_kernel<<<(unsigned)((tile + TPB - 1) / TPB), TPB, 0, s>>>(d, (int)L, tile, nc, S, obs);
+                LevelArgs la{a->level_off[L], a->level_off[L + 1], (int)L, tile, nc, nullptr, c0};
+                const int64_t items = ((int64_t)(la.hi - la.lo + NB - 1) / NB) * ((nc + 63) / 64);
+                up_level_f32<<<grid_for(items * 32, TPB, (int64_t)sms * 8), TPB, 0, s>>>(d, la, (float2 *)V, S, obs);
+            }
+            root_f32<<<gr, TPB, 0, s>>>((const float2 *)V, S, tile, a->root, (int)a->D - 1, nc, nullptr, c0, o);
+            a->launches += 3 + 2 * (int64_t)(a->D - 1);
+        } else {
+            bind_leaves_f64<<<grid_for((int64_t)a->n_leaves * tile), TPB, 0, s>>>(
+                d, es, c0, nc, tile, (const double2 *)a->d_pv, a->vec_cap, (double2 *)V, (int)a->n_leaves);
+            for (uint32_t L = 1; L < a->D; ++L) {
+                LevelArgs la{a->level_off[L], a->level_off[L + 1], (int)L, tile, nc, nullptr, c0};
+                const int64_t items = ((int64_t)(la.hi - la.lo + NB - 1) / NB) * ((nc + 31) / 32);
+                up_level_f64<<<grid_for(items * 32, TPB, (int64_t)sms * 8), TPB, 0, s>>>(d, la, (double2 *)V);
+            }
+            root_f64<<<gr, TPB, 0, s>>>((const double2 *)V, tile, a->root, nc, nullptr, c0, o);
+            a->launches += 2 + (int64_t)(a->D - 1);
+        }
+        QKC_LAUNCH_CHECK();
+    }
     return QKC_OK;
 }

@@ -68,6 +68,7 @@ def lib():
         "qkc_marginals": [P, P, P, I64, P, P, P],
         "qkc_gradient": [P, P, P, P, I64, I64, P, P, P],
         "qkc_sample": [P, P, P, I64, I64, P, P],
+        "qkc_evaluate_static": [P, P, P, I64, P, P],
         "qkc_stats_enable": [P, I32, I64],
         "qkc_get_stats": [P, ctypes.POINTER(Stats)],
     }
@@ -240,6 +241,15 @@ def evaluate(ac: AC, col_vec, evidence, out=None, stream=None):
     if out is None:
         out = torch.empty((n, 2), dtype=torch.float64, device=evidence.device)
     _check(lib().qkc_evaluate(ac._h, _ptr(col_vec), _ptr(evidence), n, _ptr(out), _stream(stream)))
+    return out
+
+
+def evaluate_static(ac: AC, col_vec, evidence, out, stream=None):
+    """qkc_evaluate_static: the upward pass into the caller's `out` [n_cols][2] float64,
+    with the library's fixed device scratch instead of allocated buffers (for callers
+    that cannot allocate device memory; see include/qkc.h)."""
+    n = _cols(col_vec, evidence, ac)
+    _check(lib().qkc_evaluate_static(ac._h, _ptr(col_vec), _ptr(evidence), n, _ptr(out), _stream(stream)))
     return out
 
 
