@@ -42,11 +42,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["qaoa32", "hea16"], default="qaoa32")
+    ap.add_argument("--workload", choices=["qaoa32", "hea16", "serve"], default="qaoa32")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: Poisson arrivals per second")
+    ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
     ap.add_argument("--shots", type=int, default=10000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["step", "uppass"], default="step",
-                    help="uppass: only the upward pass over --columns sampling-prefix columns (profiling case)")
+    ap.add_argument("--mode", choices=["step", "uppass", "gradpass"], default="step",
+                    help="uppass: only the upward pass over --columns sampling-prefix columns; gradpass: "
+                         "upward + downward pass (gradient) over --columns Z-string columns (profiling cases)")
     ap.add_argument("--columns", type=int, default=2048)
     return ap.parse_args()
 
@@ -347,6 +350,34 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_gradpass(args):
+    """Small profiling case: qkc_gradient (upward + downward pass) over `--columns`
+    Z-string columns of the workload's Hamiltonian."""
+    import torch
+    from paper_2103_17226_gb300.build import build_library
+    build_library()
+    from paper_2103_17226_gb300 import native as N
+    W = make_workload(args.workload, args.shots)
+    ac = N.load_ac(N.Context(0), N.compile(W["circuit"], N.QKC_AC_DENSITY), precision=32)
+    ev, cv, w = hamiltonian_columns(W)
+    reps = (args.columns + len(cv) - 1) // len(cv)
+    ev, cv, w = np.tile(ev, (reps, 1))[:args.columns], np.tile(cv, reps)[:args.columns], np.tile(w, reps)[:args.columns]
+    d_ev, d_cv, d_w = (torch.tensor(x, device="cuda") for x in (ev, cv, w))
+    N.set_params(ac, torch.tensor(W["angles"], device="cuda"))
+    N.reserve(ac, W["V"], args.columns)
+    for _ in range(args.warmup + 1):
+        N.gradient(ac, d_cv, d_ev, d_w, W["V"])
+    torch.cuda.synchronize()
+    N.stats_enable(ac, True, 1 << 12)
+    for _ in range(args.steps):
+        N.gradient(ac, d_cv, d_ev, d_w, W["V"])
+    st = N.get_stats(ac)
+    print(json.dumps({"mode": "gradpass", "workload": W["name"], "columns": args.columns,
+                      "up_gbs": st["up_bytes"] / (st["up_ms"] * 1e6), "down_gbs": st["down_bytes"] / (st["down_ms"] * 1e6),
+                      "down_ms_per_pass": st["down_ms"] / max(1, st["down_passes"]), "launches": st["launches"]}),
+          flush=True)
+
+
 def run_uppass(args):
     """Small profiling case: the upward pass alone over `--columns` columns whose
     evidence fixes a random prefix of the qubits (the sampler's column shape)."""
@@ -380,10 +411,46 @@ def run_uppass(args):
                       "up_gbs": st["up_bytes"] / (st["up_ms"] * 1e6), "launches": st["launches"]}), flush=True)
 
 
+def run_serve(args):
+    """Serving: Poisson arrivals over 8 resident noisy-QAOA density ACs (p=1 on 8, 12, 16, 20
+    qubits, two random 3-regular graphs each; 1q depolarising 0.001, 2q depolarising 0.01),
+    one parameter vector and log-uniform shots in [100, 10000] per request.  Continuous
+    batching (FP32, 2 lanes per AC) vs the FP64 one-request-at-a-time path on the same stream."""
+    import torch
+    from paper_2103_17226_gb300.build import build_library
+    build_library()
+    from paper_2103_17226_gb300 import inputs as I, native as N
+    from paper_2103_17226_gb300.serve import Server, poisson_requests
+    circs = {}
+    for n in (8, 12, 16, 20):
+        for g in (0, 1):
+            circs[f"qaoa{n}_g{g}"] = I.qaoa_maxcut(n, I.random_regular_graph(n, 3, seed=40 + n + 100 * g), 1,
+                                                  I.NOISE_CFG2, name=f"qaoa{n}_g{g}")
+    acs = {k: N.compile(c, N.QKC_AC_DENSITY) for k, c in circs.items()}
+    reqs = poisson_requests(list(acs), {k: c.n_angles for k, c in circs.items()}, args.rate, args.duration, seed=4)
+    ctx = N.Context(0)
+    srv = Server(ctx, acs, precision=32, lanes=2, max_batch=32, max_shots=10000, tile_columns=8192)
+    res, st = srv.run(reqs, time_limit=args.duration * 4)
+    del srv
+    torch.cuda.empty_cache()
+    base = Server(ctx, acs, precision=64, lanes=1, max_batch=1, max_shots=10000, tile_columns=4096, serial=True)
+    res_b, st_b = base.run(reqs, time_limit=args.duration * 4)
+    print(json.dumps({"metric": "serving samples/s and p50/p99 latency", "workload": "serve_qaoa_8acs",
+                      "rate_per_s": args.rate, "duration_s": args.duration, "requests": len(reqs),
+                      "ours_fp32_continuous": st, "baseline_fp64_one_at_a_time": st_b,
+                      "ac_nodes": {k: N.header(b)["n_nodes"] for k, b in acs.items()}}), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "serve":
+        run_serve(args)
+        return
     if args.mode == "uppass":
         run_uppass(args)
+        return
+    if args.mode == "gradpass":
+        run_gradpass(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -171,6 +171,15 @@ qkc_status qkc_get_info(const qkc_ac *ac, qkc_ac_info *out);
 qkc_status qkc_reserve(qkc_ac *ac, int64_t max_vectors, int64_t max_columns);
 
 /*
+ * qkc_set_tile_limit -- cap the column tile of this AC (0 = default: values and
+ * adjoints each within 35% of the device memory; otherwise >= 64, rounded down
+ * to a multiple of 64).  Calls with more columns than the tile process them in
+ * tiles.  Lets many resident ACs share one device (serving).  Takes effect on
+ * the next scratch growth; set it before the first query.
+ */
+qkc_status qkc_set_tile_limit(qkc_ac *ac, int64_t max_tile_columns);
+
+/*
  * qkc_set_params -- bind gate parameters (Sec. 3.2.1, Table 4: parameters are
  * weight variables resolved at simulation time).  angles_dev is [n_vectors]
  * [n_angles] float64, row-major.  Every PARAM leaf gets c g(angle) per vector.

@@ -345,16 +345,42 @@ __global__ void __launch_bounds__(TPB) up_level_f64(DevAC ac, LevelArgs a, doubl
     }
 }
 
-// ------------------------------------------------------------------ downward pass, one level
-// A[n] = sum over parents p of A[p] * (p is + ? 1 : true value of the sibling).
-// Adjoints are plain (unscaled) values; FP32 siblings are rebuilt as m * 2^S.
-__global__ void __launch_bounds__(TPB) down_level_f32(DevAC ac, LevelArgs a, const float2 *__restrict__ V,
-                                                       const int *__restrict__ S, float2 *__restrict__ A) {
-    int64_t ncols = a.ncols;
-    if (ncols <= 0) return;
+// ------------------------------------------------------------------ downward pass, split by fan-out
+// Per level, nodes whose parent lists hold at most HEAVY entries are "light": a warp owns NB
+// of them x one column chunk and walks each parent list four entries at a time (independent
+// loads in flight).  "Heavy" nodes get a whole block per column chunk: its 8 warps take the
+// parents round-robin and the partial sums are added in warp order (deterministic).  CONST
+// leaves are never visited: their adjoints are not used.
+constexpr int HEAVY = 64;
+
+__device__ __forceinline__ float4 down_term_f32(const int2 ps, const float4 *A4, const float4 *V4, const int *S,
+                                                const uint16_t *node_level, int64_t hp, int64_t pitch, int64_t col) {
+    const float4 dp = A4[(int64_t)ps.x * hp + (col >> 1)];
+    if (ps.y < 0) return dp;
+    const int ls = node_level[ps.y];
+    const float4 vs = __ldg(V4 + (int64_t)ps.y * hp + (col >> 1));
+    const int2 ss = __ldg(reinterpret_cast<const int2 *>(S + (int64_t)ls * pitch + col));
+    const float2 s0 = cscale(make_float2(vs.x, vs.y), pow2f(ss.x));
+    const float2 s1 = cscale(make_float2(vs.z, vs.w), pow2f(ss.y));
+    const float2 t0 = cmul(make_float2(dp.x, dp.y), s0);
+    const float2 t1 = cmul(make_float2(dp.z, dp.w), s1);
+    return make_float4(t0.x, t0.y, t1.x, t1.y);
+}
+__device__ __forceinline__ void acc4(float4 &a, const float4 b) { a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w; }
+
+struct DownArgs {
+    const uint32_t *nodes;  // node ids of this level's light (or heavy) list
+    int64_t count;
+    int64_t pitch, ncols;
+};
+
+__global__ void __launch_bounds__(TPB) down_light_f32(DevAC ac, DownArgs a, const float2 *__restrict__ V,
+                                                       const int *__restrict__ S, float2 *A) {
+    const int64_t ncols = a.ncols;
+    if (ncols <= 0 || a.count <= 0) return;
     const int lane = threadIdx.x & 31;
     const int64_t nchunks = (ncols + 63) >> 6;
-    const int64_t nblk = (a.hi - a.lo + NB - 1) / NB;
+    const int64_t nblk = (a.count + NB - 1) / NB;
     const int64_t items = nblk * nchunks;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -366,38 +392,68 @@ __global__ void __launch_bounds__(TPB) down_level_f32(DevAC ac, LevelArgs a, con
         const int64_t blk = it / nchunks;
         const int64_t col = chunk * 64 + lane * 2;
         if (col >= ncols) continue;
-        const uint32_t n0 = a.lo + (uint32_t)blk * NB;
-        const uint32_t n1 = min(a.hi, n0 + NB);
-        for (uint32_t n = n0; n < n1; ++n) {
+        const int64_t k1 = min(a.count, (blk + 1) * NB);
+        for (int64_t k = blk * NB; k < k1; ++k) {
+            const uint32_t n = a.nodes[k];
+            const uint32_t e1 = ac.par_off[n + 1];
+            uint32_t e = ac.par_off[n];
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (uint32_t e = ac.par_off[n]; e < ac.par_off[n + 1]; ++e) {
-                const int2 ps = ac.par[e];
-                const float4 dp = A4[(int64_t)ps.x * hp + (col >> 1)];
-                if (ps.y < 0) {
-                    acc.x += dp.x; acc.y += dp.y; acc.z += dp.z; acc.w += dp.w;
-                } else {
-                    const int ls = ac.node_level[ps.y];
-                    const float4 vs = __ldg(V4 + (int64_t)ps.y * hp + (col >> 1));
-                    const int2 ss = __ldg(reinterpret_cast<const int2 *>(S + (int64_t)ls * a.pitch + col));
-                    const float2 s0 = cscale(make_float2(vs.x, vs.y), pow2f(ss.x));
-                    const float2 s1 = cscale(make_float2(vs.z, vs.w), pow2f(ss.y));
-                    const float2 t0 = cmul(make_float2(dp.x, dp.y), s0);
-                    const float2 t1 = cmul(make_float2(dp.z, dp.w), s1);
-                    acc.x += t0.x; acc.y += t0.y; acc.z += t1.x; acc.w += t1.y;
-                }
+            for (; e + 4 <= e1; e += 4) {
+                const int2 p0 = ac.par[e], p1 = ac.par[e + 1], p2 = ac.par[e + 2], p3 = ac.par[e + 3];
+                const float4 t0 = down_term_f32(p0, A4, V4, S, ac.node_level, hp, a.pitch, col);
+                const float4 t1 = down_term_f32(p1, A4, V4, S, ac.node_level, hp, a.pitch, col);
+                const float4 t2 = down_term_f32(p2, A4, V4, S, ac.node_level, hp, a.pitch, col);
+                const float4 t3 = down_term_f32(p3, A4, V4, S, ac.node_level, hp, a.pitch, col);
+                acc4(acc, t0); acc4(acc, t1); acc4(acc, t2); acc4(acc, t3);
             }
+            for (; e < e1; ++e) acc4(acc, down_term_f32(ac.par[e], A4, V4, S, ac.node_level, hp, a.pitch, col));
             A4[(int64_t)n * hp + (col >> 1)] = acc;
         }
     }
 }
 
-__global__ void __launch_bounds__(TPB) down_level_f64(DevAC ac, LevelArgs a, const double2 *__restrict__ V,
-                                                       double2 *__restrict__ A) {
-    int64_t ncols = a.ncols;
-    if (ncols <= 0) return;
+__global__ void __launch_bounds__(TPB) down_heavy_f32(DevAC ac, DownArgs a, const float2 *__restrict__ V,
+                                                       const int *__restrict__ S, float2 *A) {
+    __shared__ float4 part[TPB / 32][32];
+    const int64_t ncols = a.ncols;
+    const int64_t nchunks = (ncols + 63) >> 6;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t hp = a.pitch >> 1;
+    const float4 *V4 = reinterpret_cast<const float4 *>(V);
+    float4 *A4 = reinterpret_cast<float4 *>(A);
+    for (int64_t it = blockIdx.x; it < a.count * nchunks; it += gridDim.x) {
+        const int64_t chunk = it % nchunks;
+        const uint32_t n = a.nodes[it / nchunks];
+        const int64_t col = chunk * 64 + lane * 2;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (col < ncols)
+            for (uint32_t e = ac.par_off[n] + w; e < ac.par_off[n + 1]; e += TPB / 32)
+                acc4(acc, down_term_f32(ac.par[e], A4, V4, S, ac.node_level, hp, a.pitch, col));
+        part[w][lane] = acc;
+        __syncthreads();
+        if (w == 0 && col < ncols) {
+            float4 t = part[0][lane];
+            for (int k = 1; k < TPB / 32; ++k) acc4(t, part[k][lane]);
+            A4[(int64_t)n * hp + (col >> 1)] = t;
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ double2 down_term_f64(const int2 ps, const double2 *A, const double2 *V, int64_t pitch,
+                                                 int64_t col) {
+    const double2 dp = A[(int64_t)ps.x * pitch + col];
+    if (ps.y < 0) return dp;
+    return cmul(dp, __ldg(V + (int64_t)ps.y * pitch + col));
+}
+
+__global__ void __launch_bounds__(TPB) down_light_f64(DevAC ac, DownArgs a, const double2 *__restrict__ V,
+                                                       double2 *A) {
+    const int64_t ncols = a.ncols;
+    if (ncols <= 0 || a.count <= 0) return;
     const int lane = threadIdx.x & 31;
     const int64_t nchunks = (ncols + 31) >> 5;
-    const int64_t nblk = (a.hi - a.lo + NB - 1) / NB;
+    const int64_t nblk = (a.count + NB - 1) / NB;
     const int64_t items = nblk * nchunks;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -406,22 +462,52 @@ __global__ void __launch_bounds__(TPB) down_level_f64(DevAC ac, LevelArgs a, con
         const int64_t blk = it / nchunks;
         const int64_t col = chunk * 32 + lane;
         if (col >= ncols) continue;
-        const uint32_t n0 = a.lo + (uint32_t)blk * NB;
-        const uint32_t n1 = min(a.hi, n0 + NB);
-        for (uint32_t n = n0; n < n1; ++n) {
+        const int64_t k1 = min(a.count, (blk + 1) * NB);
+        for (int64_t k = blk * NB; k < k1; ++k) {
+            const uint32_t n = a.nodes[k];
+            const uint32_t e1 = ac.par_off[n + 1];
+            uint32_t e = ac.par_off[n];
             double2 acc = make_double2(0.0, 0.0);
-            for (uint32_t e = ac.par_off[n]; e < ac.par_off[n + 1]; ++e) {
-                const int2 ps = ac.par[e];
-                const double2 dp = A[(int64_t)ps.x * a.pitch + col];
-                if (ps.y < 0) {
-                    acc.x += dp.x; acc.y += dp.y;
-                } else {
-                    const double2 t = cmul(dp, __ldg(V + (int64_t)ps.y * a.pitch + col));
-                    acc.x += t.x; acc.y += t.y;
-                }
+            for (; e + 4 <= e1; e += 4) {
+                const int2 p0 = ac.par[e], p1 = ac.par[e + 1], p2 = ac.par[e + 2], p3 = ac.par[e + 3];
+                const double2 t0 = down_term_f64(p0, A, V, a.pitch, col), t1 = down_term_f64(p1, A, V, a.pitch, col);
+                const double2 t2 = down_term_f64(p2, A, V, a.pitch, col), t3 = down_term_f64(p3, A, V, a.pitch, col);
+                acc.x += t0.x; acc.y += t0.y; acc.x += t1.x; acc.y += t1.y;
+                acc.x += t2.x; acc.y += t2.y; acc.x += t3.x; acc.y += t3.y;
+            }
+            for (; e < e1; ++e) {
+                const double2 t = down_term_f64(ac.par[e], A, V, a.pitch, col);
+                acc.x += t.x; acc.y += t.y;
             }
             A[(int64_t)n * a.pitch + col] = acc;
         }
+    }
+}
+
+__global__ void __launch_bounds__(TPB) down_heavy_f64(DevAC ac, DownArgs a, const double2 *__restrict__ V,
+                                                       double2 *A) {
+    __shared__ double2 part[TPB / 32][32];
+    const int64_t ncols = a.ncols;
+    const int64_t nchunks = (ncols + 31) >> 5;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t it = blockIdx.x; it < a.count * nchunks; it += gridDim.x) {
+        const int64_t chunk = it % nchunks;
+        const uint32_t n = a.nodes[it / nchunks];
+        const int64_t col = chunk * 32 + lane;
+        double2 acc = make_double2(0.0, 0.0);
+        if (col < ncols)
+            for (uint32_t e = ac.par_off[n] + w; e < ac.par_off[n + 1]; e += TPB / 32) {
+                const double2 t = down_term_f64(ac.par[e], A, V, a.pitch, col);
+                acc.x += t.x; acc.y += t.y;
+            }
+        part[w][lane] = acc;
+        __syncthreads();
+        if (w == 0 && col < ncols) {
+            double2 t = part[0][lane];
+            for (int k = 1; k < TPB / 32; ++k) { t.x += part[k][lane].x; t.y += part[k][lane].y; }
+            A[(int64_t)n * a.pitch + col] = t;
+        }
+        __syncthreads();
     }
 }
 
@@ -662,6 +748,11 @@ struct qkc_ac {
     std::vector<uint32_t> level_off;
     int64_t max_width = 0;
     int64_t n_mul_edges = 0;  // parent entries that carry a sibling (children of products)
+    // downward-pass work lists: per level, light and heavy nodes (CONST leaves left out)
+    std::vector<int64_t> light_off, heavy_off;
+    uint32_t *d_light = nullptr, *d_heavy = nullptr;
+    int64_t down_edges = 0;   // parent entries visited by the downward pass
+    int64_t down_sib = 0;     // ... of which carry a sibling (product parents)
     int64_t struct_bytes = 0;
     // device structure
     uint8_t *d_op = nullptr;
@@ -676,6 +767,7 @@ struct qkc_ac {
     void *d_pv = nullptr;     // [n_param][vec_cap]
     const double *last_angles = nullptr;  // not owned; for gradient chaining
     int64_t tile = 0;         // columns per tile (multiple of 64)
+    int64_t tile_limit = 0;   // caller's cap on the tile (0: 35% of device memory)
     void *d_V = nullptr;      // [N][tile]
     void *d_A = nullptr;      // [N][tile], allocated by the first downward pass
     bool adj_ok = false;
@@ -765,6 +857,7 @@ extern "C" void qkc_free_ac(qkc_ac *a) {
     cudaFree(a->d_par); cudaFree(a->d_node_level); cudaFree(a->d_cl_off); cudaFree(a->d_cl);
     cudaFree(a->d_ind_var); cudaFree(a->d_ind_val); cudaFree(a->d_param_angle); cudaFree(a->d_param_fn);
     cudaFree(a->d_param_coef); cudaFree(a->d_const_val);
+    cudaFree(a->d_light); cudaFree(a->d_heavy);
     delete a;
 }
 
@@ -875,6 +968,21 @@ extern "C" qkc_status qkc_load_ac(qkc_ctx *ctx, const uint8_t *bytes, uint64_t l
             par[fillp[child[e]]++] = make_int2((int)p, sib);
         }
     }
+    // downward-pass work lists (level order; CONST leaves never need an adjoint)
+    std::vector<uint32_t> light, heavy;
+    std::vector<int64_t> light_off(D + 1, 0), heavy_off(D + 1, 0);
+    int64_t down_edges = 0, down_sib = 0;
+    for (uint32_t l = 0; l < D; ++l) {
+        for (uint32_t i = lo[l]; i < lo[l + 1]; ++i) {
+            if (op[i] == OP_CONST) continue;
+            const uint32_t fo = poff[i + 1] - poff[i];
+            down_edges += fo;
+            for (uint32_t e = poff[i]; e < poff[i + 1]; ++e) down_sib += par[e].y >= 0;
+            (fo > 64 ? heavy : light).push_back(i);
+        }
+        light_off[l + 1] = (int64_t)light.size();
+        heavy_off[l + 1] = (int64_t)heavy.size();
+    }
     // child-level lists per level
     std::vector<uint32_t> cloff(D + 1, 0);
     std::vector<uint16_t> cl;
@@ -908,6 +1016,10 @@ extern "C" qkc_status qkc_load_ac(qkc_ctx *ctx, const uint8_t *bytes, uint64_t l
     a->n_const = nl - nind - n_param; a->level_off = lo;
     for (uint32_t i = nl; i < N; ++i)
         if (op[i] == OP_MUL) a->n_mul_edges += coff[i + 1] - coff[i];
+    a->light_off = light_off;
+    a->heavy_off = heavy_off;
+    a->down_edges = down_edges;
+    a->down_sib = down_sib;
     for (uint32_t l = 0; l < D; ++l) a->max_width = std::max<int64_t>(a->max_width, lo[l + 1] - lo[l]);
     qkc_status st = QKC_OK;
     int64_t &b = a->struct_bytes;
@@ -919,7 +1031,9 @@ extern "C" qkc_status qkc_load_ac(qkc_ctx *ctx, const uint8_t *bytes, uint64_t l
         (st = upload(&a->d_param_angle, p_angle.data(), n_param, b)) ||
         (st = upload(&a->d_param_fn, p_fn.data(), n_param, b)) ||
         (st = upload(&a->d_param_coef, p_coef.data(), n_param, b)) ||
-        (st = upload(&a->d_const_val, c_val.data(), c_val.size(), b))) {
+        (st = upload(&a->d_const_val, c_val.data(), c_val.size(), b)) ||
+        (st = upload(&a->d_light, light.data(), light.size(), b)) ||
+        (st = upload(&a->d_heavy, heavy.data(), heavy.size(), b))) {
         qkc_free_ac(a);
         return st;
     }
@@ -960,6 +1074,7 @@ static qkc_status ensure_tile(qkc_ac *a, int64_t cols) {
         const long long lim = std::atoll(env);
         if (lim > 0) cap = std::min<int64_t>(cap, lim);
     }
+    if (a->tile_limit > 0) cap = std::min<int64_t>(cap, a->tile_limit);
     cap = cap / 64 * 64;
     if (cap < 64) return fail(QKC_ERR_NOMEM, "qkc: AC too large for one 64-column tile");
     want = std::min(want, cap);
@@ -1014,6 +1129,14 @@ extern "C" qkc_status qkc_reserve(qkc_ac *a, int64_t max_vectors, int64_t max_co
         if ((st = ensure_tile(a, max_columns))) return st;
         if ((st = ensure_roots(a, max_columns))) return st;
     }
+    return QKC_OK;
+}
+
+extern "C" qkc_status qkc_set_tile_limit(qkc_ac *a, int64_t max_tile_columns) {
+    if (!a || max_tile_columns < 0) return fail(QKC_ERR_ARG, "qkc_set_tile_limit: bad argument");
+    if (max_tile_columns > 0 && max_tile_columns < 64)
+        return fail(QKC_ERR_ARG, "qkc_set_tile_limit: the tile holds at least 64 columns");
+    a->tile_limit = max_tile_columns;
     return QKC_OK;
 }
 
@@ -1131,18 +1254,38 @@ static qkc_status run_down(qkc_ac *a, int64_t ncols, cudaStream_t s) {
     if (a->prec == 32) {
         seed_root<float2><<<g, TPB, 0, s>>>((float2 *)a->d_A, pitch, a->root, ncols);
         for (int L = (int)a->D - 2; L >= 0; --L) {
-            LevelArgs la{a->level_off[L], a->level_off[L + 1], L, pitch, ncols, nullptr, 0};
-            const int64_t items = ((int64_t)(la.hi - la.lo + NB - 1) / NB) * ((ncols + 63) / 64);
-            down_level_f32<<<grid_for(items * 32, TPB, (int64_t)sms * 8), TPB, 0, s>>>(
-                d, la, (const float2 *)a->d_V, a->d_S, (float2 *)a->d_A);
+            const int64_t nl = a->light_off[L + 1] - a->light_off[L], nh = a->heavy_off[L + 1] - a->heavy_off[L];
+            if (nl) {
+                DownArgs da{a->d_light + a->light_off[L], nl, pitch, ncols};
+                const int64_t items = ((nl + NB - 1) / NB) * ((ncols + 63) / 64);
+                down_light_f32<<<grid_for(items * 32, TPB, (int64_t)sms * 8), TPB, 0, s>>>(
+                    d, da, (const float2 *)a->d_V, a->d_S, (float2 *)a->d_A);
+            }
+            if (nh) {
+                DownArgs da{a->d_heavy + a->heavy_off[L], nh, pitch, ncols};
+                const int64_t items = nh * ((ncols + 63) / 64);
+                down_heavy_f32<<<(unsigned)std::min<int64_t>(items, (int64_t)sms * 8), TPB, 0, s>>>(
+                    d, da, (const float2 *)a->d_V, a->d_S, (float2 *)a->d_A);
+                ++a->launches;
+            }
         }
     } else {
         seed_root<double2><<<g, TPB, 0, s>>>((double2 *)a->d_A, pitch, a->root, ncols);
         for (int L = (int)a->D - 2; L >= 0; --L) {
-            LevelArgs la{a->level_off[L], a->level_off[L + 1], L, pitch, ncols, nullptr, 0};
-            const int64_t items = ((int64_t)(la.hi - la.lo + NB - 1) / NB) * ((ncols + 31) / 32);
-            down_level_f64<<<grid_for(items * 32, TPB, (int64_t)sms * 8), TPB, 0, s>>>(
-                d, la, (const double2 *)a->d_V, (double2 *)a->d_A);
+            const int64_t nl = a->light_off[L + 1] - a->light_off[L], nh = a->heavy_off[L + 1] - a->heavy_off[L];
+            if (nl) {
+                DownArgs da{a->d_light + a->light_off[L], nl, pitch, ncols};
+                const int64_t items = ((nl + NB - 1) / NB) * ((ncols + 31) / 32);
+                down_light_f64<<<grid_for(items * 32, TPB, (int64_t)sms * 8), TPB, 0, s>>>(
+                    d, da, (const double2 *)a->d_V, (double2 *)a->d_A);
+            }
+            if (nh) {
+                DownArgs da{a->d_heavy + a->heavy_off[L], nh, pitch, ncols};
+                const int64_t items = nh * ((ncols + 31) / 32);
+                down_heavy_f64<<<(unsigned)std::min<int64_t>(items, (int64_t)sms * 8), TPB, 0, s>>>(
+                    d, da, (const double2 *)a->d_V, (double2 *)a->d_A);
+                ++a->launches;
+            }
         }
     }
     if ((st = rec_end(a, ri, s))) return st;
@@ -1380,9 +1523,11 @@ extern "C" qkc_status qkc_get_stats(qkc_ac *a, qkc_stats *o) {
                 o->down_ms += ms;
                 o->down_launches += (int64_t)(a->D - 1);
                 // per parent entry: the parent's adjoint (+ the sibling value for a product), one write per node
-                double reads = 0.0;
-                reads = (double)a->E + (double)a->n_mul_edges;
-                o->down_bytes += elem * (reads + (double)(a->N - 1)) * (double)cols[i];
+                // parent adjoint per visited parent entry, sibling value per product parent,
+                // one write per visited node (CONST leaves are not visited)
+                const double reads = (double)a->down_edges + (double)a->down_sib;
+                const double writes = (double)(a->light_off[a->D] + a->heavy_off[a->D]);
+                o->down_bytes += elem * (reads + writes) * (double)cols[i];
             }
         }
     }

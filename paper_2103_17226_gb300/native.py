@@ -63,6 +63,7 @@ def lib():
         "qkc_load_ac": [P, P, U64, I32, ctypes.POINTER(ctypes.c_void_p)],
         "qkc_get_info": [P, ctypes.POINTER(ACInfo)],
         "qkc_reserve": [P, I64, I64],
+        "qkc_set_tile_limit": [P, I64],
         "qkc_set_params": [P, P, I64, P],
         "qkc_evaluate": [P, P, P, I64, P, P],
         "qkc_marginals": [P, P, P, I64, P, P, P],
@@ -216,6 +217,11 @@ def load_ac(ctx: Context, ac_bytes: bytes, precision: int = 32) -> AC:
 
 def reserve(ac: AC, max_vectors: int, max_columns: int):
     _check(lib().qkc_reserve(ac._h, max_vectors, max_columns))
+
+
+def set_tile_limit(ac: AC, max_tile_columns: int):
+    """qkc_set_tile_limit: cap this AC's column tile (0 = default)."""
+    _check(lib().qkc_set_tile_limit(ac._h, max_tile_columns))
 
 
 def set_params(ac: AC, angles, stream=None):
