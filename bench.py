@@ -317,13 +317,18 @@ def run_ours(args):
             pass
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-        up_gbs = stats["up_bytes"] / (stats["up_ms"] * 1e6) if stats["up_ms"] > 0 else None
-        dn_gbs = stats["down_bytes"] / (stats["down_ms"] * 1e6) if stats["down_ms"] > 0 else None
-        dominant = "up_level_f32" if stats["up_ms"] >= stats["down_ms"] else "down_level_f32"
-        ach = up_gbs if dominant == "up_level_f32" else dn_gbs
-        per_launch_bytes = (stats["up_bytes"] / max(1, stats["up_launches"])) if dominant == "up_level_f32" else \
-            (stats["down_bytes"] / max(1, stats["down_launches"]))
-        edge_evals = (info["n_edges"] * (stats["up_columns"] + stats["down_columns"]))
+        def gbs(kind):
+            return stats[kind + "_bytes"] / (stats[kind + "_ms"] * 1e6) if stats[kind + "_ms"] > 0 else None
+
+        names = {"up": "up_level_f32 (upward pass)", "down": "down_light_f32/down_heavy_f32 (downward pass)",
+                 "memo": "memoA_level/memoB_level_f32 (memoised sampling pass)"}
+        dom = max(("up", "down", "memo"), key=lambda k: stats[k + "_ms"])
+        ach = gbs(dom)
+        launches_dom = max(1, stats.get(dom + "_passes", 1))
+        per_launch_bytes = stats[dom + "_bytes"] / launches_dom
+        up_gbs, dn_gbs, memo_gbs = gbs("up"), gbs("down"), gbs("memo")
+        # edge evaluations the per-column method would do for the same queries
+        edge_evals = info["n_edges"] * (stats["up_columns"] + stats["down_columns"] + stats["memo_columns"])
         line = {
             "metric": W["metric"], "value": value, "unit": W["unit"], "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -334,10 +339,11 @@ def run_ours(args):
                        "precision": "complex FP32 nodes, power-of-two scale per (level, column); FP64 decisions",
                        "l2": "inputs larger than L2: node buffer = nodes x tile columns x 8 B "
                              f"({info['n_nodes'] * info['reserved_columns'] * 8 / 1e9:.1f} GB)"},
-            "roofline": {"bound": "hbm", "kernel": dominant, "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": ach, "peak": hbm, "unit": "GB/s",
                          "frac": (ach / hbm) if ach else None, "peak_source": peak_src,
-                         "bytes_per_launch": per_launch_bytes, "traffic": None,
-                         "up_pass_gbs": up_gbs, "down_pass_gbs": dn_gbs},
+                         "bytes_per_pass": per_launch_bytes, "traffic": None,
+                         "up_pass_gbs": up_gbs, "down_pass_gbs": dn_gbs, "memo_pass_gbs": memo_gbs,
+                         "time_ms": {k: stats[k + "_ms"] for k in ("up", "down", "memo")}},
             "gpu_launches": stats["launches"],
             "edge_evals_per_s": edge_evals * world / (ms_max / 1e3),
             "clocks": clk,
@@ -433,7 +439,8 @@ def run_serve(args):
     res, st = srv.run(reqs, time_limit=args.duration * 4)
     del srv
     torch.cuda.empty_cache()
-    base = Server(ctx, acs, precision=64, lanes=1, max_batch=1, max_shots=10000, tile_columns=4096, serial=True)
+    base = Server(ctx, acs, precision=64, lanes=1, max_batch=1, max_shots=10000, tile_columns=4096, serial=True,
+                  memoised=False)
     res_b, st_b = base.run(reqs, time_limit=args.duration * 4)
     print(json.dumps({"metric": "serving samples/s and p50/p99 latency", "workload": "serve_qaoa_8acs",
                       "rate_per_s": args.rate, "duration_s": args.duration, "requests": len(reqs),

@@ -235,9 +235,31 @@ qkc_status qkc_gradient(qkc_ac *ac, const int32_t *col_vec_dev, const int8_t *ev
  * Samples of one vector that share a prefix share one evaluation.
  * bits_dev [n_vectors][max_shots] uint64: outcome index of each sample
  * (entries s >= shots[v] are left untouched).  shots_dev [n_vectors] int32.
+ * total_shots: a host-side upper bound on sum_v min(shots[v], max_shots) used
+ * to size the launches (<= 0: n_vectors x max_shots); an understated bound
+ * never makes a kernel read or write out of range -- the excess samples are
+ * dropped and qkc_check_status reports it.
  */
 qkc_status qkc_sample(qkc_ac *ac, const uint64_t *seeds_dev, const int32_t *shots_dev,
-                      int64_t n_vectors, int64_t max_shots, uint64_t *bits_dev, void *stream);
+                      int64_t n_vectors, int64_t max_shots, int64_t total_shots, uint64_t *bits_dev,
+                      void *stream);
+
+/*
+ * qkc_set_sampler -- how qkc_sample evaluates its columns.  mode 1 (default):
+ * memoised -- at qubit j a node's value depends only on the vector and on the
+ * prefix bits of the qubits < j in the node's indicator support, so nodes with
+ * a small such support are evaluated once per (vector, key) instead of once
+ * per prefix group (same results).  mode 0: every node once per group.
+ */
+qkc_status qkc_set_sampler(qkc_ac *ac, int32_t mode);
+
+/*
+ * qkc_check_status -- waits for the device and reports (then clears) the AC's
+ * device-side error word: QKC_ERR_ARG if a qkc_sample call was given a
+ * total_shots below the sum of its shots (the samples beyond the bound were
+ * dropped and their entries are invalid).
+ */
+qkc_status qkc_check_status(qkc_ac *ac);
 
 /*
  * qkc_evaluate_static -- the upward pass of qkc_evaluate (same arguments, same
@@ -277,6 +299,8 @@ qkc_status qkc_evaluate_static(qkc_ac *ac, const int32_t *col_vec_dev, const int
  * upward  (E + N - leaves) x elem per column (child reads, node writes);
  * downward (E + E_mul + N - 1) x elem per column (parent adjoints, siblings of
  * products, node writes); elem = 8 (FP32 complex) or 16 (FP64 complex).
+ * A memoised sampling pass moves (children + 1) x elem per tier-A slot and per
+ * tier-B node and group column.
  */
 typedef struct {
     int64_t launches, records;
@@ -284,6 +308,8 @@ typedef struct {
     double up_ms, up_bytes;
     int64_t down_passes, down_columns, down_launches;
     double down_ms, down_bytes;
+    int64_t memo_passes, memo_columns;  /* memoised sampling passes (qkc_set_sampler mode 1) */
+    double memo_ms, memo_bytes;
 } qkc_stats;
 qkc_status qkc_stats_enable(qkc_ac *ac, int32_t enable, int64_t max_records);
 qkc_status qkc_get_stats(qkc_ac *ac, qkc_stats *out);

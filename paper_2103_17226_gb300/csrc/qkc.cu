@@ -149,6 +149,21 @@ struct EvSrc {
     int64_t n_vec;             // bound vectors; out-of-range map entries are clamped
 };
 
+// Everything that changes from one pass to the next lives in device memory, so the
+// per-level launch sequence of a pass can be captured once as a CUDA graph and replayed.
+struct PassDesc {
+    EvSrc es;
+    const void *pv;       // parameter leaf values [n_param][pv_pitch]
+    int64_t pv_pitch;
+    int64_t col0, ncols;  // first global column of this tile, columns in the tile (host bound)
+};
+__global__ void set_desc(PassDesc *dst, PassDesc v) { *dst = v; }
+__device__ __forceinline__ int64_t desc_cols(const PassDesc &d) {
+    int64_t n = d.ncols;
+    if (d.es.n_active) n = min(n, (int64_t)(*d.es.n_active) - d.col0);
+    return n;
+}
+
 __device__ __forceinline__ int64_t vec_of(const EvSrc &e, int64_t gc) {
     int64_t v = e.col_vec ? (int64_t)e.col_vec[gc] : gc;
     return v < 0 ? 0 : (v >= e.n_vec ? e.n_vec - 1 : v);
@@ -168,10 +183,11 @@ __device__ __forceinline__ double ind_value(int code, int val) {
 }
 
 // FP32 leaves; also initialises the level-0 scale (0) and observed exponent.
-__global__ void bind_leaves_f32(DevAC ac, EvSrc es, int64_t col0, int64_t ncols_host, int64_t pitch,
-                                const float2 *pv, int64_t pv_pitch, float2 *V, int *obs, int n_leaves) {
-    int64_t ncols = ncols_host;
-    if (es.n_active) ncols = min(ncols_host, (int64_t)(*es.n_active) - col0);
+__global__ void bind_leaves_f32(DevAC ac, const PassDesc *pd, int64_t pitch, float2 *V, int *obs, int n_leaves) {
+    const PassDesc d = *pd;
+    const EvSrc &es = d.es;
+    const int64_t col0 = d.col0, ncols = desc_cols(d), pv_pitch = d.pv_pitch;
+    const float2 *pv = static_cast<const float2 *>(d.pv);
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t total = (int64_t)n_leaves * pitch;
     for (; t < total; t += (int64_t)gridDim.x * blockDim.x) {
@@ -193,10 +209,11 @@ __global__ void bind_leaves_f32(DevAC ac, EvSrc es, int64_t col0, int64_t ncols_
     }
 }
 
-__global__ void bind_leaves_f64(DevAC ac, EvSrc es, int64_t col0, int64_t ncols_host, int64_t pitch,
-                                const double2 *pv, int64_t pv_pitch, double2 *V, int n_leaves) {
-    int64_t ncols = ncols_host;
-    if (es.n_active) ncols = min(ncols_host, (int64_t)(*es.n_active) - col0);
+__global__ void bind_leaves_f64(DevAC ac, const PassDesc *pd, int64_t pitch, double2 *V, int n_leaves) {
+    const PassDesc d = *pd;
+    const EvSrc &es = d.es;
+    const int64_t col0 = d.col0, ncols = desc_cols(d), pv_pitch = d.pv_pitch;
+    const double2 *pv = static_cast<const double2 *>(d.pv);
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t total = (int64_t)n_leaves * pitch;
     for (; t < total; t += (int64_t)gridDim.x * blockDim.x) {
@@ -219,7 +236,7 @@ __global__ void bind_leaves_f64(DevAC ac, EvSrc es, int64_t col0, int64_t ncols_
 // ------------------------------------------------------------------ per-level scale (FP32)
 // S[L][c] = max over the child levels L' of level L of S[L'][c] + obs[L'][c];
 // obs[L][c] reset.  Order-independent, so deterministic and per column.
-__global__ void level_scale_kernel(DevAC ac, int L, int64_t pitch, int64_t ncols, int *S, int *obs) {
+__global__ void level_scale_kernel(DevAC ac, int L, int64_t pitch, int floor_zero, int *S, int *obs) {
     int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= pitch) return;
     int s = INT_MIN;
@@ -231,9 +248,9 @@ __global__ void level_scale_kernel(DevAC ac, int L, int64_t pitch, int64_t ncols
         s = max(s, cand);
     }
     if (s == INT_MIN) s = 0;
+    if (floor_zero && s < 0) s = 0;  // the level also reads unscaled values (memoised sampling)
     S[(int64_t)L * pitch + c] = s;
     obs[(int64_t)L * pitch + c] = OBS_EMPTY;
-    (void)ncols;
 }
 
 // ------------------------------------------------------------------ upward pass, one level
@@ -241,16 +258,13 @@ struct LevelArgs {
     uint32_t lo, hi;   // node range of the level
     int L;
     int64_t pitch;     // columns per node row in the buffer
-    int64_t ncols;     // active columns of this tile (host bound)
-    const int32_t *n_active;  // device-side active count (sampling) or null
-    int64_t col0;
 };
 
 // FP32: lane holds 2 columns (one float4), warp covers 64 columns.
-__global__ void __launch_bounds__(TPB) up_level_f32(DevAC ac, LevelArgs a, float2 *__restrict__ V,
-                                                     const int *__restrict__ S, int *__restrict__ obs) {
-    int64_t ncols = a.ncols;
-    if (a.n_active) ncols = min(a.ncols, (int64_t)(*a.n_active) - a.col0);
+__global__ void __launch_bounds__(TPB) up_level_f32(DevAC ac, LevelArgs a, const PassDesc *pd,
+                                                     float2 *__restrict__ V, const int *__restrict__ S,
+                                                     int *__restrict__ obs) {
+    const int64_t ncols = desc_cols(*pd);
     if (ncols <= 0) return;
     const int lane = threadIdx.x & 31;
     const int64_t nchunks = (ncols + 63) >> 6;
@@ -308,9 +322,9 @@ __global__ void __launch_bounds__(TPB) up_level_f32(DevAC ac, LevelArgs a, float
 }
 
 // FP64: lane holds 1 column (one double2), warp covers 32 columns.  No scaling.
-__global__ void __launch_bounds__(TPB) up_level_f64(DevAC ac, LevelArgs a, double2 *__restrict__ V) {
-    int64_t ncols = a.ncols;
-    if (a.n_active) ncols = min(a.ncols, (int64_t)(*a.n_active) - a.col0);
+__global__ void __launch_bounds__(TPB) up_level_f64(DevAC ac, LevelArgs a, const PassDesc *pd,
+                                                     double2 *__restrict__ V) {
+    const int64_t ncols = desc_cols(*pd);
     if (ncols <= 0) return;
     const int lane = threadIdx.x & 31;
     const int64_t nchunks = (ncols + 31) >> 5;
@@ -371,12 +385,12 @@ __device__ __forceinline__ void acc4(float4 &a, const float4 b) { a.x += b.x; a.
 struct DownArgs {
     const uint32_t *nodes;  // node ids of this level's light (or heavy) list
     int64_t count;
-    int64_t pitch, ncols;
+    int64_t pitch;
 };
 
-__global__ void __launch_bounds__(TPB) down_light_f32(DevAC ac, DownArgs a, const float2 *__restrict__ V,
+__global__ void __launch_bounds__(TPB) down_light_f32(DevAC ac, DownArgs a, const PassDesc *pd, const float2 *__restrict__ V,
                                                        const int *__restrict__ S, float2 *A) {
-    const int64_t ncols = a.ncols;
+    const int64_t ncols = pd->ncols;
     if (ncols <= 0 || a.count <= 0) return;
     const int lane = threadIdx.x & 31;
     const int64_t nchunks = (ncols + 63) >> 6;
@@ -412,10 +426,10 @@ __global__ void __launch_bounds__(TPB) down_light_f32(DevAC ac, DownArgs a, cons
     }
 }
 
-__global__ void __launch_bounds__(TPB) down_heavy_f32(DevAC ac, DownArgs a, const float2 *__restrict__ V,
+__global__ void __launch_bounds__(TPB) down_heavy_f32(DevAC ac, DownArgs a, const PassDesc *pd, const float2 *__restrict__ V,
                                                        const int *__restrict__ S, float2 *A) {
     __shared__ float4 part[TPB / 32][32];
-    const int64_t ncols = a.ncols;
+    const int64_t ncols = pd->ncols;
     const int64_t nchunks = (ncols + 63) >> 6;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t hp = a.pitch >> 1;
@@ -447,9 +461,9 @@ __device__ __forceinline__ double2 down_term_f64(const int2 ps, const double2 *A
     return cmul(dp, __ldg(V + (int64_t)ps.y * pitch + col));
 }
 
-__global__ void __launch_bounds__(TPB) down_light_f64(DevAC ac, DownArgs a, const double2 *__restrict__ V,
+__global__ void __launch_bounds__(TPB) down_light_f64(DevAC ac, DownArgs a, const PassDesc *pd, const double2 *__restrict__ V,
                                                        double2 *A) {
-    const int64_t ncols = a.ncols;
+    const int64_t ncols = pd->ncols;
     if (ncols <= 0 || a.count <= 0) return;
     const int lane = threadIdx.x & 31;
     const int64_t nchunks = (ncols + 31) >> 5;
@@ -484,10 +498,10 @@ __global__ void __launch_bounds__(TPB) down_light_f64(DevAC ac, DownArgs a, cons
     }
 }
 
-__global__ void __launch_bounds__(TPB) down_heavy_f64(DevAC ac, DownArgs a, const double2 *__restrict__ V,
+__global__ void __launch_bounds__(TPB) down_heavy_f64(DevAC ac, DownArgs a, const PassDesc *pd, const double2 *__restrict__ V,
                                                        double2 *A) {
     __shared__ double2 part[TPB / 32][32];
-    const int64_t ncols = a.ncols;
+    const int64_t ncols = pd->ncols;
     const int64_t nchunks = (ncols + 31) >> 5;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int64_t it = blockIdx.x; it < a.count * nchunks; it += gridDim.x) {
@@ -511,6 +525,279 @@ __global__ void __launch_bounds__(TPB) down_heavy_f64(DevAC ac, DownArgs a, cons
     }
 }
 
+// ------------------------------------------------------------------ memoised sampling
+// At sampling step j a group's evidence fixes qubits < j to its prefix and qubit j to 0, so a
+// node's value depends only on the vector and on the prefix bits of the qubits < j in the
+// node's indicator support sigma(n).  With k = |sigma(n) & jmask| such bits, a node needs at
+// most V * 2^k distinct values.  Nodes with k <= t_j ("tier A") are computed once per
+// (vector, key) on a dense slot space -- slot = vector * 2^k + key, key bit i = prefix bit of
+// the i-th smallest qubit of sigma(n) & jmask -- instead of once per group; tier A is closed
+// under children (sigma(child) is a subset of sigma(parent)).  The other nodes ("tier B") are
+// computed per group as before and read tier-A children through their key.  Tier-A values are
+// unscaled; a tier-B level that reads one keeps its scale exponent at least 0.
+struct MemoDesc {
+    int64_t V;            // vectors
+    int32_t j, clamp;
+    uint64_t jmask;       // qubits < j
+    const void *pv;       // parameter leaf values
+    int64_t pv_pitch;
+    void *VA;             // tier-A values
+    const int64_t *offu;  // per node: start of its tier-A block in units (x V slots), -1 for tier B
+    const uint64_t *sigma;
+};
+__global__ void set_memo_desc(MemoDesc *dst, MemoDesc v) { *dst = v; }
+
+// bits of `key` are ranked within rn; return those of the qubits in rc (subset of rn), ranked within rc
+__device__ __forceinline__ uint32_t subkey(uint32_t key, uint64_t rn, uint64_t rc) {
+    uint32_t out = 0;
+    for (int i = 0; rc; ++i) {
+        const int q = __ffsll((long long)rc) - 1;
+        rc &= rc - 1;
+        const int pos = __popcll(rn & ((1ull << q) - 1ull));
+        out |= ((key >> pos) & 1u) << i;
+    }
+    return out;
+}
+// key of a group prefix (j bits, qubit 0 first) on the qubits of rc (all < j)
+__device__ __forceinline__ uint32_t prefix_key(uint64_t prefix, int j, uint64_t rc) {
+    uint32_t out = 0;
+    for (int i = 0; rc; ++i) {
+        const int q = __ffsll((long long)rc) - 1;
+        rc &= rc - 1;
+        out |= (uint32_t)((prefix >> (j - 1 - q)) & 1ull) << i;
+    }
+    return out;
+}
+
+template <typename C>
+__device__ __forceinline__ C memo_leaf(const DevAC &ac, const MemoDesc &md, uint32_t n, int64_t vec, uint32_t key) {
+    C r;
+    const uint8_t o = ac.op[n];
+    if (o == OP_IND) {
+        const int q = ac.ind_var[n], val = ac.ind_val[n];
+        double lam = 1.0;
+        if (q < md.j) lam = ((int)(key & 1u) == val) ? 1.0 : 0.0;
+        else if (q == md.j && md.clamp) lam = (val == 0) ? 1.0 : 0.0;
+        r.x = lam;
+        r.y = 0;
+    } else if (o == OP_PARAM) {
+        r = static_cast<const C *>(md.pv)[(int64_t)(n - ac.n_ind) * md.pv_pitch + vec];
+    } else {
+        const double2 k = ac.const_val[n - ac.n_ind - ac.n_param];
+        r.x = k.x;
+        r.y = k.y;
+    }
+    return r;
+}
+
+// One level of tier A: a thread per slot of the level's tier-A blocks.
+template <typename C>
+__global__ void __launch_bounds__(TPB) memoA_level(DevAC ac, const MemoDesc *mdp, const uint32_t *nodes,
+                                                    const int64_t *ustart, int64_t count, int64_t u0, int64_t u1) {
+    const MemoDesc md = *mdp;
+    C *VA = static_cast<C *>(md.VA);
+    const int64_t total = md.V * (u1 - u0);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t sl = md.V * u0 + t;
+        int64_t lo = 0, hi = count - 1;  // largest i with V * ustart[i] <= sl
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (md.V * ustart[mid] <= sl) lo = mid;
+            else hi = mid - 1;
+        }
+        const uint32_t n = nodes[lo];
+        const int64_t local = sl - md.V * ustart[lo];
+        const uint64_t rn = md.sigma[n] & md.jmask;
+        const int k = __popcll(rn);
+        const int64_t vec = local >> k;
+        const uint32_t key = (uint32_t)(local & ((1ll << k) - 1));
+        C r;
+        const uint8_t o = ac.op[n];
+        if (o <= OP_CONST) {
+            r = memo_leaf<C>(ac, md, n, vec, key);
+        } else {
+            const uint32_t e0 = ac.child_off[n], e1 = ac.child_off[n + 1];
+            r.x = (o == OP_MUL) ? 1 : 0;
+            r.y = 0;
+            for (uint32_t e = e0; e < e1; ++e) {
+                const uint32_t c = ac.child[e];
+                const uint64_t rc = md.sigma[c] & md.jmask;
+                const int kc = __popcll(rc);
+                const int64_t cs = (vec << kc) | (int64_t)subkey(key, rn, rc);
+                const C v = VA[md.V * md.offu[c] + cs];
+                if (o == OP_MUL) {
+                    C m;
+                    m.x = r.x * v.x - r.y * v.y;
+                    m.y = r.x * v.y + r.y * v.x;
+                    r = m;
+                } else {
+                    r.x += v.x;
+                    r.y += v.y;
+                }
+            }
+        }
+        VA[md.V * ustart[lo] + local] = r;
+    }
+}
+
+// One level of tier B (FP32): as up_level_f32 over a node list, tier-A children read by key.
+__global__ void __launch_bounds__(TPB) memoB_level_f32(DevAC ac, LevelArgs a, const uint32_t *nodes, int64_t count,
+                                                        const PassDesc *pd, const MemoDesc *mdp,
+                                                        float2 *__restrict__ V, const int *__restrict__ S,
+                                                        int *__restrict__ obs) {
+    const int64_t ncols = desc_cols(*pd);
+    if (ncols <= 0 || count <= 0) return;
+    const MemoDesc md = *mdp;
+    const float2 *VA = static_cast<const float2 *>(md.VA);
+    const EvSrc es = pd->es;
+    const int64_t col0 = pd->col0;
+    const int lane = threadIdx.x & 31;
+    const int64_t nchunks = (ncols + 63) >> 6;
+    const int64_t items = ((count + NB - 1) / NB) * nchunks;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t hp = a.pitch >> 1;
+    float4 *V4 = reinterpret_cast<float4 *>(V);
+    for (int64_t it = wid; it < items; it += nw) {
+        const int64_t chunk = it % nchunks;
+        const int64_t blk = it / nchunks;
+        const int64_t col = chunk * 64 + lane * 2;
+        if (col >= ncols) continue;
+        const bool two = col + 1 < ncols;
+        const int64_t g0 = col0 + col, g1 = two ? g0 + 1 : g0;
+        const int64_t vec0 = vec_of(es, g0), vec1 = vec_of(es, g1);
+        const uint64_t pre0 = es.prefix[g0], pre1 = es.prefix[g1];
+        const int2 sL = *reinterpret_cast<const int2 *>(S + (int64_t)a.L * a.pitch + col);
+        int m0 = -127, m1 = -127;
+        const int64_t k1 = min(count, (blk + 1) * NB);
+        // one child's two column values and scale exponents (tier A: unscaled, exponent 0)
+        auto child_vals = [&](uint32_t c, float2 &v0, float2 &v1, int &s0, int &s1) {
+            const int64_t off = md.offu[c];
+            if (off < 0) {
+                const int lc = ac.node_level[c];
+                const float4 v = __ldg(V4 + (int64_t)c * hp + (col >> 1));
+                const int2 sc = __ldg(reinterpret_cast<const int2 *>(S + (int64_t)lc * a.pitch + col));
+                v0 = make_float2(v.x, v.y);
+                v1 = make_float2(v.z, v.w);
+                s0 = sc.x;
+                s1 = sc.y;
+            } else {
+                const uint64_t rc = md.sigma[c] & md.jmask;
+                const int kc = __popcll(rc);
+                v0 = VA[md.V * off + ((vec0 << kc) | (int64_t)prefix_key(pre0, md.j, rc))];
+                v1 = VA[md.V * off + ((vec1 << kc) | (int64_t)prefix_key(pre1, md.j, rc))];
+                s0 = s1 = 0;
+            }
+        };
+        for (int64_t kk = blk * NB; kk < k1; ++kk) {
+            const uint32_t n = nodes[kk];
+            const uint8_t o = ac.op[n];
+            const uint32_t e0 = ac.child_off[n], e1 = ac.child_off[n + 1];
+            float2 r0, r1;
+            if (o == OP_MUL) {
+                float2 a0, a1, b0, b1;
+                int sa0, sa1, sb0, sb1;
+                child_vals(ac.child[e0], a0, a1, sa0, sa1);
+                child_vals(ac.child[e0 + 1], b0, b1, sb0, sb1);
+                r0 = cscale(cmul(a0, b0), pow2f(sa0 + sb0 - sL.x));
+                r1 = cscale(cmul(a1, b1), pow2f(sa1 + sb1 - sL.y));
+            } else {
+                r0 = make_float2(0.f, 0.f);
+                r1 = r0;
+                for (uint32_t e = e0; e < e1; ++e) {
+                    float2 v0, v1;
+                    int s0, s1;
+                    child_vals(ac.child[e], v0, v1, s0, s1);
+                    const float f0 = pow2f(s0 - sL.x), f1 = pow2f(s1 - sL.y);
+                    r0.x += v0.x * f0; r0.y += v0.y * f0;
+                    r1.x += v1.x * f1; r1.y += v1.y * f1;
+                }
+            }
+            V4[(int64_t)n * hp + (col >> 1)] = make_float4(r0.x, r0.y, r1.x, r1.y);
+            m0 = max(m0, exp_of(r0));
+            m1 = max(m1, exp_of(r1));
+        }
+        atomicMax(obs + (int64_t)a.L * a.pitch + col, m0);
+        if (two) atomicMax(obs + (int64_t)a.L * a.pitch + col + 1, m1);
+    }
+}
+
+// One level of tier B (FP64, unscaled).
+__global__ void __launch_bounds__(TPB) memoB_level_f64(DevAC ac, LevelArgs a, const uint32_t *nodes, int64_t count,
+                                                        const PassDesc *pd, const MemoDesc *mdp,
+                                                        double2 *__restrict__ V) {
+    const int64_t ncols = desc_cols(*pd);
+    if (ncols <= 0 || count <= 0) return;
+    const MemoDesc md = *mdp;
+    const double2 *VA = static_cast<const double2 *>(md.VA);
+    const EvSrc es = pd->es;
+    const int64_t col0 = pd->col0;
+    const int lane = threadIdx.x & 31;
+    const int64_t nchunks = (ncols + 31) >> 5;
+    const int64_t items = ((count + NB - 1) / NB) * nchunks;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t it = wid; it < items; it += nw) {
+        const int64_t chunk = it % nchunks;
+        const int64_t blk = it / nchunks;
+        const int64_t col = chunk * 32 + lane;
+        if (col >= ncols) continue;
+        const int64_t g = col0 + col;
+        const int64_t vec = vec_of(es, g);
+        const uint64_t pre = es.prefix[g];
+        const int64_t k1 = min(count, (blk + 1) * NB);
+        for (int64_t kk = blk * NB; kk < k1; ++kk) {
+            const uint32_t n = nodes[kk];
+            const uint8_t o = ac.op[n];
+            double2 r = make_double2(o == OP_MUL ? 1.0 : 0.0, 0.0);
+            for (uint32_t e = ac.child_off[n]; e < ac.child_off[n + 1]; ++e) {
+                const uint32_t c = ac.child[e];
+                const int64_t off = md.offu[c];
+                double2 v;
+                if (off < 0) {
+                    v = __ldg(V + (int64_t)c * a.pitch + col);
+                } else {
+                    const uint64_t rc = md.sigma[c] & md.jmask;
+                    v = VA[md.V * off + ((vec << __popcll(rc)) | (int64_t)prefix_key(pre, md.j, rc))];
+                }
+                if (o == OP_MUL) r = cmul(r, v);
+                else { r.x += v.x; r.y += v.y; }
+            }
+            V[(int64_t)n * a.pitch + col] = r;
+        }
+    }
+}
+
+// Root value of every active group column: from the tier-A slots or the tier-B tile.
+__global__ void memo_root(const MemoDesc *mdp, const PassDesc *pd, uint32_t root, int Lroot, const void *Vb,
+                          const int *S, int64_t pitch, int prec32, double2 *out) {
+    const int64_t ncols = desc_cols(*pd);
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    const MemoDesc md = *mdp;
+    const int64_t g = pd->col0 + c;
+    const int64_t off = md.offu[root];
+    double2 r;
+    if (off >= 0) {
+        const uint64_t rc = md.sigma[root] & md.jmask;
+        const int64_t sl = md.V * off + ((vec_of(pd->es, g) << __popcll(rc)) | (int64_t)prefix_key(pd->es.prefix[g], md.j, rc));
+        if (prec32) {
+            const float2 v = static_cast<const float2 *>(md.VA)[sl];
+            r = make_double2(v.x, v.y);
+        } else {
+            r = static_cast<const double2 *>(md.VA)[sl];
+        }
+    } else if (prec32) {
+        const float2 m = static_cast<const float2 *>(Vb)[(int64_t)root * pitch + c];
+        const int sc = S[(int64_t)Lroot * pitch + c];
+        r = make_double2(ldexp((double)m.x, sc), ldexp((double)m.y, sc));
+    } else {
+        r = static_cast<const double2 *>(Vb)[(int64_t)root * pitch + c];
+    }
+    out[g] = r;
+}
+
 // ------------------------------------------------------------------ small kernels
 // root value of every active column, in FP64 (FP32 mantissa times 2^S)
 __global__ void root_f32(const float2 *V, const int *S, int64_t pitch, uint32_t root, int Lroot, int64_t ncols,
@@ -531,9 +818,9 @@ __global__ void root_f64(const double2 *V, int64_t pitch, uint32_t root, int64_t
 }
 
 template <typename C>
-__global__ void seed_root(C *A, int64_t pitch, uint32_t root, int64_t ncols) {
+__global__ void seed_root(C *A, int64_t pitch, uint32_t root, const PassDesc *pd) {
     int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= ncols) return;
+    if (c >= pd->ncols) return;
     C one;
     one.x = 1;
     one.y = 0;
@@ -620,12 +907,16 @@ __global__ void sample_set_total(const double2 *root, int64_t n_vec, double *g_P
 // Decide bit j of every live sample; mark the child group (2g + bit).
 __global__ void sample_decide(int64_t n_vec, int64_t max_shots, const int32_t *shots, const uint64_t *seeds, int j,
                               int n_qubits, const double2 *p0v, const double *g_P, int32_t *s_group,
-                              uint64_t *s_bits, int32_t *flag) {
+                              uint64_t *s_bits, int32_t *flag, const int32_t *g_count, int32_t *status) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n_vec * max_shots) return;
     int64_t v = t / max_shots, s = t % max_shots;
     if (s >= shots[v]) return;
     int g = s_group[t];
+    if (g < 0 || g >= *g_count) {  // a sample dropped by an understated shot total
+        atomicExch(status, 1);
+        return;
+    }
     double p0 = p0v[g].x, P = g_P[g];
     uint64_t k = (uint64_t)s * (uint64_t)n_qubits + (uint64_t)j + 1ull;
     double u = (double)(splitmix64_k(seeds[v], k) >> 11) * (1.0 / 9007199254740992.0);
@@ -679,9 +970,9 @@ __global__ void scan_sums(int32_t *bsum, int64_t nb) {
 __global__ void sample_regroup(const int32_t *g_count_old, const int32_t *flag, const int32_t *pos,
                                const int32_t *bsum, const int32_t *g_vec, const uint64_t *g_prefix,
                                const double *g_P, const double2 *p0v, int32_t *g_vec_n, uint64_t *g_prefix_n,
-                               double *g_P_n, int32_t *g_count_new) {
+                               double *g_P_n, int32_t *g_count_new, int64_t nflag) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int64_t n = 2LL * (*g_count_old);
+    int64_t n = min((int64_t)(2LL * (*g_count_old)), nflag);  // only the scanned child slots
     if (k >= n) return;
     int32_t id = pos[k] + bsum[k >> 10];
     if (k == n - 1) *g_count_new = id + flag[k];
@@ -694,12 +985,18 @@ __global__ void sample_regroup(const int32_t *g_count_old, const int32_t *flag, 
     g_P_n[id] = bit ? fmax(P - p0, 0.0) : p0;
 }
 __global__ void sample_remap(int64_t n_vec, int64_t max_shots, const int32_t *shots, const int32_t *pos,
-                             const int32_t *bsum, int32_t *s_group, const uint64_t *s_bits) {
+                             const int32_t *bsum, int32_t *s_group, const uint64_t *s_bits, int64_t nflag,
+                             int32_t *status) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n_vec * max_shots) return;
     int64_t v = t / max_shots, s = t % max_shots;
-    if (s >= shots[v]) return;
+    if (s >= shots[v] || s_group[t] < 0) return;
     int64_t k = 2LL * s_group[t] + (int64_t)(s_bits[t] & 1ull);
+    if (k >= nflag) {  // beyond the host bound (understated shot total): drop the sample
+        s_group[t] = -1;
+        atomicExch(status, 1);
+        return;
+    }
     s_group[t] = pos[k] + bsum[k >> 10];
 }
 __global__ void sample_write(int64_t n_vec, int64_t max_shots, const int32_t *shots, const uint64_t *s_bits,
@@ -782,11 +1079,34 @@ struct qkc_ac {
     uint64_t *d_g_prefix[2] = {nullptr, nullptr};
     double *d_g_P[2] = {nullptr, nullptr};
 
+    PassDesc *d_desc = nullptr;  // the pass descriptor the level kernels read
+    // memoised sampling: indicator support of every node, per-cap step metadata, tier-A slots
+    std::vector<uint64_t> sigma;
+    std::vector<uint32_t> h_child_off, h_child;  // host copy of the structure (density ACs)
+    uint64_t *d_sigma = nullptr;
+    MemoDesc *d_mdesc = nullptr;
+    struct MemoMeta {
+        int cap = 0;
+        int64_t max_units = 0;
+        std::vector<std::vector<int64_t>> a_lvl, u_lvl, b_lvl;  // per step, [D + 1]
+        std::vector<std::vector<uint8_t>> floor0;               // per step, [D]
+        std::vector<int64_t> a_base, b_base, offu_base;          // per step
+        std::vector<double> a_bytes_slot, b_bytes_col;           // per step: algorithmic bytes per slot unit / column
+        uint32_t *d_a_nodes = nullptr, *d_b_nodes = nullptr;
+        int64_t *d_a_ustart = nullptr, *d_offu = nullptr;
+    };
+    std::vector<MemoMeta *> memo;  // indexed by cap
+    void *d_VA = nullptr;
+    int64_t va_bytes = 0;
+    int sampler = 1;  // 1: memoised, 0: one column per group for every node
+    int32_t *d_status = nullptr; // device-side error word (sampling input checks)
+    struct GraphSlot { cudaGraphExec_t exec = nullptr; const void *V = nullptr, *A = nullptr; int64_t pitch = 0; };
+    GraphSlot g_up, g_down;
     // stats: launches of this library's kernels, and (when enabled) CUDA events around
     // every chain of level kernels with the number of columns it processed
     int64_t launches = 0;
     bool timing = false;
-    struct Rec { cudaEvent_t e0, e1; int kind; };  // kind 0 upward, 1 downward
+    struct Rec { cudaEvent_t e0, e1; int kind; double fixed_bytes, col_bytes; };  // kind 0 up, 1 down, 2 memo
     std::vector<Rec> recs;
     int64_t *d_statcols = nullptr;
     int64_t statcap = 0;
@@ -852,6 +1172,18 @@ extern "C" void qkc_free_ac(qkc_ac *a) {
     cudaDeviceSynchronize();
     drop_records(a);
     cudaFree(a->d_statcols);
+    if (a->g_up.exec) cudaGraphExecDestroy(a->g_up.exec);
+    if (a->g_down.exec) cudaGraphExecDestroy(a->g_down.exec);
+    cudaFree(a->d_desc);
+    cudaFree(a->d_status);
+    cudaFree(a->d_sigma);
+    cudaFree(a->d_mdesc);
+    cudaFree(a->d_VA);
+    for (auto *m : a->memo) {
+        if (!m) continue;
+        cudaFree(m->d_a_nodes); cudaFree(m->d_b_nodes); cudaFree(m->d_a_ustart); cudaFree(m->d_offu);
+        delete m;
+    }
     free_scratch(a);
     cudaFree(a->d_op); cudaFree(a->d_child_off); cudaFree(a->d_child); cudaFree(a->d_par_off);
     cudaFree(a->d_par); cudaFree(a->d_node_level); cudaFree(a->d_cl_off); cudaFree(a->d_cl);
@@ -978,7 +1310,7 @@ extern "C" qkc_status qkc_load_ac(qkc_ctx *ctx, const uint8_t *bytes, uint64_t l
             const uint32_t fo = poff[i + 1] - poff[i];
             down_edges += fo;
             for (uint32_t e = poff[i]; e < poff[i + 1]; ++e) down_sib += par[e].y >= 0;
-            (fo > 64 ? heavy : light).push_back(i);
+            (fo > (uint32_t)HEAVY ? heavy : light).push_back(i);
         }
         light_off[l + 1] = (int64_t)light.size();
         heavy_off[l + 1] = (int64_t)heavy.size();
@@ -1036,6 +1368,26 @@ extern "C" qkc_status qkc_load_ac(qkc_ctx *ctx, const uint8_t *bytes, uint64_t l
         (st = upload(&a->d_heavy, heavy.data(), heavy.size(), b))) {
         qkc_free_ac(a);
         return st;
+    }
+    if (kind == QKC_AC_DENSITY) {  // indicator support of every node (sampling memoisation)
+        a->sigma.assign(N, 0ull);
+        for (uint32_t i = 0; i < nind; ++i) a->sigma[i] = 1ull << (uint32_t)ind_var[i];
+        for (uint32_t i = nl; i < N; ++i)
+            for (uint32_t e = coff[i]; e < coff[i + 1]; ++e) a->sigma[i] |= a->sigma[child[e]];
+        a->h_child_off = coff;
+        a->h_child = child;
+        if ((st = upload(&a->d_sigma, a->sigma.data(), N, b))) {
+            qkc_free_ac(a);
+            return st;
+        }
+    }
+    if (cudaMalloc((void **)&a->d_mdesc, sizeof(MemoDesc)) != cudaSuccess ||
+        cudaMalloc((void **)&a->d_desc, sizeof(PassDesc)) != cudaSuccess ||
+        cudaMalloc((void **)&a->d_status, sizeof(int32_t)) != cudaSuccess ||
+        cudaMemset(a->d_status, 0, sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        qkc_free_ac(a);
+        return fail(QKC_ERR_NOMEM, "qkc_load_ac: cannot allocate the pass descriptor");
     }
     *out = a;
     return QKC_OK;
@@ -1171,6 +1523,8 @@ static qkc_status rec_begin(qkc_ac *a, int kind, const int32_t *n_active, int64_
     if ((int64_t)a->recs.size() >= a->statcap) return QKC_OK;  // record buffer full: stop recording
     qkc_ac::Rec r;
     r.kind = kind;
+    r.fixed_bytes = 0.0;
+    r.col_bytes = 0.0;
     QKC_CUDA(cudaEventCreate(&r.e0));
     QKC_CUDA(cudaEventCreate(&r.e1));
     stat_record<<<1, 1, 0, s>>>(n_active, col0, ncols, a->d_statcols + a->recs.size());
@@ -1185,48 +1539,127 @@ static qkc_status rec_end(qkc_ac *a, size_t idx, cudaStream_t s) {
     return QKC_OK;
 }
 
-static qkc_status run_up(qkc_ac *a, const EvSrc &es, int64_t col0, int64_t ncols, cudaStream_t s) {
+// The launches of one upward pass over a tile of `pitch` columns (levels 0 .. D-1). Every
+// kernel reads the pass descriptor a->d_desc, and grids are sized for a full tile, so the
+// same sequence serves any column count: it is captured once as a CUDA graph and replayed.
+static void launch_up_sequence(qkc_ac *a, cudaStream_t s, void *V, int *S, int *obs, int64_t pitch) {
+    const DevAC d = a->dev();
+    const int sms = a->ctx->sm_count;
+    const PassDesc *pd = a->d_desc;
+    const unsigned gs = (unsigned)((pitch + TPB - 1) / TPB);
+    if (a->prec == 32) {
+        // level 0: leaves (S[0] = 0 and obs[0] reset by the scale kernel, then observed)
+        level_scale_kernel<<<gs, TPB, 0, s>>>(d, 0, pitch, 0, S, obs);
+        bind_leaves_f32<<<grid_for((int64_t)a->n_leaves * pitch), TPB, 0, s>>>(d, pd, pitch, (float2 *)V, obs,
+                                                                              (int)a->n_leaves);
+        for (uint32_t L = 1; L < a->D; ++L) {
+            level_scale_kernel<<<gs, TPB, 0, s>>>(d, (int)L, pitch, 0, S, obs);
+            LevelArgs la{a->level_off[L], a->level_off[L + 1], (int)L, pitch};
+            const int64_t items = ((int64_t)(la.hi - la.lo + NB - 1) / NB) * ((pitch + 63) / 64);
+            up_level_f32<<<grid_for(items * 32, TPB, (int64_t)sms * 8), TPB, 0, s>>>(d, la, pd, (float2 *)V, S, obs);
+        }
+    } else {
+        bind_leaves_f64<<<grid_for((int64_t)a->n_leaves * pitch), TPB, 0, s>>>(d, pd, pitch, (double2 *)V,
+                                                                              (int)a->n_leaves);
+        for (uint32_t L = 1; L < a->D; ++L) {
+            LevelArgs la{a->level_off[L], a->level_off[L + 1], (int)L, pitch};
+            const int64_t items = ((int64_t)(la.hi - la.lo + NB - 1) / NB) * ((pitch + 31) / 32);
+            up_level_f64<<<grid_for(items * 32, TPB, (int64_t)sms * 8), TPB, 0, s>>>(d, la, pd, (double2 *)V);
+        }
+    }
+}
+static int64_t up_sequence_launches(const qkc_ac *a) {
+    return a->prec == 32 ? 2 + 2 * (int64_t)(a->D - 1) : 1 + (int64_t)(a->D - 1);
+}
+
+// The launches of one downward pass over the current tile (levels D-1 .. 0).
+static void launch_down_sequence(qkc_ac *a, cudaStream_t s) {
     const int64_t pitch = a->tile;
     const DevAC d = a->dev();
     const int sms = a->ctx->sm_count;
-    qkc_status st;
-    if (a->prec == 32) {
-        // level 0: leaves (S[0] = 0 and obs[0] reset by the scale kernel, then observed)
-        level_scale_kernel<<<(unsigned)((pitch + TPB - 1) / TPB), TPB, 0, s>>>(d, 0, pitch, ncols, a->d_S, a->d_obs);
-        bind_leaves_f32<<<grid_for((int64_t)a->n_leaves * pitch), TPB, 0, s>>>(
-            d, es, col0, ncols, pitch, (const float2 *)a->d_pv, a->vec_cap, (float2 *)a->d_V, a->d_obs,
-            (int)a->n_leaves);
-        QKC_LAUNCH_CHECK();
-        a->launches += 2;
-        const size_t ri = a->recs.size();
-        if ((st = rec_begin(a, 0, es.n_active, col0, ncols, s))) return st;
-        for (uint32_t L = 1; L < a->D; ++L) {
-            level_scale_kernel<<<(unsigned)((pitch + TPB - 1) / TPB), TPB, 0, s>>>(d, (int)L, pitch, ncols, a->d_S,
-                                                                                   a->d_obs);
-            LevelArgs la{a->level_off[L], a->level_off[L + 1], (int)L, pitch, ncols, es.n_active, col0};
-            const int64_t items = ((int64_t)(la.hi - la.lo + NB - 1) / NB) * ((ncols + 63) / 64);
-            up_level_f32<<<grid_for(items * 32, TPB, (int64_t)sms * 8), TPB, 0, s>>>(d, la, (float2 *)a->d_V, a->d_S,
-                                                                                    a->d_obs);
+    const PassDesc *pd = a->d_desc;
+    const unsigned g = (unsigned)((pitch + TPB - 1) / TPB);
+    const int64_t cw = a->prec == 32 ? 64 : 32;  // columns per warp chunk
+    if (a->prec == 32) seed_root<float2><<<g, TPB, 0, s>>>((float2 *)a->d_A, pitch, a->root, pd);
+    else seed_root<double2><<<g, TPB, 0, s>>>((double2 *)a->d_A, pitch, a->root, pd);
+    for (int L = (int)a->D - 2; L >= 0; --L) {
+        const int64_t nl = a->light_off[L + 1] - a->light_off[L], nh = a->heavy_off[L + 1] - a->heavy_off[L];
+        if (nl) {
+            DownArgs da{a->d_light + a->light_off[L], nl, pitch};
+            const int64_t items = ((nl + NB - 1) / NB) * ((pitch + cw - 1) / cw);
+            const unsigned gl = grid_for(items * 32, TPB, (int64_t)sms * 8);
+            if (a->prec == 32)
+                down_light_f32<<<gl, TPB, 0, s>>>(d, da, pd, (const float2 *)a->d_V, a->d_S, (float2 *)a->d_A);
+            else
+                down_light_f64<<<gl, TPB, 0, s>>>(d, da, pd, (const double2 *)a->d_V, (double2 *)a->d_A);
         }
-        a->launches += 2 * (int64_t)(a->D - 1);
-        if ((st = rec_end(a, ri, s))) return st;
-        QKC_LAUNCH_CHECK();
-    } else {
-        bind_leaves_f64<<<grid_for((int64_t)a->n_leaves * pitch), TPB, 0, s>>>(
-            d, es, col0, ncols, pitch, (const double2 *)a->d_pv, a->vec_cap, (double2 *)a->d_V, (int)a->n_leaves);
-        QKC_LAUNCH_CHECK();
-        a->launches += 1;
-        const size_t ri = a->recs.size();
-        if ((st = rec_begin(a, 0, es.n_active, col0, ncols, s))) return st;
-        for (uint32_t L = 1; L < a->D; ++L) {
-            LevelArgs la{a->level_off[L], a->level_off[L + 1], (int)L, pitch, ncols, es.n_active, col0};
-            const int64_t items = ((int64_t)(la.hi - la.lo + NB - 1) / NB) * ((ncols + 31) / 32);
-            up_level_f64<<<grid_for(items * 32, TPB, (int64_t)sms * 8), TPB, 0, s>>>(d, la, (double2 *)a->d_V);
+        if (nh) {
+            DownArgs da{a->d_heavy + a->heavy_off[L], nh, pitch};
+            const unsigned gh = (unsigned)std::min<int64_t>(nh * ((pitch + cw - 1) / cw), (int64_t)sms * 8);
+            if (a->prec == 32)
+                down_heavy_f32<<<gh, TPB, 0, s>>>(d, da, pd, (const float2 *)a->d_V, a->d_S, (float2 *)a->d_A);
+            else
+                down_heavy_f64<<<gh, TPB, 0, s>>>(d, da, pd, (const double2 *)a->d_V, (double2 *)a->d_A);
         }
-        a->launches += (int64_t)(a->D - 1);
-        if ((st = rec_end(a, ri, s))) return st;
-        QKC_LAUNCH_CHECK();
     }
+}
+static int64_t down_sequence_launches(const qkc_ac *a) {
+    int64_t n = 1;
+    for (int L = (int)a->D - 2; L >= 0; --L)
+        n += (a->light_off[L + 1] > a->light_off[L]) + (a->heavy_off[L + 1] > a->heavy_off[L]);
+    return n;
+}
+
+// Capture (or reuse) the graph of one pass kind; rebuilt when the tile buffers move.
+static qkc_status pass_graph(qkc_ac *a, bool down, cudaGraphExec_t *out) {
+    qkc_ac::GraphSlot &g = down ? a->g_down : a->g_up;
+    if (g.exec && g.V == a->d_V && g.A == a->d_A && g.pitch == a->tile) {
+        *out = g.exec;
+        return QKC_OK;
+    }
+    if (g.exec) {
+        cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+    }
+    cudaStream_t cs;
+    QKC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        if (down) launch_down_sequence(a, cs);
+        else launch_up_sequence(a, cs, a->d_V, a->d_S, a->d_obs, a->tile);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) {
+            e = cudaGraphInstantiate(&g.exec, graph, 0);
+            cudaGraphDestroy(graph);
+        }
+    }
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        g.exec = nullptr;
+        return fail(QKC_ERR_CUDA, "qkc: capturing the %s-pass graph failed: %s", down ? "downward" : "upward",
+                    cudaGetErrorString(e));
+    }
+    g.V = a->d_V;
+    g.A = a->d_A;
+    g.pitch = a->tile;
+    *out = g.exec;
+    return QKC_OK;
+}
+
+static qkc_status run_up(qkc_ac *a, const EvSrc &es, int64_t col0, int64_t ncols, cudaStream_t s) {
+    qkc_status st;
+    cudaGraphExec_t exec;
+    if ((st = pass_graph(a, false, &exec))) return st;
+    PassDesc desc{es, a->d_pv, a->vec_cap, col0, ncols};
+    set_desc<<<1, 1, 0, s>>>(a->d_desc, desc);
+    ++a->launches;
+    QKC_LAUNCH_CHECK();
+    const size_t ri = a->recs.size();
+    if ((st = rec_begin(a, 0, es.n_active, col0, ncols, s))) return st;
+    QKC_CUDA(cudaGraphLaunch(exec, s));
+    a->launches += up_sequence_launches(a);
+    if ((st = rec_end(a, ri, s))) return st;
     return QKC_OK;
 }
 
@@ -1243,53 +1676,18 @@ static qkc_status run_roots(qkc_ac *a, int64_t col0, int64_t ncols, const int32_
 }
 
 static qkc_status run_down(qkc_ac *a, int64_t ncols, cudaStream_t s) {
-    const int64_t pitch = a->tile;
-    const DevAC d = a->dev();
-    const int sms = a->ctx->sm_count;
-    const unsigned g = (unsigned)((ncols + TPB - 1) / TPB);
     qkc_status st;
+    cudaGraphExec_t exec;
+    if ((st = pass_graph(a, true, &exec))) return st;
+    PassDesc desc{EvSrc{nullptr, nullptr, 0, 0, nullptr, nullptr, 1}, a->d_pv, a->vec_cap, 0, ncols};
+    set_desc<<<1, 1, 0, s>>>(a->d_desc, desc);
+    ++a->launches;
+    QKC_LAUNCH_CHECK();
     const size_t ri = a->recs.size();
     if ((st = rec_begin(a, 1, nullptr, 0, ncols, s))) return st;
-    a->launches += (int64_t)a->D;
-    if (a->prec == 32) {
-        seed_root<float2><<<g, TPB, 0, s>>>((float2 *)a->d_A, pitch, a->root, ncols);
-        for (int L = (int)a->D - 2; L >= 0; --L) {
-            const int64_t nl = a->light_off[L + 1] - a->light_off[L], nh = a->heavy_off[L + 1] - a->heavy_off[L];
-            if (nl) {
-                DownArgs da{a->d_light + a->light_off[L], nl, pitch, ncols};
-                const int64_t items = ((nl + NB - 1) / NB) * ((ncols + 63) / 64);
-                down_light_f32<<<grid_for(items * 32, TPB, (int64_t)sms * 8), TPB, 0, s>>>(
-                    d, da, (const float2 *)a->d_V, a->d_S, (float2 *)a->d_A);
-            }
-            if (nh) {
-                DownArgs da{a->d_heavy + a->heavy_off[L], nh, pitch, ncols};
-                const int64_t items = nh * ((ncols + 63) / 64);
-                down_heavy_f32<<<(unsigned)std::min<int64_t>(items, (int64_t)sms * 8), TPB, 0, s>>>(
-                    d, da, (const float2 *)a->d_V, a->d_S, (float2 *)a->d_A);
-                ++a->launches;
-            }
-        }
-    } else {
-        seed_root<double2><<<g, TPB, 0, s>>>((double2 *)a->d_A, pitch, a->root, ncols);
-        for (int L = (int)a->D - 2; L >= 0; --L) {
-            const int64_t nl = a->light_off[L + 1] - a->light_off[L], nh = a->heavy_off[L + 1] - a->heavy_off[L];
-            if (nl) {
-                DownArgs da{a->d_light + a->light_off[L], nl, pitch, ncols};
-                const int64_t items = ((nl + NB - 1) / NB) * ((ncols + 31) / 32);
-                down_light_f64<<<grid_for(items * 32, TPB, (int64_t)sms * 8), TPB, 0, s>>>(
-                    d, da, (const double2 *)a->d_V, (double2 *)a->d_A);
-            }
-            if (nh) {
-                DownArgs da{a->d_heavy + a->heavy_off[L], nh, pitch, ncols};
-                const int64_t items = nh * ((ncols + 31) / 32);
-                down_heavy_f64<<<(unsigned)std::min<int64_t>(items, (int64_t)sms * 8), TPB, 0, s>>>(
-                    d, da, (const double2 *)a->d_V, (double2 *)a->d_A);
-                ++a->launches;
-            }
-        }
-    }
+    QKC_CUDA(cudaGraphLaunch(exec, s));
+    a->launches += down_sequence_launches(a);
     if ((st = rec_end(a, ri, s))) return st;
-    QKC_LAUNCH_CHECK();
     return QKC_OK;
 }
 
@@ -1414,8 +1812,152 @@ static qkc_status ensure_sampling(qkc_ac *a, int64_t n_samples, int64_t n_groups
     return QKC_OK;
 }
 
+
+// ---- memoised sampling (host side)
+static const qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
+    *st = QKC_OK;
+    if ((int)a->memo.size() <= cap) a->memo.resize(cap + 1, nullptr);
+    if (a->memo[cap]) return a->memo[cap];
+    auto *m = new qkc_ac::MemoMeta;
+    m->cap = cap;
+    const int nq = (int)a->n_qubits;
+    const uint32_t N = a->N, D = a->D;
+    std::vector<uint32_t> an, bn;
+    std::vector<int64_t> au, offu;
+    const std::vector<uint32_t> &child_off = a->h_child_off, &child = a->h_child;
+    m->a_lvl.assign(nq, std::vector<int64_t>(D + 1, 0));
+    m->u_lvl = m->a_lvl;
+    m->b_lvl = m->a_lvl;
+    m->floor0.assign(nq, std::vector<uint8_t>(D, 0));
+    for (int j = 0; j < nq; ++j) {
+        const uint64_t jmask = j == 0 ? 0ull : (j >= 64 ? ~0ull : ((1ull << j) - 1ull));
+        const int t = std::min(cap, j);
+        m->a_base.push_back((int64_t)an.size());
+        m->b_base.push_back((int64_t)bn.size());
+        m->offu_base.push_back((int64_t)offu.size());
+        const size_t ob = offu.size();
+        offu.resize(ob + N, -1);
+        int64_t units = 0;
+        double abytes = 0.0, bbytes = 0.0;
+        for (uint32_t L = 0; L < D; ++L) {
+            for (uint32_t n = a->level_off[L]; n < a->level_off[L + 1]; ++n) {
+                const int k = __builtin_popcountll(a->sigma[n] & jmask);
+                const double deg = (double)(child_off[n + 1] - child_off[n]);
+                if (k <= t) {
+                    offu[ob + n] = units;
+                    an.push_back(n);
+                    au.push_back(units);
+                    units += 1ll << k;
+                    abytes += (double)(1ll << k) * (deg + 1.0);
+                } else {
+                    bn.push_back(n);
+                    bbytes += deg + 1.0;
+                    for (uint32_t e = child_off[n]; e < child_off[n + 1]; ++e)
+                        if (offu[ob + child[e]] >= 0) m->floor0[j][L] = 1;
+                }
+            }
+            m->a_lvl[j][L + 1] = (int64_t)an.size() - m->a_base[j];
+            m->u_lvl[j][L + 1] = units;
+            m->b_lvl[j][L + 1] = (int64_t)bn.size() - m->b_base[j];
+        }
+        m->a_bytes_slot.push_back(abytes * (double)a->elem());
+        m->b_bytes_col.push_back(bbytes * (double)a->elem());
+        m->max_units = std::max(m->max_units, units);
+    }
+    int64_t dummy = 0;
+    if ((*st = upload(&m->d_a_nodes, an.data(), an.size(), dummy)) ||
+        (*st = upload(&m->d_a_ustart, au.data(), au.size(), dummy)) ||
+        (*st = upload(&m->d_b_nodes, bn.data(), bn.size(), dummy)) ||
+        (*st = upload(&m->d_offu, offu.data(), offu.size(), dummy))) {
+        cudaFree(m->d_a_nodes); cudaFree(m->d_a_ustart); cudaFree(m->d_b_nodes); cudaFree(m->d_offu);
+        delete m;
+        return nullptr;
+    }
+    a->memo[cap] = m;
+    return m;
+}
+
+// One memoised upward pass of step j over `bound` group columns (device count n_active).
+static qkc_status memo_pass(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, int clamp, int64_t n_vec,
+                            const int32_t *n_active, int64_t bound, int cur, cudaStream_t s) {
+    const DevAC d = a->dev();
+    const int sms = a->ctx->sm_count;
+    const uint32_t D = a->D;
+    const uint64_t jmask = j == 0 ? 0ull : (j >= 64 ? ~0ull : ((1ull << j) - 1ull));
+    MemoDesc md{n_vec, j, clamp, jmask, a->d_pv, a->vec_cap, a->d_VA, m->d_offu + m->offu_base[j], a->d_sigma};
+    set_memo_desc<<<1, 1, 0, s>>>(a->d_mdesc, md);
+    ++a->launches;
+    qkc_status st;
+    const size_t ri = a->recs.size();
+    if ((st = rec_begin(a, 2, n_active, 0, bound, s))) return st;
+    if (ri < a->recs.size()) {
+        a->recs[ri].fixed_bytes = (double)n_vec * m->a_bytes_slot[j];
+        a->recs[ri].col_bytes = m->b_bytes_col[j];
+    }
+    // tier A, level by level (no tiles: V * 2^k slots per node)
+    for (uint32_t L = 0; L < D; ++L) {
+        const int64_t i0 = m->a_lvl[j][L], i1 = m->a_lvl[j][L + 1];
+        if (i1 == i0) continue;
+        const int64_t u0 = m->u_lvl[j][L], u1 = m->u_lvl[j][L + 1];
+        const unsigned g = grid_for(n_vec * (u1 - u0), TPB, (int64_t)sms * 16);
+        const uint32_t *nodes = m->d_a_nodes + m->a_base[j] + i0;
+        const int64_t *us = m->d_a_ustart + m->a_base[j] + i0;
+        if (a->prec == 32) memoA_level<float2><<<g, TPB, 0, s>>>(d, a->d_mdesc, nodes, us, i1 - i0, u0, u1);
+        else memoA_level<double2><<<g, TPB, 0, s>>>(d, a->d_mdesc, nodes, us, i1 - i0, u0, u1);
+        ++a->launches;
+    }
+    // tier B per tile of groups, then the roots
+    const int64_t pitch = a->tile;
+    const bool anyB = m->b_lvl[j][D] > 0;
+    for (int64_t c0 = 0; c0 < bound; c0 += pitch) {
+        const int64_t nc = std::min<int64_t>(pitch, bound - c0);
+        EvSrc es{nullptr, a->d_g_prefix[cur], j, clamp, a->d_g_vec[cur], n_active, std::max<int64_t>(1, n_vec)};
+        PassDesc desc{es, a->d_pv, a->vec_cap, c0, nc};
+        set_desc<<<1, 1, 0, s>>>(a->d_desc, desc);
+        ++a->launches;
+        if (anyB) {
+            const unsigned gs = (unsigned)((pitch + TPB - 1) / TPB);
+            if (a->prec == 32) {
+                level_scale_kernel<<<gs, TPB, 0, s>>>(d, 0, pitch, 0, a->d_S, a->d_obs);
+                ++a->launches;
+            }
+            for (uint32_t L = 1; L < D; ++L) {
+                const int64_t b0 = m->b_lvl[j][L], b1 = m->b_lvl[j][L + 1];
+                if (a->prec == 32) {
+                    level_scale_kernel<<<gs, TPB, 0, s>>>(d, (int)L, pitch, m->floor0[j][L], a->d_S, a->d_obs);
+                    ++a->launches;
+                }
+                if (b1 == b0) continue;
+                LevelArgs la{0, 0, (int)L, pitch};
+                const uint32_t *nodes = m->d_b_nodes + m->b_base[j] + b0;
+                const int64_t cw = a->prec == 32 ? 64 : 32;
+                const int64_t items = ((b1 - b0 + NB - 1) / NB) * ((nc + cw - 1) / cw);
+                const unsigned g = grid_for(items * 32, TPB, (int64_t)sms * 8);
+                if (a->prec == 32)
+                    memoB_level_f32<<<g, TPB, 0, s>>>(d, la, nodes, b1 - b0, a->d_desc, a->d_mdesc, (float2 *)a->d_V,
+                                                       a->d_S, a->d_obs);
+                else
+                    memoB_level_f64<<<g, TPB, 0, s>>>(d, la, nodes, b1 - b0, a->d_desc, a->d_mdesc, (double2 *)a->d_V);
+                ++a->launches;
+            }
+        }
+        memo_root<<<(unsigned)((nc + TPB - 1) / TPB), TPB, 0, s>>>(a->d_mdesc, a->d_desc, a->root, (int)D - 1, a->d_V,
+                                                                   a->d_S, pitch, a->prec == 32, a->d_root);
+        ++a->launches;
+    }
+    if ((st = rec_end(a, ri, s))) return st;
+    QKC_LAUNCH_CHECK();
+    return QKC_OK;
+}
+
+extern "C" qkc_status qkc_set_sampler(qkc_ac *a, int32_t mode) {
+    if (!a || (mode != 0 && mode != 1)) return fail(QKC_ERR_ARG, "qkc_set_sampler: mode must be 0 or 1");
+    a->sampler = mode;
+    return QKC_OK;
+}
+
 extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t *shots, int64_t n_vec,
-                                 int64_t max_shots, uint64_t *bits, void *stream) {
+                                 int64_t max_shots, int64_t total_shots, uint64_t *bits, void *stream) {
     if (!a || !seeds || !shots || !bits || n_vec <= 0 || max_shots < 0)
         return fail(QKC_ERR_ARG, "qkc_sample: bad argument");
     if (a->kind != QKC_AC_DENSITY) return fail(QKC_ERR_UNSUPPORTED, "qkc_sample: needs a DENSITY AC");
@@ -1425,18 +1967,52 @@ extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t
     QKC_CUDA(cudaSetDevice(a->ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n_samp = n_vec * max_shots;
+    // host bound on the live samples, hence on the groups of every step
+    const int64_t live = (total_shots > 0 && total_shots < n_samp) ? total_shots : n_samp;
     const int nq = (int)a->n_qubits;
     qkc_status st;
     if ((st = ensure_sampling(a, n_samp, std::max(n_samp, n_vec)))) return st;
     // tile sized for the largest step (bounded by the sample count), roots for every group
     if ((st = ensure_tile(a, std::max(n_samp, n_vec))) || (st = ensure_roots(a, std::max(n_samp, n_vec)))) return st;
+    // memoised passes: the largest cap (bits per node key) whose tier-A slots fit the budget
+    const qkc_ac::MemoMeta *meta = nullptr;
+    if (a->sampler == 1 && nq <= 63) {
+        int ks = 0;
+        while (ks < 24 && (2ll << ks) <= max_shots) ++ks;  // floor(log2(max_shots))
+        const double budget = 0.15 * (double)a->ctx->total_mem;
+        for (int cap = ks; cap >= 1 && !meta; --cap) {
+            const qkc_ac::MemoMeta *m = memo_meta(a, cap, &st);
+            if (st) return st;
+            if ((double)n_vec * (double)m->max_units * (double)a->elem() <= budget) meta = m;
+        }
+        if (meta) {
+            const int64_t need = n_vec * meta->max_units * (int64_t)a->elem();
+            if (need > a->va_bytes) {
+                QKC_CUDA(cudaDeviceSynchronize());
+                cudaFree(a->d_VA);
+                a->d_VA = nullptr;
+                a->va_bytes = 0;
+                if (cudaMalloc(&a->d_VA, (size_t)std::max<int64_t>(need, 256)) != cudaSuccess) {
+                    cudaGetLastError();
+                    return fail(QKC_ERR_NOMEM, "qkc_sample: cannot allocate %lld bytes of memoised slots",
+                                (long long)need);
+                }
+                a->va_bytes = need;
+            }
+        }
+    }
     const unsigned gs = (unsigned)((n_samp + TPB - 1) / TPB);
     sample_init<<<std::max(gs, (unsigned)((n_vec + TPB - 1) / TPB)), TPB, 0, s>>>(
         n_vec, max_shots, shots, a->d_s_group, a->d_s_bits, a->d_g_vec[0], a->d_g_prefix[0], a->d_gcount);
     QKC_LAUNCH_CHECK();
     int cur = 0;
     // P(empty prefix) for every vector: all indicators free
-    {
+    if (meta) {
+        if ((st = memo_pass(a, meta, 0, 0, n_vec, nullptr, n_vec, cur, s))) return st;
+        sample_set_total<<<(unsigned)((n_vec + TPB - 1) / TPB), TPB, 0, s>>>(a->d_root, n_vec, a->d_g_P[cur]);
+        a->launches += 2;
+        QKC_LAUNCH_CHECK();
+    } else {
         for (int64_t c0 = 0; c0 < n_vec; c0 += a->tile) {
             const int64_t nc = std::min<int64_t>(a->tile, n_vec - c0);
             EvSrc es{nullptr, a->d_g_prefix[cur], 0, 0, a->d_g_vec[cur], nullptr, std::max<int64_t>(1, a->n_vec)};
@@ -1451,32 +2027,50 @@ extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t
     for (int j = 0; j < nq; ++j) {
         // p0 = P(prefix, X_j = 0) for every group (count on the device, bound on the host)
         int32_t *gcount = a->d_gcount + cur;
-        for (int64_t c0 = 0; c0 < bound; c0 += a->tile) {
-            const int64_t nc = std::min<int64_t>(a->tile, bound - c0);
-            EvSrc es{nullptr, a->d_g_prefix[cur], j, 1, a->d_g_vec[cur], gcount, std::max<int64_t>(1, a->n_vec)};
-            if ((st = run_up(a, es, c0, nc, s))) return st;
-            if ((st = run_roots(a, c0, nc, gcount, s))) return st;
+        if (meta) {
+            if ((st = memo_pass(a, meta, j, 1, n_vec, gcount, bound, cur, s))) return st;
+        } else {
+            for (int64_t c0 = 0; c0 < bound; c0 += a->tile) {
+                const int64_t nc = std::min<int64_t>(a->tile, bound - c0);
+                EvSrc es{nullptr, a->d_g_prefix[cur], j, 1, a->d_g_vec[cur], gcount, std::max<int64_t>(1, a->n_vec)};
+                if ((st = run_up(a, es, c0, nc, s))) return st;
+                if ((st = run_roots(a, c0, nc, gcount, s))) return st;
+            }
         }
         const int64_t nflag = 2 * bound;
         QKC_CUDA(cudaMemsetAsync(a->d_flag, 0, sizeof(int32_t) * nflag, s));
         sample_decide<<<gs, TPB, 0, s>>>(n_vec, max_shots, shots, seeds, j, nq, a->d_root, a->d_g_P[cur],
-                                         a->d_s_group, a->d_s_bits, a->d_flag);
+                                         a->d_s_group, a->d_s_bits, a->d_flag, gcount, a->d_status);
         const int64_t nb = (nflag + 1023) / 1024;
         scan_block<<<(unsigned)nb, 1024, 0, s>>>(a->d_flag, gcount, 2, a->d_pos, a->d_bsum);
         scan_sums<<<1, 1024, 0, s>>>(a->d_bsum, nb);
         const int nxt = cur ^ 1;
         sample_regroup<<<(unsigned)((nflag + TPB - 1) / TPB), TPB, 0, s>>>(
             gcount, a->d_flag, a->d_pos, a->d_bsum, a->d_g_vec[cur], a->d_g_prefix[cur], a->d_g_P[cur], a->d_root,
-            a->d_g_vec[nxt], a->d_g_prefix[nxt], a->d_g_P[nxt], a->d_gcount + nxt);
-        sample_remap<<<gs, TPB, 0, s>>>(n_vec, max_shots, shots, a->d_pos, a->d_bsum, a->d_s_group, a->d_s_bits);
+            a->d_g_vec[nxt], a->d_g_prefix[nxt], a->d_g_P[nxt], a->d_gcount + nxt, nflag);
+        sample_remap<<<gs, TPB, 0, s>>>(n_vec, max_shots, shots, a->d_pos, a->d_bsum, a->d_s_group, a->d_s_bits,
+                                        nflag, a->d_status);
         a->launches += 5;
         QKC_LAUNCH_CHECK();
         cur = nxt;
-        bound = std::min<int64_t>(2 * bound, n_samp);
+        bound = std::min<int64_t>(2 * bound, live);
     }
     sample_write<<<gs, TPB, 0, s>>>(n_vec, max_shots, shots, a->d_s_bits, bits);
     ++a->launches;
     QKC_LAUNCH_CHECK();
+    return QKC_OK;
+}
+
+extern "C" qkc_status qkc_check_status(qkc_ac *a) {
+    if (!a) return fail(QKC_ERR_ARG, "qkc_check_status: null AC");
+    QKC_CUDA(cudaSetDevice(a->ctx->device));
+    int32_t v = 0;
+    QKC_CUDA(cudaMemcpy(&v, a->d_status, sizeof v, cudaMemcpyDeviceToHost));
+    if (v) {
+        QKC_CUDA(cudaMemset(a->d_status, 0, sizeof(int32_t)));
+        return fail(QKC_ERR_ARG, "qkc_check_status: a qkc_sample call was given total_shots below the sum of its "
+                                 "shots; samples beyond it were dropped");
+    }
     return QKC_OK;
 }
 
@@ -1510,7 +2104,12 @@ extern "C" qkc_status qkc_get_stats(qkc_ac *a, qkc_stats *o) {
             float ms = 0.f;
             QKC_CUDA(cudaEventSynchronize(a->recs[i].e1));
             QKC_CUDA(cudaEventElapsedTime(&ms, a->recs[i].e0, a->recs[i].e1));
-            if (a->recs[i].kind == 0) {
+            if (a->recs[i].kind == 2) {  // memoised sampling pass: tier-A slots + tier-B columns
+                o->memo_passes += 1;
+                o->memo_columns += cols[i];
+                o->memo_ms += ms;
+                o->memo_bytes += a->recs[i].fixed_bytes + a->recs[i].col_bytes * (double)cols[i];
+            } else if (a->recs[i].kind == 0) {
                 o->up_passes += 1;
                 o->up_columns += cols[i];
                 o->up_ms += ms;
@@ -1588,38 +2187,21 @@ extern "C" qkc_status qkc_evaluate_static(qkc_ac *a, const int32_t *col_vec, con
     int *S = reinterpret_cast<int *>(p + (size_t)a->N * tile * a->elem());
     int *obs = S + (size_t)a->D * tile;
     cudaStream_t s = (cudaStream_t)stream;
-    const DevAC d = a->dev();
-    const int sms = a->ctx->sm_count;
     double2 *o = reinterpret_cast<double2 *>(out);
     // Every scratch word a tile reads is written earlier in the same tile (leaves, then each
     // level's scale words, then its values), so nothing left from a previous call is used.
     for (int64_t c0 = 0; c0 < n_cols; c0 += tile) {
         const int64_t nc = std::min<int64_t>(tile, n_cols - c0);
         EvSrc es{ev, nullptr, 0, 0, col_vec, nullptr, std::max<int64_t>(1, a->n_vec)};
+        PassDesc desc{es, a->d_pv, a->vec_cap, c0, nc};
+        set_desc<<<1, 1, 0, s>>>(a->d_desc, desc);
+        launch_up_sequence(a, s, V, S, obs, tile);
         const unsigned gr = (unsigned)((nc + TPB - 1) / TPB);
-        if (a->prec == 32) {
-            level_scale_kernel<<<(unsigned)((tile + TPB - 1) / TPB), TPB, 0, s>>>(d, 0, tile, nc, S, obs);
-            bind_leaves_f32<<<grid_for((int64_t)a->n_leaves * tile), TPB, 0, s>>>(
-                d, es, c0, nc, tile, (const float2 *)a->d_pv, a->vec_cap, (float2 *)V, obs, (int)a->n_leaves);
-            for (uint32_t L = 1; L < a->D; ++L) {
-                level_scale_kernel<<<(unsigned)((tile + TPB - 1) / TPB), TPB, 0, s>>>(d, (int)L, tile, nc, S, obs);
-                LevelArgs la{a->level_off[L], a->level_off[L + 1], (int)L, tile, nc, nullptr, c0};
-                const int64_t items = ((int64_t)(la.hi - la.lo + NB - 1) / NB) * ((nc + 63) / 64);
-                up_level_f32<<<grid_for(items * 32, TPB, (int64_t)sms * 8), TPB, 0, s>>>(d, la, (float2 *)V, S, obs);
-            }
+        if (a->prec == 32)
             root_f32<<<gr, TPB, 0, s>>>((const float2 *)V, S, tile, a->root, (int)a->D - 1, nc, nullptr, c0, o);
-            a->launches += 3 + 2 * (int64_t)(a->D - 1);
-        } else {
-            bind_leaves_f64<<<grid_for((int64_t)a->n_leaves * tile), TPB, 0, s>>>(
-                d, es, c0, nc, tile, (const double2 *)a->d_pv, a->vec_cap, (double2 *)V, (int)a->n_leaves);
-            for (uint32_t L = 1; L < a->D; ++L) {
-                LevelArgs la{a->level_off[L], a->level_off[L + 1], (int)L, tile, nc, nullptr, c0};
-                const int64_t items = ((int64_t)(la.hi - la.lo + NB - 1) / NB) * ((nc + 31) / 32);
-                up_level_f64<<<grid_for(items * 32, TPB, (int64_t)sms * 8), TPB, 0, s>>>(d, la, (double2 *)V);
-            }
+        else
             root_f64<<<gr, TPB, 0, s>>>((const double2 *)V, tile, a->root, nc, nullptr, c0, o);
-            a->launches += 2 + (int64_t)(a->D - 1);
-        }
+        a->launches += 2 + up_sequence_launches(a);
         QKC_LAUNCH_CHECK();
     }
     return QKC_OK;

@@ -43,7 +43,9 @@ class Stats(ctypes.Structure):
                 ("up_passes", ctypes.c_int64), ("up_columns", ctypes.c_int64), ("up_launches", ctypes.c_int64),
                 ("up_ms", ctypes.c_double), ("up_bytes", ctypes.c_double),
                 ("down_passes", ctypes.c_int64), ("down_columns", ctypes.c_int64), ("down_launches", ctypes.c_int64),
-                ("down_ms", ctypes.c_double), ("down_bytes", ctypes.c_double)]
+                ("down_ms", ctypes.c_double), ("down_bytes", ctypes.c_double),
+                ("memo_passes", ctypes.c_int64), ("memo_columns", ctypes.c_int64),
+                ("memo_ms", ctypes.c_double), ("memo_bytes", ctypes.c_double)]
 
 
 def lib():
@@ -68,7 +70,9 @@ def lib():
         "qkc_evaluate": [P, P, P, I64, P, P],
         "qkc_marginals": [P, P, P, I64, P, P, P],
         "qkc_gradient": [P, P, P, P, I64, I64, P, P, P],
-        "qkc_sample": [P, P, P, I64, I64, P, P],
+        "qkc_sample": [P, P, P, I64, I64, I64, P, P],
+        "qkc_check_status": [P],
+        "qkc_set_sampler": [P, I32],
         "qkc_evaluate_static": [P, P, P, I64, P, P],
         "qkc_stats_enable": [P, I32, I64],
         "qkc_get_stats": [P, ctypes.POINTER(Stats)],
@@ -280,14 +284,26 @@ def gradient(ac: AC, col_vec, evidence, weight, n_vectors: int, stream=None):
     return value, grad[:, :ac.n_angles]
 
 
-def sample(ac: AC, seeds, shots, max_shots: int, out=None, stream=None):
-    """Chain-rule samples: uint64 outcome indices [n_vectors][max_shots] (int64 tensor view)."""
+def sample(ac: AC, seeds, shots, max_shots: int, out=None, stream=None, total_shots: int = 0):
+    """Chain-rule samples: uint64 outcome indices [n_vectors][max_shots] (int64 tensor view).
+    total_shots: host-known sum of the shots (0: n_vectors x max_shots), sizes the launches."""
     import torch
     n_vec = seeds.shape[0]
     if out is None:
         out = torch.zeros((n_vec, max_shots), dtype=torch.int64, device=seeds.device)
-    _check(lib().qkc_sample(ac._h, _ptr(seeds), _ptr(shots), n_vec, max_shots, _ptr(out), _stream(stream)))
+    _check(lib().qkc_sample(ac._h, _ptr(seeds), _ptr(shots), n_vec, max_shots, int(total_shots), _ptr(out),
+                            _stream(stream)))
     return out
+
+
+def set_sampler(ac: AC, mode: int):
+    """qkc_set_sampler: 1 memoised (default), 0 one column per prefix group for every node."""
+    _check(lib().qkc_set_sampler(ac._h, mode))
+
+
+def check_status(ac: AC):
+    """qkc_check_status: raise if an earlier sampling call dropped samples (synchronises)."""
+    _check(lib().qkc_check_status(ac._h))
 
 
 def stats_enable(ac: AC, enable: bool = True, max_records: int = 1 << 16):

@@ -19,7 +19,8 @@ on the host:
     its latency from arrival to completion.
 
 The one-request-at-a-time FP64 baseline is the same loop with precision 64,
-one lane, batches of one request and at most one batch in flight.
+one lane, batches of one request, at most one batch in flight and the plain
+sampler (every node evaluated once per prefix group).
 
 A request's samples depend only on its AC, angles, seed and shot count: every
 column of a batch is computed on its own (per-column scale words included), so
@@ -80,7 +81,7 @@ class _Lane:
 class Server:
     def __init__(self, ctx: N.Context, ac_bytes: dict, precision: int = 32, lanes: int = 2, max_batch: int = 32,
                  max_shots: int = 10000, tile_columns: int = 16384, budget_samples: int = 4_000_000,
-                 serial: bool = False):
+                 serial: bool = False, memoised: bool = True):
         self.max_batch = max_batch
         self.max_shots = max_shots
         self.budget = budget_samples
@@ -93,6 +94,7 @@ class Server:
             for _ in range(lanes):
                 ac = N.load_ac(ctx, b, precision=precision)
                 N.set_tile_limit(ac, tile_columns)
+                N.set_sampler(ac, 1 if memoised else 0)
                 na = max(1, ac.n_angles)
                 self.n_angles[name] = ac.n_angles
                 ln = _Lane(
@@ -135,7 +137,7 @@ class Server:
             ln.d_shots[:B].copy_(ln.h_shots[:B], non_blocking=True)
             N.set_params(ln.ac, ln.d_angles[:B], stream=ln.stream)
             N.sample(ln.ac, ln.d_seeds[:B], ln.d_shots[:B], S, out=ln.d_bits[:B].view(-1)[:B * S].view(B, S),
-                     stream=ln.stream)
+                     stream=ln.stream, total_shots=sum(r.shots for r in reqs))
             ln.h_bits[:B].view(-1)[:B * S].copy_(ln.d_bits[:B].view(-1)[:B * S], non_blocking=True)
             ln.event = torch.cuda.Event()
             ln.event.record(ln.stream)

@@ -423,3 +423,59 @@ def test_qaoa10_p2_amplitude_ac_full_batch(cuda_ctx):
         psi = Q.statevector(c, angs[cv[k]], evr[k])
         want = psi[tuple(evx[k])]
         assert abs(complex(*out[k]) - want) < 1e-5
+
+
+def test_sample_total_shots_bound_exact_and_understated(cuda_ctx):
+    """total_shots sizes the launches: the exact sum gives the same samples as no hint; an
+    understated one drops samples without any out-of-range access and is reported."""
+    c = I.random_circuit(7, 28, seed=905, noise_prob=0.4)  # up to 6 x 64 prefix groups: above the bound below
+    V = 6
+    angs = I.uniform_angles(V, c.n_angles, seed=9)
+    seeds = t(I.vector_seeds(V, 9).astype(np.int64))
+    shots = np.array([5, 300, 17, 0, 250, 64], dtype=np.int32)
+    ac = N().load_ac(cuda_ctx, N().compile(c, 1), precision=32)
+    N().set_params(ac, t(angs))
+    a = N().sample(ac, seeds, t(shots), 300).cpu().numpy()
+    b = N().sample(ac, seeds, t(shots), 300, total_shots=int(shots.sum())).cpu().numpy()
+    for v in range(V):
+        assert np.array_equal(a[v, :shots[v]], b[v, :shots[v]])
+    N().check_status(ac)
+    N().sample(ac, seeds, t(shots), 300, total_shots=40)
+    with pytest.raises(N().QKCError) as e:
+        N().check_status(ac)
+    assert e.value.status == 1
+    N().check_status(ac)  # cleared
+    again = N().sample(ac, seeds, t(shots), 300, total_shots=int(shots.sum())).cpu().numpy()
+    for v in range(V):
+        assert np.array_equal(a[v, :shots[v]], again[v, :shots[v]])
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("name", ["qaoa4_ring_p1", "random6", "qaoa32_3reg_p1_ideal"])
+def test_memoised_sampler_equals_per_group_sampler(cuda_ctx, prec, name):
+    """The memoised sampler evaluates a node once per (vector, prefix bits on its support) and
+    must give exactly the samples of the plain sampler (one column per prefix group)."""
+    if name == "random6":
+        c = I.random_circuit(6, 24, seed=901, noise_prob=0.4)
+        b = N().compile(c, 1)
+    else:
+        c = I.workload(name)
+        b = compiled(name)
+    V, S = (5, 700) if c.n_qubits < 32 else (4, 400)
+    angs = I.uniform_angles(V, c.n_angles, seed=17)
+    seeds = t(I.vector_seeds(V, 17).astype(np.int64))
+    shots = t(np.array([S, S // 3, 1, S - 7, 64][:V], dtype=np.int32))
+    outs = []
+    for mode in (0, 1):
+        ac = N().load_ac(cuda_ctx, b, precision=prec)
+        N().set_sampler(ac, mode)
+        N().set_params(ac, t(angs))
+        outs.append(N().sample(ac, seeds, shots, S).cpu().numpy())
+        N().check_status(ac)
+    sh = shots.cpu().numpy()
+    for v in range(V):
+        assert np.array_equal(outs[0][v, :sh[v]], outs[1][v, :sh[v]]), v
+    if c.n_qubits <= 6:
+        for v in range(V):
+            ref = Q.chain_rule_samples(Q.probabilities(c, angs[v]), int(I.vector_seeds(V, 17)[v]), int(sh[v]))
+            assert (outs[1][v, :sh[v]].astype(np.uint64) != ref).sum() <= (0 if prec == 64 else 2)
