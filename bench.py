@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["qaoa32", "hea16", "serve"], default="qaoa32")
+    ap.add_argument("--workload", choices=["qaoa32", "hea16", "serve", "gibbs_kl"], default="qaoa32")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: Poisson arrivals per second")
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
     ap.add_argument("--shots", type=int, default=10000)
@@ -193,6 +193,23 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- multi-rank aggregation
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The slowest rank's figure (timing is the max over ranks; no data-path collective)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_step: int, world: int, steps: int, seconds: float) -> float:
+    """Weak scaling: every rank processes its own units; the job rate is all units over the max time."""
+    return units_per_step * world * steps / seconds
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -262,12 +279,9 @@ def run_ours(args):
     clk = clocks.stop()
     stats = N.get_stats(ac)
     N.stats_enable(ac, False, 0)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, dev)
     units_per_step = V * S if S else n_cols
-    value = units_per_step * world * args.steps / (ms_max / 1e3)
+    value = whole_job_rate(units_per_step, world, args.steps, ms_max / 1e3)
 
     # ---- end to end through the public API: pinned host inputs in, results out, every step
     h_angles = [torch.tensor(a).pin_memory() for a in angle_sets]
@@ -303,10 +317,7 @@ def run_ours(args):
         e2e_step(k)
     barrier()
     e2e_s = time.perf_counter() - t0
-    t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = units_per_step * world * args.steps / float(t.item())
+    e2e_value = whole_job_rate(units_per_step, world, args.steps, max_over_ranks(e2e_s, world, dev))
 
     if rank == 0:
         peaks = {}
@@ -448,8 +459,68 @@ def run_serve(args):
                       "ac_nodes": {k: N.header(b)["n_nodes"] for k, b in acs.items()}}), flush=True)
 
 
+def run_gibbs_kl(args):
+    """Sampling error vs number of samples (the paper's Sec. 3.3.3 evaluation): KL divergence
+    of the empirical distribution from the exact one, for the exact chain-rule sampler on the
+    density AC and for the Gibbs chain on the amplitude AC; an 8-qubit noisy QAOA (symmetric
+    depolarising 0.5% after every gate) and a 16-qubit noise-free QAOA."""
+    import torch
+    from paper_2103_17226_gb300.build import build_library
+    build_library()
+    from paper_2103_17226_gb300 import inputs as I, native as N
+    ctx = N.Context(0)
+    out = {}
+    cases = {"qaoa8_noisy": I.qaoa_maxcut(8, I.random_regular_graph(8, 3, seed=8), 1, [("DEP1", 0.005, "all")]),
+             "qaoa16_ideal": I.qaoa_maxcut(16, I.random_regular_graph(16, 3, seed=16), 1, None)}
+    for name, c in cases.items():
+        n = c.n_qubits
+        ang = I.uniform_angles(1, c.n_angles, seed=31)
+        den = N.load_ac(ctx, N.compile(c, N.QKC_AC_DENSITY), precision=64)
+        N.set_params(den, torch.tensor(ang, device="cuda"))
+        ev = torch.tensor([[(x >> (n - 1 - q)) & 1 for q in range(n)] for x in range(2 ** n)], dtype=torch.int8,
+                          device="cuda")
+        P = N.evaluate(den, torch.zeros(2 ** n, dtype=torch.int32, device="cuda"), ev)[:, 0].cpu().numpy()
+        P = np.clip(P, 0, None)
+        P /= P.sum()
+
+        def kl(samples):
+            cnt = np.bincount(samples.astype(np.int64), minlength=2 ** n).astype(float)
+            q = cnt / cnt.sum()
+            m = q > 0
+            return float(np.sum(q[m] * np.log(q[m] / P[m])))
+
+        Ns = [100, 1000, 10000, 100000]
+        exact = N.sample(den, torch.tensor([12345], dtype=torch.int64, device="cuda"),
+                         torch.tensor([Ns[-1]], dtype=torch.int32, device="cuda"), Ns[-1])[0].cpu().numpy()
+        amp = N.load_ac(ctx, N.compile(c, N.QKC_AC_AMPLITUDE), precision=32)
+        N.set_params(amp, torch.tensor(ang, device="cuda"))
+        chains, burn = 1000, 20
+        n_rv = amp.n_vars - n
+        # start: every noise variable at its first (no-error) value, outputs at the most likely noise-free one
+        x0 = int(np.argmax(P))
+        st = np.zeros((chains, amp.n_vars), dtype=np.int8)
+        st[:, :n] = [(x0 >> (n - 1 - q)) & 1 for q in range(n)]
+        state = torch.tensor(st, device="cuda")
+        cv = torch.zeros(chains, dtype=torch.int32, device="cuda")
+        seeds = torch.tensor(I.vector_seeds(chains, 77).astype(np.int64), device="cuda")
+        t0 = time.perf_counter()
+        N.gibbs(amp, cv, seeds, state, burn)
+        sweeps = Ns[-1] // chains
+        g = N.gibbs(amp, cv, seeds, state, sweeps, sweep_offset=burn).cpu().numpy()
+        t_gibbs = time.perf_counter() - t0
+        gs = g.T.reshape(-1)  # sweep-major: the first N samples use every chain
+        out[name] = {"qubits": n, "noise_variables": n_rv,
+                     "kl_exact": {str(k): kl(exact[:k]) for k in Ns},
+                     "kl_gibbs": {str(k): kl(gs[:k]) for k in Ns},
+                     "gibbs": {"chains": chains, "burn_in_sweeps": burn, "seconds": t_gibbs}}
+    print(json.dumps({"metric": "KL(empirical || exact) vs samples", **out}), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "gibbs_kl":
+        run_gibbs_kl(args)
+        return
     if args.workload == "serve":
         run_serve(args)
         return

@@ -245,13 +245,38 @@ qkc_status qkc_sample(qkc_ac *ac, const uint64_t *seeds_dev, const int32_t *shot
                       void *stream);
 
 /*
+ * qkc_gibbs -- the paper's Markov-chain sampler (Sec. 3.3.2) on an AMPLITUDE AC:
+ * chains over full assignments of the indicator variables (outputs and noise
+ * variables) whose stationary distribution is proportional to |A(x, r)|^2, so
+ * the output marginal is the noisy outcome distribution.  One update of
+ * variable V is an upward and a downward pass at the chain's assignment: the
+ * adjoint of lambda_{V=v} is the amplitude of the assignment with V set to v
+ * (the polynomial is multilinear), and V is redrawn with probability
+ * |A|^2 / sum |A|^2.  Systematic scan over the variables in index order,
+ * n_sweeps sweeps per call.  Chain c uses the parameter vector col_vec_dev[c]
+ * and, for the update of variable V in sweep t (counting from sweep_offset),
+ * the uniform (SplitMix64_k(seeds_dev[c]) >> 11) 2^-53 with
+ * k = t * n_vars + V + 1; the new value is the smallest v with
+ * u * sum_w |A_w|^2 < sum_{w <= v} |A_w|^2, in FP64.
+ * state_dev [n_chains][n_vars] int8: in, an assignment with nonzero amplitude;
+ * out, the last one.  samples_dev [n_chains][n_sweeps] uint64 (nullable): the
+ * outcome index after every sweep.  Variables may have at most 16 values.
+ */
+qkc_status qkc_gibbs(qkc_ac *ac, const int32_t *col_vec_dev, const uint64_t *seeds_dev, int64_t n_chains,
+                     int8_t *state_dev, int64_t n_sweeps, int64_t sweep_offset, uint64_t *samples_dev,
+                     void *stream);
+
+/*
  * qkc_set_sampler -- how qkc_sample evaluates its columns.  mode 1 (default):
  * memoised -- at qubit j a node's value depends only on the vector and on the
  * prefix bits of the qubits < j in the node's indicator support, so nodes with
  * a small such support are evaluated once per (vector, key) instead of once
  * per prefix group (same results).  mode 0: every node once per group.
+ * memo_budget_bytes caps the device memory of the memoised values (0: 15% of
+ * the device memory and at most half of what is free); the sampler picks the
+ * largest key width that fits and falls back to mode 0 when none does.
  */
-qkc_status qkc_set_sampler(qkc_ac *ac, int32_t mode);
+qkc_status qkc_set_sampler(qkc_ac *ac, int32_t mode, int64_t memo_budget_bytes);
 
 /*
  * qkc_check_status -- waits for the device and reports (then clears) the AC's

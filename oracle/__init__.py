@@ -14,6 +14,8 @@ Modules
               gradients (forward mode), chain-rule sampling.  Ground truth.
   bn       -- the paper's Bayesian-network semantics (Sec. 3.1) evaluated by
               brute force over every assignment of every BN variable.
+  gibbs    -- the paper's Gibbs sampler (Sec. 3.3.2) with every candidate amplitude
+              recomputed by a pure-state run.
   acref    -- ctypes binding of acref.c, a plain FP64 evaluator of compiled
               ACs (upward and downward pass, gradient, chain-rule sampler),
               the timed CPU baseline.

@@ -597,15 +597,29 @@ __global__ void __launch_bounds__(TPB) memoA_level(DevAC ac, const MemoDesc *mdp
     const MemoDesc md = *mdp;
     C *VA = static_cast<C *>(md.VA);
     const int64_t total = md.V * (u1 - u0);
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t sl = md.V * u0 + t;
-        int64_t lo = 0, hi = count - 1;  // largest i with V * ustart[i] <= sl
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if (md.V * ustart[mid] <= sl) lo = mid;
-            else hi = mid - 1;
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = wid * 32; base < total; base += nw * 32) {
+        // one binary search per warp (largest i with V * ustart[i] <= first slot), then each lane
+        // steps over the few node boundaries inside the warp's 32 slots
+        int64_t lo0 = 0;
+        if (lane == 0) {
+            const int64_t sl0 = md.V * u0 + base;
+            int64_t l = 0, h = count - 1;
+            while (l < h) {
+                const int64_t mid = (l + h + 1) >> 1;
+                if (md.V * ustart[mid] <= sl0) l = mid;
+                else h = mid - 1;
+            }
+            lo0 = l;
         }
+        lo0 = __shfl_sync(0xffffffffu, lo0, 0);
+        const int64_t t = base + lane;
+        if (t >= total) continue;
+        const int64_t sl = md.V * u0 + t;
+        int64_t lo = lo0;
+        while (lo + 1 < count && md.V * ustart[lo + 1] <= sl) ++lo;
         const uint32_t n = nodes[lo];
         const int64_t local = sl - md.V * ustart[lo];
         const uint64_t rn = md.sigma[n] & md.jmask;
@@ -796,6 +810,49 @@ __global__ void memo_root(const MemoDesc *mdp, const PassDesc *pd, uint32_t root
         r = static_cast<const double2 *>(Vb)[(int64_t)root * pitch + c];
     }
     out[g] = r;
+}
+
+// ------------------------------------------------------------------ Gibbs sampling (amplitude AC)
+// Redraw variable `var` of every chain from |A(state with var = v)|^2, where the amplitudes are
+// the adjoints of the indicator leaves of `var` after an upward and a downward pass at the
+// chain's full assignment.  Decision in FP64: the smallest v with u * W < W_0 + ... + W_v.
+template <typename C>
+__global__ void gibbs_choose(const C *A, int64_t pitch, int64_t col0, int64_t ncols, int var, int card,
+                             int ind0, int n_vars, const uint64_t *seeds, uint64_t k, int8_t *state) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    const int64_t g = col0 + c;
+    double w[16];
+    double tot = 0.0;
+    for (int v = 0; v < card; ++v) {
+        const C a = A[(int64_t)(ind0 + v) * pitch + c];
+        w[v] = (double)a.x * (double)a.x + (double)a.y * (double)a.y;
+        tot += w[v];
+    }
+    if (!(tot > 0.0)) return;  // keep the current value (no neighbour has weight)
+    uint64_t z = seeds[g] + k * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    const double target = u * tot;
+    double acc = 0.0;
+    int pick = card - 1;
+    for (int v = 0; v < card; ++v) {
+        acc += w[v];
+        if (target < acc) { pick = v; break; }
+    }
+    state[g * n_vars + var] = (int8_t)pick;
+}
+
+// outcome index of every chain (output variables are the qubits 0 .. n_qubits-1)
+__global__ void gibbs_record(const int8_t *state, int64_t n_chains, int n_vars, int n_qubits, int64_t n_sweeps,
+                             int64_t sweep, uint64_t *samples) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= n_chains) return;
+    uint64_t x = 0;
+    for (int q = 0; q < n_qubits; ++q) x = (x << 1) | (uint64_t)(state[c * n_vars + q] & 1);
+    samples[c * n_sweeps + sweep] = x;
 }
 
 // ------------------------------------------------------------------ small kernels
@@ -1082,9 +1139,11 @@ struct qkc_ac {
     PassDesc *d_desc = nullptr;  // the pass descriptor the level kernels read
     // memoised sampling: indicator support of every node, per-cap step metadata, tier-A slots
     std::vector<uint64_t> sigma;
+    std::vector<uint32_t> var_card;               // cardinality of every indicator variable
     std::vector<uint32_t> h_child_off, h_child;  // host copy of the structure (density ACs)
     uint64_t *d_sigma = nullptr;
     MemoDesc *d_mdesc = nullptr;
+    struct GraphSlot { cudaGraphExec_t exec = nullptr; const void *V = nullptr, *A = nullptr; int64_t pitch = 0; };
     struct MemoMeta {
         int cap = 0;
         int64_t max_units = 0;
@@ -1094,13 +1153,14 @@ struct qkc_ac {
         std::vector<double> a_bytes_slot, b_bytes_col;           // per step: algorithmic bytes per slot unit / column
         uint32_t *d_a_nodes = nullptr, *d_b_nodes = nullptr;
         int64_t *d_a_ustart = nullptr, *d_offu = nullptr;
+        std::vector<GraphSlot> gA, gB;  // captured launch sequences per step
     };
     std::vector<MemoMeta *> memo;  // indexed by cap
     void *d_VA = nullptr;
     int64_t va_bytes = 0;
     int sampler = 1;  // 1: memoised, 0: one column per group for every node
+    int64_t memo_budget = 0;  // bytes for memoised slots (0: automatic)
     int32_t *d_status = nullptr; // device-side error word (sampling input checks)
-    struct GraphSlot { cudaGraphExec_t exec = nullptr; const void *V = nullptr, *A = nullptr; int64_t pitch = 0; };
     GraphSlot g_up, g_down;
     // stats: launches of this library's kernels, and (when enabled) CUDA events around
     // every chain of level kernels with the number of columns it processed
@@ -1182,6 +1242,8 @@ extern "C" void qkc_free_ac(qkc_ac *a) {
     for (auto *m : a->memo) {
         if (!m) continue;
         cudaFree(m->d_a_nodes); cudaFree(m->d_b_nodes); cudaFree(m->d_a_ustart); cudaFree(m->d_offu);
+        for (auto &g : m->gA) if (g.exec) cudaGraphExecDestroy(g.exec);
+        for (auto &g : m->gB) if (g.exec) cudaGraphExecDestroy(g.exec);
         delete m;
     }
     free_scratch(a);
@@ -1346,6 +1408,7 @@ extern "C" qkc_status qkc_load_ac(qkc_ctx *ctx, const uint8_t *bytes, uint64_t l
     a->ctx = ctx; a->prec = precision; a->kind = kind; a->n_qubits = nq; a->n_angles = na; a->n_vars = nv;
     a->N = N; a->E = E; a->D = D; a->n_leaves = nl; a->root = root; a->n_ind = nind; a->n_param = n_param;
     a->n_const = nl - nind - n_param; a->level_off = lo;
+    a->var_card = card;
     for (uint32_t i = nl; i < N; ++i)
         if (op[i] == OP_MUL) a->n_mul_edges += coff[i + 1] - coff[i];
     a->light_off = light_off;
@@ -1814,7 +1877,7 @@ static qkc_status ensure_sampling(qkc_ac *a, int64_t n_samples, int64_t n_groups
 
 
 // ---- memoised sampling (host side)
-static const qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
+static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
     *st = QKC_OK;
     if ((int)a->memo.size() <= cap) a->memo.resize(cap + 1, nullptr);
     if (a->memo[cap]) return a->memo[cap];
@@ -1877,82 +1940,136 @@ static const qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
     return m;
 }
 
-// One memoised upward pass of step j over `bound` group columns (device count n_active).
-static qkc_status memo_pass(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, int clamp, int64_t n_vec,
-                            const int32_t *n_active, int64_t bound, int cur, cudaStream_t s) {
+// Launch sequences of a memoised pass, captured once per (cap, step) as CUDA graphs.  They
+// read the memo descriptor (vectors, step, slots) and the pass descriptor (tile columns), and
+// their grids do not depend on the number of vectors or columns.
+static void launch_memoA_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, cudaStream_t s) {
+    const DevAC d = a->dev();
+    const unsigned g = (unsigned)(a->ctx->sm_count * 16);
+    for (uint32_t L = 0; L < a->D; ++L) {
+        const int64_t i0 = m->a_lvl[j][L], i1 = m->a_lvl[j][L + 1];
+        if (i1 == i0) continue;
+        const int64_t u0 = m->u_lvl[j][L], u1 = m->u_lvl[j][L + 1];
+        const uint32_t *nodes = m->d_a_nodes + m->a_base[j] + i0;
+        const int64_t *us = m->d_a_ustart + m->a_base[j] + i0;
+        if (a->prec == 32) memoA_level<float2><<<g, TPB, 0, s>>>(d, a->d_mdesc, nodes, us, i1 - i0, u0, u1);
+        else memoA_level<double2><<<g, TPB, 0, s>>>(d, a->d_mdesc, nodes, us, i1 - i0, u0, u1);
+    }
+}
+static int64_t memoA_launches(const qkc_ac *a, const qkc_ac::MemoMeta *m, int j) {
+    int64_t n = 0;
+    for (uint32_t L = 0; L < a->D; ++L) n += m->a_lvl[j][L + 1] > m->a_lvl[j][L];
+    return n;
+}
+static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, cudaStream_t s) {
     const DevAC d = a->dev();
     const int sms = a->ctx->sm_count;
     const uint32_t D = a->D;
+    const int64_t pitch = a->tile;
+    if (m->b_lvl[j][D] > 0) {
+        const unsigned gs = (unsigned)((pitch + TPB - 1) / TPB);
+        if (a->prec == 32) level_scale_kernel<<<gs, TPB, 0, s>>>(d, 0, pitch, 0, a->d_S, a->d_obs);
+        for (uint32_t L = 1; L < D; ++L) {
+            const int64_t b0 = m->b_lvl[j][L], b1 = m->b_lvl[j][L + 1];
+            if (a->prec == 32)
+                level_scale_kernel<<<gs, TPB, 0, s>>>(d, (int)L, pitch, m->floor0[j][L], a->d_S, a->d_obs);
+            if (b1 == b0) continue;
+            LevelArgs la{0, 0, (int)L, pitch};
+            const uint32_t *nodes = m->d_b_nodes + m->b_base[j] + b0;
+            const int64_t cw = a->prec == 32 ? 64 : 32;
+            const int64_t items = ((b1 - b0 + NB - 1) / NB) * ((pitch + cw - 1) / cw);
+            const unsigned g = grid_for(items * 32, TPB, (int64_t)sms * 8);
+            if (a->prec == 32)
+                memoB_level_f32<<<g, TPB, 0, s>>>(d, la, nodes, b1 - b0, a->d_desc, a->d_mdesc, (float2 *)a->d_V,
+                                                   a->d_S, a->d_obs);
+            else
+                memoB_level_f64<<<g, TPB, 0, s>>>(d, la, nodes, b1 - b0, a->d_desc, a->d_mdesc, (double2 *)a->d_V);
+        }
+    }
+    memo_root<<<(unsigned)((pitch + TPB - 1) / TPB), TPB, 0, s>>>(a->d_mdesc, a->d_desc, a->root, (int)D - 1, a->d_V,
+                                                                  a->d_S, pitch, a->prec == 32, a->d_root);
+}
+static int64_t memoB_launches(const qkc_ac *a, const qkc_ac::MemoMeta *m, int j) {
+    int64_t n = 1;
+    if (m->b_lvl[j][a->D] > 0) {
+        n += a->prec == 32 ? (int64_t)a->D : 0;
+        for (uint32_t L = 1; L < a->D; ++L) n += m->b_lvl[j][L + 1] > m->b_lvl[j][L];
+    }
+    return n;
+}
+
+static qkc_status memo_graph(qkc_ac *a, qkc_ac::MemoMeta *m, int j, bool partB, cudaGraphExec_t *out) {
+    auto &slot = partB ? m->gB : m->gA;
+    if ((int)slot.size() <= j) slot.resize(a->n_qubits);
+    auto &g = slot[j];
+    if (g.exec && (!partB || (g.V == a->d_V && g.A == (const void *)a->d_root && g.pitch == a->tile))) {
+        *out = g.exec;
+        return QKC_OK;
+    }
+    if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
+    cudaStream_t cs;
+    QKC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        if (partB) launch_memoB_sequence(a, m, j, cs);
+        else launch_memoA_sequence(a, m, j, cs);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) {
+            e = cudaGraphInstantiate(&g.exec, graph, 0);
+            cudaGraphDestroy(graph);
+        }
+    }
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        g.exec = nullptr;
+        return fail(QKC_ERR_CUDA, "qkc: capturing a memoised-pass graph failed: %s", cudaGetErrorString(e));
+    }
+    g.V = a->d_V;
+    g.A = a->d_root;
+    g.pitch = a->tile;
+    *out = g.exec;
+    return QKC_OK;
+}
+
+// One memoised upward pass of step j over `bound` group columns (device count n_active).
+static qkc_status memo_pass(qkc_ac *a, qkc_ac::MemoMeta *m, int j, int clamp, int64_t n_vec,
+                            const int32_t *n_active, int64_t bound, int cur, cudaStream_t s) {
     const uint64_t jmask = j == 0 ? 0ull : (j >= 64 ? ~0ull : ((1ull << j) - 1ull));
+    qkc_status st;
+    cudaGraphExec_t gA, gB;
+    if ((st = memo_graph(a, m, j, false, &gA)) || (st = memo_graph(a, m, j, true, &gB))) return st;
     MemoDesc md{n_vec, j, clamp, jmask, a->d_pv, a->vec_cap, a->d_VA, m->d_offu + m->offu_base[j], a->d_sigma};
     set_memo_desc<<<1, 1, 0, s>>>(a->d_mdesc, md);
     ++a->launches;
-    qkc_status st;
     const size_t ri = a->recs.size();
     if ((st = rec_begin(a, 2, n_active, 0, bound, s))) return st;
     if (ri < a->recs.size()) {
         a->recs[ri].fixed_bytes = (double)n_vec * m->a_bytes_slot[j];
         a->recs[ri].col_bytes = m->b_bytes_col[j];
     }
-    // tier A, level by level (no tiles: V * 2^k slots per node)
-    for (uint32_t L = 0; L < D; ++L) {
-        const int64_t i0 = m->a_lvl[j][L], i1 = m->a_lvl[j][L + 1];
-        if (i1 == i0) continue;
-        const int64_t u0 = m->u_lvl[j][L], u1 = m->u_lvl[j][L + 1];
-        const unsigned g = grid_for(n_vec * (u1 - u0), TPB, (int64_t)sms * 16);
-        const uint32_t *nodes = m->d_a_nodes + m->a_base[j] + i0;
-        const int64_t *us = m->d_a_ustart + m->a_base[j] + i0;
-        if (a->prec == 32) memoA_level<float2><<<g, TPB, 0, s>>>(d, a->d_mdesc, nodes, us, i1 - i0, u0, u1);
-        else memoA_level<double2><<<g, TPB, 0, s>>>(d, a->d_mdesc, nodes, us, i1 - i0, u0, u1);
-        ++a->launches;
-    }
-    // tier B per tile of groups, then the roots
+    QKC_CUDA(cudaGraphLaunch(gA, s));  // tier A: once per step
+    a->launches += memoA_launches(a, m, j);
     const int64_t pitch = a->tile;
-    const bool anyB = m->b_lvl[j][D] > 0;
-    for (int64_t c0 = 0; c0 < bound; c0 += pitch) {
+    for (int64_t c0 = 0; c0 < bound; c0 += pitch) {  // tier B and the roots, per tile of groups
         const int64_t nc = std::min<int64_t>(pitch, bound - c0);
         EvSrc es{nullptr, a->d_g_prefix[cur], j, clamp, a->d_g_vec[cur], n_active, std::max<int64_t>(1, n_vec)};
         PassDesc desc{es, a->d_pv, a->vec_cap, c0, nc};
         set_desc<<<1, 1, 0, s>>>(a->d_desc, desc);
         ++a->launches;
-        if (anyB) {
-            const unsigned gs = (unsigned)((pitch + TPB - 1) / TPB);
-            if (a->prec == 32) {
-                level_scale_kernel<<<gs, TPB, 0, s>>>(d, 0, pitch, 0, a->d_S, a->d_obs);
-                ++a->launches;
-            }
-            for (uint32_t L = 1; L < D; ++L) {
-                const int64_t b0 = m->b_lvl[j][L], b1 = m->b_lvl[j][L + 1];
-                if (a->prec == 32) {
-                    level_scale_kernel<<<gs, TPB, 0, s>>>(d, (int)L, pitch, m->floor0[j][L], a->d_S, a->d_obs);
-                    ++a->launches;
-                }
-                if (b1 == b0) continue;
-                LevelArgs la{0, 0, (int)L, pitch};
-                const uint32_t *nodes = m->d_b_nodes + m->b_base[j] + b0;
-                const int64_t cw = a->prec == 32 ? 64 : 32;
-                const int64_t items = ((b1 - b0 + NB - 1) / NB) * ((nc + cw - 1) / cw);
-                const unsigned g = grid_for(items * 32, TPB, (int64_t)sms * 8);
-                if (a->prec == 32)
-                    memoB_level_f32<<<g, TPB, 0, s>>>(d, la, nodes, b1 - b0, a->d_desc, a->d_mdesc, (float2 *)a->d_V,
-                                                       a->d_S, a->d_obs);
-                else
-                    memoB_level_f64<<<g, TPB, 0, s>>>(d, la, nodes, b1 - b0, a->d_desc, a->d_mdesc, (double2 *)a->d_V);
-                ++a->launches;
-            }
-        }
-        memo_root<<<(unsigned)((nc + TPB - 1) / TPB), TPB, 0, s>>>(a->d_mdesc, a->d_desc, a->root, (int)D - 1, a->d_V,
-                                                                   a->d_S, pitch, a->prec == 32, a->d_root);
-        ++a->launches;
+        QKC_CUDA(cudaGraphLaunch(gB, s));
+        a->launches += memoB_launches(a, m, j);
     }
     if ((st = rec_end(a, ri, s))) return st;
     QKC_LAUNCH_CHECK();
     return QKC_OK;
 }
 
-extern "C" qkc_status qkc_set_sampler(qkc_ac *a, int32_t mode) {
-    if (!a || (mode != 0 && mode != 1)) return fail(QKC_ERR_ARG, "qkc_set_sampler: mode must be 0 or 1");
+extern "C" qkc_status qkc_set_sampler(qkc_ac *a, int32_t mode, int64_t memo_budget_bytes) {
+    if (!a || (mode != 0 && mode != 1) || memo_budget_bytes < 0)
+        return fail(QKC_ERR_ARG, "qkc_set_sampler: mode must be 0 or 1 and the budget >= 0");
     a->sampler = mode;
+    a->memo_budget = memo_budget_bytes;
     return QKC_OK;
 }
 
@@ -1975,18 +2092,27 @@ extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t
     // tile sized for the largest step (bounded by the sample count), roots for every group
     if ((st = ensure_tile(a, std::max(n_samp, n_vec))) || (st = ensure_roots(a, std::max(n_samp, n_vec)))) return st;
     // memoised passes: the largest cap (bits per node key) whose tier-A slots fit the budget
-    const qkc_ac::MemoMeta *meta = nullptr;
+    // (the caller's, else 15% of the device memory and half of what is free); if the slots
+    // cannot be allocated, smaller caps, then the per-group sampler
+    qkc_ac::MemoMeta *meta = nullptr;
     if (a->sampler == 1 && nq <= 63) {
+        // an already built key width whose slots fit the current allocation (no new metadata)
+        for (int cap = (int)a->memo.size() - 1; cap >= 1 && !meta; --cap)
+            if (a->memo[cap] && n_vec * a->memo[cap]->max_units * (int64_t)a->elem() <= a->va_bytes) meta = a->memo[cap];
+    }
+    if (a->sampler == 1 && nq <= 63 && !meta) {
         int ks = 0;
         while (ks < 24 && (2ll << ks) <= max_shots) ++ks;  // floor(log2(max_shots))
-        const double budget = 0.15 * (double)a->ctx->total_mem;
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); fr = 0; }
+        double budget = a->memo_budget > 0 ? (double)a->memo_budget
+                                            : std::min(0.15 * (double)a->ctx->total_mem,
+                                                       0.5 * (double)(fr + (size_t)a->va_bytes));
         for (int cap = ks; cap >= 1 && !meta; --cap) {
-            const qkc_ac::MemoMeta *m = memo_meta(a, cap, &st);
+            qkc_ac::MemoMeta *m = memo_meta(a, cap, &st);
             if (st) return st;
-            if ((double)n_vec * (double)m->max_units * (double)a->elem() <= budget) meta = m;
-        }
-        if (meta) {
-            const int64_t need = n_vec * meta->max_units * (int64_t)a->elem();
+            const int64_t need = n_vec * m->max_units * (int64_t)a->elem();
+            if ((double)need > budget) continue;
             if (need > a->va_bytes) {
                 QKC_CUDA(cudaDeviceSynchronize());
                 cudaFree(a->d_VA);
@@ -1994,11 +2120,11 @@ extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t
                 a->va_bytes = 0;
                 if (cudaMalloc(&a->d_VA, (size_t)std::max<int64_t>(need, 256)) != cudaSuccess) {
                     cudaGetLastError();
-                    return fail(QKC_ERR_NOMEM, "qkc_sample: cannot allocate %lld bytes of memoised slots",
-                                (long long)need);
+                    continue;  // try a smaller cap
                 }
                 a->va_bytes = need;
             }
+            meta = m;
         }
     }
     const unsigned gs = (unsigned)((n_samp + TPB - 1) / TPB);
@@ -2058,6 +2184,54 @@ extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t
     sample_write<<<gs, TPB, 0, s>>>(n_vec, max_shots, shots, a->d_s_bits, bits);
     ++a->launches;
     QKC_LAUNCH_CHECK();
+    return QKC_OK;
+}
+
+
+extern "C" qkc_status qkc_gibbs(qkc_ac *a, const int32_t *col_vec, const uint64_t *seeds, int64_t n_chains,
+                                int8_t *state, int64_t n_sweeps, int64_t sweep_offset, uint64_t *samples,
+                                void *stream) {
+    qkc_status st = check_query(a, col_vec, state, n_chains, "qkc_gibbs");
+    if (st) return st;
+    if (a->kind != QKC_AC_AMPLITUDE) return fail(QKC_ERR_UNSUPPORTED, "qkc_gibbs: needs an AMPLITUDE AC");
+    if (!seeds || n_sweeps < 0 || sweep_offset < 0) return fail(QKC_ERR_ARG, "qkc_gibbs: bad argument");
+    if (n_chains == 0 || n_sweeps == 0) return QKC_OK;
+    QKC_CUDA(cudaSetDevice(a->ctx->device));
+    if ((st = ensure_tile(a, n_chains)) || (st = ensure_roots(a, n_chains)) || (st = ensure_adj(a))) return st;
+    std::vector<int> ind0(a->n_vars + 1, 0), card(a->n_vars, 0);
+    for (uint32_t v = 0; v < a->n_vars; ++v) {
+        card[v] = (int)a->var_card[v];
+        ind0[v + 1] = ind0[v] + card[v];
+        if (card[v] > 16) return fail(QKC_ERR_UNSUPPORTED, "qkc_gibbs: variable with more than 16 values");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nv = (int)a->n_vars;
+    for (int64_t sw = 0; sw < n_sweeps; ++sw) {
+        for (int v = 0; v < nv; ++v) {
+            const uint64_t k = (uint64_t)(sweep_offset + sw) * (uint64_t)nv + (uint64_t)v + 1ull;
+            for (int64_t c0 = 0; c0 < n_chains; c0 += a->tile) {
+                const int64_t nc = std::min<int64_t>(a->tile, n_chains - c0);
+                EvSrc es{state, nullptr, 0, 0, col_vec, nullptr, std::max<int64_t>(1, a->n_vec)};
+                if ((st = run_up(a, es, c0, nc, s))) return st;
+                if ((st = run_down(a, nc, s))) return st;
+                const unsigned g = (unsigned)((nc + TPB - 1) / TPB);
+                if (a->prec == 32)
+                    gibbs_choose<float2><<<g, TPB, 0, s>>>((const float2 *)a->d_A, a->tile, c0, nc, v, card[v], ind0[v],
+                                                          nv, seeds, k, state);
+                else
+                    gibbs_choose<double2><<<g, TPB, 0, s>>>((const double2 *)a->d_A, a->tile, c0, nc, v, card[v],
+                                                           ind0[v], nv, seeds, k, state);
+                ++a->launches;
+                QKC_LAUNCH_CHECK();
+            }
+        }
+        if (samples) {
+            gibbs_record<<<(unsigned)((n_chains + TPB - 1) / TPB), TPB, 0, s>>>(state, n_chains, nv, (int)a->n_qubits,
+                                                                               n_sweeps, sw, samples);
+            ++a->launches;
+            QKC_LAUNCH_CHECK();
+        }
+    }
     return QKC_OK;
 }
 

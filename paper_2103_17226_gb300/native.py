@@ -72,7 +72,8 @@ def lib():
         "qkc_gradient": [P, P, P, P, I64, I64, P, P, P],
         "qkc_sample": [P, P, P, I64, I64, I64, P, P],
         "qkc_check_status": [P],
-        "qkc_set_sampler": [P, I32],
+        "qkc_gibbs": [P, P, P, I64, P, I64, I64, P, P],
+        "qkc_set_sampler": [P, I32, I64],
         "qkc_evaluate_static": [P, P, P, I64, P, P],
         "qkc_stats_enable": [P, I32, I64],
         "qkc_get_stats": [P, ctypes.POINTER(Stats)],
@@ -296,9 +297,10 @@ def sample(ac: AC, seeds, shots, max_shots: int, out=None, stream=None, total_sh
     return out
 
 
-def set_sampler(ac: AC, mode: int):
-    """qkc_set_sampler: 1 memoised (default), 0 one column per prefix group for every node."""
-    _check(lib().qkc_set_sampler(ac._h, mode))
+def set_sampler(ac: AC, mode: int, memo_budget_bytes: int = 0):
+    """qkc_set_sampler: 1 memoised (default), 0 one column per prefix group for every node;
+    memo_budget_bytes caps the memoised values' device memory (0: automatic)."""
+    _check(lib().qkc_set_sampler(ac._h, mode, memo_budget_bytes))
 
 
 def check_status(ac: AC):
@@ -316,3 +318,15 @@ def get_stats(ac: AC) -> dict:
     st = Stats()
     _check(lib().qkc_get_stats(ac._h, ctypes.byref(st)))
     return {f: getattr(st, f) for f, _ in Stats._fields_}
+
+
+def gibbs(ac: AC, col_vec, seeds, state, n_sweeps: int, sweep_offset: int = 0, samples=None, stream=None):
+    """qkc_gibbs: advance Gibbs chains (one per column) by n_sweeps sweeps; `state` [chains][n_vars]
+    int8 is updated in place; returns the outcome index after every sweep [chains][n_sweeps]."""
+    import torch
+    n = state.shape[0]
+    if samples is None:
+        samples = torch.zeros((n, n_sweeps), dtype=torch.int64, device=state.device)
+    _check(lib().qkc_gibbs(ac._h, _ptr(col_vec), _ptr(seeds), n, _ptr(state), n_sweeps, sweep_offset,
+                           _ptr(samples), _stream(stream)))
+    return samples

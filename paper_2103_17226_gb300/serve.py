@@ -81,7 +81,7 @@ class _Lane:
 class Server:
     def __init__(self, ctx: N.Context, ac_bytes: dict, precision: int = 32, lanes: int = 2, max_batch: int = 32,
                  max_shots: int = 10000, tile_columns: int = 16384, budget_samples: int = 4_000_000,
-                 serial: bool = False, memoised: bool = True):
+                 serial: bool = False, memoised: bool = True, memo_budget_bytes: int = 2 << 30):
         self.max_batch = max_batch
         self.max_shots = max_shots
         self.budget = budget_samples
@@ -94,7 +94,7 @@ class Server:
             for _ in range(lanes):
                 ac = N.load_ac(ctx, b, precision=precision)
                 N.set_tile_limit(ac, tile_columns)
-                N.set_sampler(ac, 1 if memoised else 0)
+                N.set_sampler(ac, 1 if memoised else 0, memo_budget_bytes)
                 na = max(1, ac.n_angles)
                 self.n_angles[name] = ac.n_angles
                 ln = _Lane(

@@ -253,3 +253,42 @@ def test_planted_transpose_instead_of_dagger_is_caught(monkeypatch):
     bad = Q.density_matrix(I.Circuit(1, 0).add("H", 0).add("DEP1", 0, p=0.3), [])
     monkeypatch.setattr(Q, "_apply_rho", real_apply)
     assert abs(bad[0, 1] - good[0, 1]) > 0.05  # the Y Kraus operator is complex: caught by the closed form
+
+
+def test_gibbs_oracle_kernel_has_the_noisy_distribution_as_stationary_law():
+    """The oracle's Gibbs update (Sec. 3.3.2): with a uniform u, variable V moves to v with
+    probability |A(., V=v)|^2 / sum_w |A(., V=w)|^2.  The product of one update per variable
+    (a sweep) must leave pi(x, r) = |A(x, r)|^2 / Z invariant, and the x-marginal of pi must be
+    the density-matrix distribution."""
+    import itertools
+    from oracle import gibbs as G
+    c = I.Circuit(2, 1).add("H", 0).add("DEP1", 0, p=0.2).add("CNOT", (0, 1)).add("RY", 1, angle=0)
+    c.add("AD", 1, p=0.3)
+    ang = [0.7]
+    cards = [2, 2] + Q.channel_cards(c)
+    states = list(itertools.product(*[range(k) for k in cards]))
+    idx = {s: i for i, s in enumerate(states)}
+    pi = np.zeros(len(states))
+    for s in states:
+        psi = Q.statevector(c, ang, list(s[2:]))
+        pi[idx[s]] = abs(psi[s[0], s[1]]) ** 2
+    pi /= pi.sum()
+    T = np.eye(len(states))
+    for var in range(len(cards)):
+        Tv = np.zeros_like(T)
+        for s in states:
+            w = G.candidate_weights(c, ang, list(s), var)
+            if w.sum() == 0:
+                Tv[idx[s], idx[s]] = 1.0
+                continue
+            for v, wv in enumerate(w):
+                s2 = list(s)
+                s2[var] = v
+                Tv[idx[s], idx[tuple(s2)]] += wv / w.sum()
+        T = T @ Tv
+    assert np.abs(pi @ T - pi).max() < 1e-14
+    P = Q.probabilities(c, ang)
+    marg = np.zeros(4)
+    for s in states:
+        marg[s[0] * 2 + s[1]] += pi[idx[s]]
+    assert np.abs(marg - P).max() < 1e-14
