@@ -69,6 +69,7 @@ enum : uint8_t { OP_IND = 0, OP_PARAM = 1, OP_CONST = 2, OP_ADD = 3, OP_MUL = 4 
 constexpr int NB = 8;          // nodes per warp item
 constexpr int TPB = 256;       // threads per block
 constexpr int OBS_EMPTY = -1000;
+constexpr int MEMO_MARGIN = 3;  // memoise a node when its key space is >= 8x smaller than its group count
 
 // ------------------------------------------------------------------ device helpers
 __device__ __forceinline__ float pow2f(int k) {
@@ -544,27 +545,21 @@ struct MemoDesc {
     void *VA;             // tier-A values
     const int64_t *offu;  // per node: start of its tier-A block in units (x V slots), -1 for tier B
     const uint64_t *sigma;
+    const uint32_t *emask;  // per child edge of a tier-A node: the child's key bits in the parent's key
 };
 __global__ void set_memo_desc(MemoDesc *dst, MemoDesc v) { *dst = v; }
 
-// bits of `key` are ranked within rn; return those of the qubits in rc (subset of rn), ranked within rc
-__device__ __forceinline__ uint32_t subkey(uint32_t key, uint64_t rn, uint64_t rc) {
+// bits of x selected by mask m, packed into the low bits in order (contiguous runs take a shift)
+__device__ __forceinline__ uint32_t extract_bits(uint64_t x, uint64_t m) {
+    if (m == 0) return 0u;
+    const int z = __ffsll((long long)m) - 1;
+    const uint64_t r = m >> z;
+    if ((r & (r + 1)) == 0) return (uint32_t)((x >> z) & r);
     uint32_t out = 0;
-    for (int i = 0; rc; ++i) {
-        const int q = __ffsll((long long)rc) - 1;
-        rc &= rc - 1;
-        const int pos = __popcll(rn & ((1ull << q) - 1ull));
-        out |= ((key >> pos) & 1u) << i;
-    }
-    return out;
-}
-// key of a group prefix (j bits, qubit 0 first) on the qubits of rc (all < j)
-__device__ __forceinline__ uint32_t prefix_key(uint64_t prefix, int j, uint64_t rc) {
-    uint32_t out = 0;
-    for (int i = 0; rc; ++i) {
-        const int q = __ffsll((long long)rc) - 1;
-        rc &= rc - 1;
-        out |= (uint32_t)((prefix >> (j - 1 - q)) & 1ull) << i;
+    for (int i = 0; m; ++i) {
+        const uint64_t b = m & (~m + 1);
+        if (x & b) out |= 1u << i;
+        m ^= b;
     }
     return out;
 }
@@ -634,11 +629,13 @@ __global__ void __launch_bounds__(TPB) memoA_level(DevAC ac, const MemoDesc *mdp
             const uint32_t e0 = ac.child_off[n], e1 = ac.child_off[n + 1];
             r.x = (o == OP_MUL) ? 1 : 0;
             r.y = 0;
+            const uint32_t full = (uint32_t)((1ll << k) - 1);
             for (uint32_t e = e0; e < e1; ++e) {
                 const uint32_t c = ac.child[e];
-                const uint64_t rc = md.sigma[c] & md.jmask;
-                const int kc = __popcll(rc);
-                const int64_t cs = (vec << kc) | (int64_t)subkey(key, rn, rc);
+                const uint32_t me = md.emask[e];  // the child's key bits inside this node's key
+                int64_t cs;
+                if (me == full) cs = local;  // same key space: same slot layout
+                else cs = (vec << __popc(me)) | (int64_t)extract_bits(key, me);
                 const C v = VA[md.V * md.offu[c] + cs];
                 if (o == OP_MUL) {
                     C m;
@@ -681,7 +678,9 @@ __global__ void __launch_bounds__(TPB) memoB_level_f32(DevAC ac, LevelArgs a, co
         const bool two = col + 1 < ncols;
         const int64_t g0 = col0 + col, g1 = two ? g0 + 1 : g0;
         const int64_t vec0 = vec_of(es, g0), vec1 = vec_of(es, g1);
-        const uint64_t pre0 = es.prefix[g0], pre1 = es.prefix[g1];
+        // prefixes in qubit order (bit q = x_q) so a child's key is extract_bits(prefix, its support)
+        const uint64_t pre0 = md.j ? __brevll(es.prefix[g0] << (64 - md.j)) : 0ull;
+        const uint64_t pre1 = md.j ? __brevll(es.prefix[g1] << (64 - md.j)) : 0ull;
         const int2 sL = *reinterpret_cast<const int2 *>(S + (int64_t)a.L * a.pitch + col);
         int m0 = -127, m1 = -127;
         const int64_t k1 = min(count, (blk + 1) * NB);
@@ -699,8 +698,8 @@ __global__ void __launch_bounds__(TPB) memoB_level_f32(DevAC ac, LevelArgs a, co
             } else {
                 const uint64_t rc = md.sigma[c] & md.jmask;
                 const int kc = __popcll(rc);
-                v0 = VA[md.V * off + ((vec0 << kc) | (int64_t)prefix_key(pre0, md.j, rc))];
-                v1 = VA[md.V * off + ((vec1 << kc) | (int64_t)prefix_key(pre1, md.j, rc))];
+                v0 = VA[md.V * off + ((vec0 << kc) | (int64_t)extract_bits(pre0, rc))];
+                v1 = VA[md.V * off + ((vec1 << kc) | (int64_t)extract_bits(pre1, rc))];
                 s0 = s1 = 0;
             }
         };
@@ -759,7 +758,7 @@ __global__ void __launch_bounds__(TPB) memoB_level_f64(DevAC ac, LevelArgs a, co
         if (col >= ncols) continue;
         const int64_t g = col0 + col;
         const int64_t vec = vec_of(es, g);
-        const uint64_t pre = es.prefix[g];
+        const uint64_t pre = md.j ? __brevll(es.prefix[g] << (64 - md.j)) : 0ull;  // qubit order
         const int64_t k1 = min(count, (blk + 1) * NB);
         for (int64_t kk = blk * NB; kk < k1; ++kk) {
             const uint32_t n = nodes[kk];
@@ -773,7 +772,7 @@ __global__ void __launch_bounds__(TPB) memoB_level_f64(DevAC ac, LevelArgs a, co
                     v = __ldg(V + (int64_t)c * a.pitch + col);
                 } else {
                     const uint64_t rc = md.sigma[c] & md.jmask;
-                    v = VA[md.V * off + ((vec << __popcll(rc)) | (int64_t)prefix_key(pre, md.j, rc))];
+                    v = VA[md.V * off + ((vec << __popcll(rc)) | (int64_t)extract_bits(pre, rc))];
                 }
                 if (o == OP_MUL) r = cmul(r, v);
                 else { r.x += v.x; r.y += v.y; }
@@ -795,7 +794,8 @@ __global__ void memo_root(const MemoDesc *mdp, const PassDesc *pd, uint32_t root
     double2 r;
     if (off >= 0) {
         const uint64_t rc = md.sigma[root] & md.jmask;
-        const int64_t sl = md.V * off + ((vec_of(pd->es, g) << __popcll(rc)) | (int64_t)prefix_key(pd->es.prefix[g], md.j, rc));
+        const uint64_t pre = md.j ? __brevll(pd->es.prefix[g] << (64 - md.j)) : 0ull;
+        const int64_t sl = md.V * off + ((vec_of(pd->es, g) << __popcll(rc)) | (int64_t)extract_bits(pre, rc));
         if (prec32) {
             const float2 v = static_cast<const float2 *>(md.VA)[sl];
             r = make_double2(v.x, v.y);
@@ -1153,6 +1153,7 @@ struct qkc_ac {
         std::vector<double> a_bytes_slot, b_bytes_col;           // per step: algorithmic bytes per slot unit / column
         uint32_t *d_a_nodes = nullptr, *d_b_nodes = nullptr;
         int64_t *d_a_ustart = nullptr, *d_offu = nullptr;
+        uint32_t *d_emask = nullptr;    // [step][edge]: a child's key bits inside its tier-A parent's key
         std::vector<GraphSlot> gA, gB;  // captured launch sequences per step
     };
     std::vector<MemoMeta *> memo;  // indexed by cap
@@ -1242,6 +1243,7 @@ extern "C" void qkc_free_ac(qkc_ac *a) {
     for (auto *m : a->memo) {
         if (!m) continue;
         cudaFree(m->d_a_nodes); cudaFree(m->d_b_nodes); cudaFree(m->d_a_ustart); cudaFree(m->d_offu);
+        cudaFree(m->d_emask);
         for (auto &g : m->gA) if (g.exec) cudaGraphExecDestroy(g.exec);
         for (auto &g : m->gB) if (g.exec) cudaGraphExecDestroy(g.exec);
         delete m;
@@ -1885,8 +1887,9 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
     m->cap = cap;
     const int nq = (int)a->n_qubits;
     const uint32_t N = a->N, D = a->D;
-    std::vector<uint32_t> an, bn;
+    std::vector<uint32_t> an, bn, emask;
     std::vector<int64_t> au, offu;
+    emask.assign((size_t)nq * a->E, 0u);
     const std::vector<uint32_t> &child_off = a->h_child_off, &child = a->h_child;
     m->a_lvl.assign(nq, std::vector<int64_t>(D + 1, 0));
     m->u_lvl = m->a_lvl;
@@ -1894,7 +1897,9 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
     m->floor0.assign(nq, std::vector<uint8_t>(D, 0));
     for (int j = 0; j < nq; ++j) {
         const uint64_t jmask = j == 0 ? 0ull : (j >= 64 ? ~0ull : ((1ull << j) - 1ull));
-        const int t = std::min(cap, j);
+        // a node is memoised when its key space is at least 2^MEMO_MARGIN times smaller than the
+        // groups it would otherwise be evaluated for (early steps have at most V 2^j groups)
+        const int t = std::min(cap, std::max(0, j - MEMO_MARGIN));
         m->a_base.push_back((int64_t)an.size());
         m->b_base.push_back((int64_t)bn.size());
         m->offu_base.push_back((int64_t)offu.size());
@@ -1906,12 +1911,23 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
             for (uint32_t n = a->level_off[L]; n < a->level_off[L + 1]; ++n) {
                 const int k = __builtin_popcountll(a->sigma[n] & jmask);
                 const double deg = (double)(child_off[n + 1] - child_off[n]);
-                if (k <= t) {
+                // leaves are always memoised (at most one key bit, V * 2 slots): the memoised pass
+                // binds no leaf per group, so every leaf a per-group node reads must be here
+                if (k <= t || n < a->n_leaves) {
                     offu[ob + n] = units;
                     an.push_back(n);
                     au.push_back(units);
                     units += 1ll << k;
                     abytes += (double)(1ll << k) * (deg + 1.0);
+                    const uint64_t rn = a->sigma[n] & jmask;
+                    for (uint32_t e = child_off[n]; e < child_off[n + 1]; ++e) {
+                        const uint64_t rc = a->sigma[child[e]] & jmask;
+                        uint32_t me = 0;  // positions of rc's qubits among rn's, in qubit order
+                        int pos = 0;
+                        for (uint64_t r = rn; r; r &= r - 1, ++pos)
+                            if (rc & (r & (~r + 1))) me |= 1u << pos;
+                        emask[(size_t)j * a->E + e] = me;
+                    }
                 } else {
                     bn.push_back(n);
                     bbytes += deg + 1.0;
@@ -1931,8 +1947,10 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
     if ((*st = upload(&m->d_a_nodes, an.data(), an.size(), dummy)) ||
         (*st = upload(&m->d_a_ustart, au.data(), au.size(), dummy)) ||
         (*st = upload(&m->d_b_nodes, bn.data(), bn.size(), dummy)) ||
-        (*st = upload(&m->d_offu, offu.data(), offu.size(), dummy))) {
+        (*st = upload(&m->d_offu, offu.data(), offu.size(), dummy)) ||
+        (*st = upload(&m->d_emask, emask.data(), emask.size(), dummy))) {
         cudaFree(m->d_a_nodes); cudaFree(m->d_a_ustart); cudaFree(m->d_b_nodes); cudaFree(m->d_offu);
+        cudaFree(m->d_emask);
         delete m;
         return nullptr;
     }
@@ -2039,7 +2057,8 @@ static qkc_status memo_pass(qkc_ac *a, qkc_ac::MemoMeta *m, int j, int clamp, in
     qkc_status st;
     cudaGraphExec_t gA, gB;
     if ((st = memo_graph(a, m, j, false, &gA)) || (st = memo_graph(a, m, j, true, &gB))) return st;
-    MemoDesc md{n_vec, j, clamp, jmask, a->d_pv, a->vec_cap, a->d_VA, m->d_offu + m->offu_base[j], a->d_sigma};
+    MemoDesc md{n_vec,    j,         clamp, jmask, a->d_pv, a->vec_cap, a->d_VA, m->d_offu + m->offu_base[j],
+                a->d_sigma, m->d_emask + (size_t)j * a->E};
     set_memo_desc<<<1, 1, 0, s>>>(a->d_mdesc, md);
     ++a->launches;
     const size_t ri = a->recs.size();
@@ -2108,7 +2127,7 @@ extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t
         double budget = a->memo_budget > 0 ? (double)a->memo_budget
                                             : std::min(0.15 * (double)a->ctx->total_mem,
                                                        0.5 * (double)(fr + (size_t)a->va_bytes));
-        for (int cap = ks; cap >= 1 && !meta; --cap) {
+        for (int cap = ks - MEMO_MARGIN; cap >= 1 && !meta; --cap) {
             qkc_ac::MemoMeta *m = memo_meta(a, cap, &st);
             if (st) return st;
             const int64_t need = n_vec * m->max_units * (int64_t)a->elem();
