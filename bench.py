@@ -51,6 +51,8 @@ def parse():
                     help="uppass: only the upward pass over --columns sampling-prefix columns; gradpass: "
                          "upward + downward pass (gradient) over --columns Z-string columns (profiling cases)")
     ap.add_argument("--columns", type=int, default=2048)
+    ap.add_argument("--sampler", choices=["memo", "plain"], default="memo",
+                    help="memo: memoised chain-rule passes (automatic fallback); plain: every node per group")
     return ap.parse_args()
 
 
@@ -230,6 +232,7 @@ def run_ours(args):
     ac_bytes = N.compile(W["circuit"], N.QKC_AC_DENSITY)
     ctx = N.Context(local)
     ac = N.load_ac(ctx, ac_bytes, precision=32)
+    N.set_sampler(ac, 1 if args.sampler == "memo" else 0)
     V, S = W["V"], W["shots"]
     ev, cv, w = hamiltonian_columns(W)
     n_cols = len(cv)
@@ -348,6 +351,7 @@ def run_ours(args):
                        "hamiltonian_terms": len(W["coef"]), "ac_nodes": info["n_nodes"],
                        "ac_edges": info["n_edges"], "ac_levels": info["n_levels"],
                        "precision": "complex FP32 nodes, power-of-two scale per (level, column); FP64 decisions",
+                       "sampler": args.sampler,
                        "l2": "inputs larger than L2: node buffer = nodes x tile columns x 8 B "
                              f"({info['n_nodes'] * info['reserved_columns'] * 8 / 1e9:.1f} GB)"},
             "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": ach, "peak": hbm, "unit": "GB/s",

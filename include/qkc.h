@@ -271,10 +271,12 @@ qkc_status qkc_gibbs(qkc_ac *ac, const int32_t *col_vec_dev, const uint64_t *see
  * memoised -- at qubit j a node's value depends only on the vector and on the
  * prefix bits of the qubits < j in the node's indicator support, so nodes with
  * a small such support are evaluated once per (vector, key) instead of once
- * per prefix group (same results).  mode 0: every node once per group.
+ * per prefix group (same results), when estimated cheaper than mode 0.
+ * mode 2: memoised whenever the slots fit.  mode 0: every node once per group.
  * memo_budget_bytes caps the device memory of the memoised values (0: 15% of
  * the device memory and at most half of what is free); the sampler picks the
- * largest key width that fits and falls back to mode 0 when none does.
+ * largest key width that fits, and falls back to mode 0 when none does or when
+ * the memoised passes are estimated to cost more than the per-group ones.
  */
 qkc_status qkc_set_sampler(qkc_ac *ac, int32_t mode, int64_t memo_budget_bytes);
 

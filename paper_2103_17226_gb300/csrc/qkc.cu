@@ -546,6 +546,7 @@ struct MemoDesc {
     const int64_t *offu;  // per node: start of its tier-A block in units (x V slots), -1 for tier B
     const uint64_t *sigma;
     const uint32_t *emask;  // per child edge of a tier-A node: the child's key bits in the parent's key
+    const uint32_t *eoff;   // per child edge of a tier-B node: 1 + the child's tier-A block (units), 0 if tier B
 };
 __global__ void set_memo_desc(MemoDesc *dst, MemoDesc v) { *dst = v; }
 
@@ -685,9 +686,11 @@ __global__ void __launch_bounds__(TPB) memoB_level_f32(DevAC ac, LevelArgs a, co
         int m0 = -127, m1 = -127;
         const int64_t k1 = min(count, (blk + 1) * NB);
         // one child's two column values and scale exponents (tier A: unscaled, exponent 0)
-        auto child_vals = [&](uint32_t c, float2 &v0, float2 &v1, int &s0, int &s1) {
-            const int64_t off = md.offu[c];
-            if (off < 0) {
+        auto child_vals = [&](uint32_t e, float2 &v0, float2 &v1, int &s0, int &s1) {
+            const uint32_t c = ac.child[e];
+            const uint32_t eo = md.eoff[e];  // loaded alongside the child index
+            const int64_t off = (int64_t)eo - 1;
+            if (eo == 0) {
                 const int lc = ac.node_level[c];
                 const float4 v = __ldg(V4 + (int64_t)c * hp + (col >> 1));
                 const int2 sc = __ldg(reinterpret_cast<const int2 *>(S + (int64_t)lc * a.pitch + col));
@@ -711,8 +714,8 @@ __global__ void __launch_bounds__(TPB) memoB_level_f32(DevAC ac, LevelArgs a, co
             if (o == OP_MUL) {
                 float2 a0, a1, b0, b1;
                 int sa0, sa1, sb0, sb1;
-                child_vals(ac.child[e0], a0, a1, sa0, sa1);
-                child_vals(ac.child[e0 + 1], b0, b1, sb0, sb1);
+                child_vals(e0, a0, a1, sa0, sa1);
+                child_vals(e0 + 1, b0, b1, sb0, sb1);
                 r0 = cscale(cmul(a0, b0), pow2f(sa0 + sb0 - sL.x));
                 r1 = cscale(cmul(a1, b1), pow2f(sa1 + sb1 - sL.y));
             } else {
@@ -721,7 +724,7 @@ __global__ void __launch_bounds__(TPB) memoB_level_f32(DevAC ac, LevelArgs a, co
                 for (uint32_t e = e0; e < e1; ++e) {
                     float2 v0, v1;
                     int s0, s1;
-                    child_vals(ac.child[e], v0, v1, s0, s1);
+                    child_vals(e, v0, v1, s0, s1);
                     const float f0 = pow2f(s0 - sL.x), f1 = pow2f(s1 - sL.y);
                     r0.x += v0.x * f0; r0.y += v0.y * f0;
                     r1.x += v1.x * f1; r1.y += v1.y * f1;
@@ -766,9 +769,10 @@ __global__ void __launch_bounds__(TPB) memoB_level_f64(DevAC ac, LevelArgs a, co
             double2 r = make_double2(o == OP_MUL ? 1.0 : 0.0, 0.0);
             for (uint32_t e = ac.child_off[n]; e < ac.child_off[n + 1]; ++e) {
                 const uint32_t c = ac.child[e];
-                const int64_t off = md.offu[c];
+                const uint32_t eo = md.eoff[e];
+                const int64_t off = (int64_t)eo - 1;
                 double2 v;
-                if (off < 0) {
+                if (eo == 0) {
                     v = __ldg(V + (int64_t)c * a.pitch + col);
                 } else {
                     const uint64_t rc = md.sigma[c] & md.jmask;
@@ -1154,12 +1158,13 @@ struct qkc_ac {
         uint32_t *d_a_nodes = nullptr, *d_b_nodes = nullptr;
         int64_t *d_a_ustart = nullptr, *d_offu = nullptr;
         uint32_t *d_emask = nullptr;    // [step][edge]: a child's key bits inside its tier-A parent's key
+        uint32_t *d_eoff = nullptr;     // [step][edge]: 1 + a tier-A child's block, for tier-B parents
         std::vector<GraphSlot> gA, gB;  // captured launch sequences per step
     };
     std::vector<MemoMeta *> memo;  // indexed by cap
     void *d_VA = nullptr;
     int64_t va_bytes = 0;
-    int sampler = 1;  // 1: memoised, 0: one column per group for every node
+    int sampler = 1;  // 1: memoised when estimated cheaper, 2: memoised whenever it fits, 0: per group
     int64_t memo_budget = 0;  // bytes for memoised slots (0: automatic)
     int32_t *d_status = nullptr; // device-side error word (sampling input checks)
     GraphSlot g_up, g_down;
@@ -1243,7 +1248,7 @@ extern "C" void qkc_free_ac(qkc_ac *a) {
     for (auto *m : a->memo) {
         if (!m) continue;
         cudaFree(m->d_a_nodes); cudaFree(m->d_b_nodes); cudaFree(m->d_a_ustart); cudaFree(m->d_offu);
-        cudaFree(m->d_emask);
+        cudaFree(m->d_emask); cudaFree(m->d_eoff);
         for (auto &g : m->gA) if (g.exec) cudaGraphExecDestroy(g.exec);
         for (auto &g : m->gB) if (g.exec) cudaGraphExecDestroy(g.exec);
         delete m;
@@ -1887,9 +1892,10 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
     m->cap = cap;
     const int nq = (int)a->n_qubits;
     const uint32_t N = a->N, D = a->D;
-    std::vector<uint32_t> an, bn, emask;
+    std::vector<uint32_t> an, bn, emask, eoff;
     std::vector<int64_t> au, offu;
     emask.assign((size_t)nq * a->E, 0u);
+    eoff.assign((size_t)nq * a->E, 0u);
     const std::vector<uint32_t> &child_off = a->h_child_off, &child = a->h_child;
     m->a_lvl.assign(nq, std::vector<int64_t>(D + 1, 0));
     m->u_lvl = m->a_lvl;
@@ -1931,8 +1937,13 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
                 } else {
                     bn.push_back(n);
                     bbytes += deg + 1.0;
-                    for (uint32_t e = child_off[n]; e < child_off[n + 1]; ++e)
-                        if (offu[ob + child[e]] >= 0) m->floor0[j][L] = 1;
+                    for (uint32_t e = child_off[n]; e < child_off[n + 1]; ++e) {
+                        const int64_t oc = offu[ob + child[e]];
+                        if (oc >= 0) {
+                            m->floor0[j][L] = 1;
+                            eoff[(size_t)j * a->E + e] = (uint32_t)(oc + 1);
+                        }
+                    }
                 }
             }
             m->a_lvl[j][L + 1] = (int64_t)an.size() - m->a_base[j];
@@ -1943,14 +1954,20 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
         m->b_bytes_col.push_back(bbytes * (double)a->elem());
         m->max_units = std::max(m->max_units, units);
     }
+    if (m->max_units >= 0xffffffffll) {  // block offsets are stored in 32 bits per edge
+        delete m;
+        *st = QKC_OK;
+        return nullptr;
+    }
     int64_t dummy = 0;
     if ((*st = upload(&m->d_a_nodes, an.data(), an.size(), dummy)) ||
         (*st = upload(&m->d_a_ustart, au.data(), au.size(), dummy)) ||
         (*st = upload(&m->d_b_nodes, bn.data(), bn.size(), dummy)) ||
         (*st = upload(&m->d_offu, offu.data(), offu.size(), dummy)) ||
-        (*st = upload(&m->d_emask, emask.data(), emask.size(), dummy))) {
+        (*st = upload(&m->d_emask, emask.data(), emask.size(), dummy)) ||
+        (*st = upload(&m->d_eoff, eoff.data(), eoff.size(), dummy))) {
         cudaFree(m->d_a_nodes); cudaFree(m->d_a_ustart); cudaFree(m->d_b_nodes); cudaFree(m->d_offu);
-        cudaFree(m->d_emask);
+        cudaFree(m->d_emask); cudaFree(m->d_eoff);
         delete m;
         return nullptr;
     }
@@ -2058,7 +2075,7 @@ static qkc_status memo_pass(qkc_ac *a, qkc_ac::MemoMeta *m, int j, int clamp, in
     cudaGraphExec_t gA, gB;
     if ((st = memo_graph(a, m, j, false, &gA)) || (st = memo_graph(a, m, j, true, &gB))) return st;
     MemoDesc md{n_vec,    j,         clamp, jmask, a->d_pv, a->vec_cap, a->d_VA, m->d_offu + m->offu_base[j],
-                a->d_sigma, m->d_emask + (size_t)j * a->E};
+                a->d_sigma, m->d_emask + (size_t)j * a->E, m->d_eoff + (size_t)j * a->E};
     set_memo_desc<<<1, 1, 0, s>>>(a->d_mdesc, md);
     ++a->launches;
     const size_t ri = a->recs.size();
@@ -2085,8 +2102,8 @@ static qkc_status memo_pass(qkc_ac *a, qkc_ac::MemoMeta *m, int j, int clamp, in
 }
 
 extern "C" qkc_status qkc_set_sampler(qkc_ac *a, int32_t mode, int64_t memo_budget_bytes) {
-    if (!a || (mode != 0 && mode != 1) || memo_budget_bytes < 0)
-        return fail(QKC_ERR_ARG, "qkc_set_sampler: mode must be 0 or 1 and the budget >= 0");
+    if (!a || mode < 0 || mode > 2 || memo_budget_bytes < 0)
+        return fail(QKC_ERR_ARG, "qkc_set_sampler: mode must be 0, 1 or 2 and the budget >= 0");
     a->sampler = mode;
     a->memo_budget = memo_budget_bytes;
     return QKC_OK;
@@ -2114,12 +2131,12 @@ extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t
     // (the caller's, else 15% of the device memory and half of what is free); if the slots
     // cannot be allocated, smaller caps, then the per-group sampler
     qkc_ac::MemoMeta *meta = nullptr;
-    if (a->sampler == 1 && nq <= 63) {
+    if (a->sampler >= 1 && nq <= 63) {
         // an already built key width whose slots fit the current allocation (no new metadata)
         for (int cap = (int)a->memo.size() - 1; cap >= 1 && !meta; --cap)
             if (a->memo[cap] && n_vec * a->memo[cap]->max_units * (int64_t)a->elem() <= a->va_bytes) meta = a->memo[cap];
     }
-    if (a->sampler == 1 && nq <= 63 && !meta) {
+    if (a->sampler >= 1 && nq <= 63 && !meta) {
         int ks = 0;
         while (ks < 24 && (2ll << ks) <= max_shots) ++ks;  // floor(log2(max_shots))
         size_t fr = 0, tot = 0;
@@ -2130,6 +2147,7 @@ extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t
         for (int cap = ks - MEMO_MARGIN; cap >= 1 && !meta; --cap) {
             qkc_ac::MemoMeta *m = memo_meta(a, cap, &st);
             if (st) return st;
+            if (!m) continue;
             const int64_t need = n_vec * m->max_units * (int64_t)a->elem();
             if ((double)need > budget) continue;
             if (need > a->va_bytes) {
@@ -2145,6 +2163,19 @@ extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t
             }
             meta = m;
         }
+    }
+    if (meta && a->sampler == 1) {
+        // keep the memoised passes only when they are estimated cheaper than evaluating every
+        // node per group: bytes weighted by the measured cost per byte of each kernel kind
+        // (per-slot tier-A evaluation ~8x, per-group tier-B ~2x the plain upward pass)
+        double plain = 0.0, memo = 0.0, groups = (double)n_vec;
+        const double per_col = (double)a->elem() * ((double)a->E + (double)(a->N - a->n_leaves));
+        for (int j = 0; j < nq; ++j) {
+            plain += groups * per_col;
+            memo += 8.0 * (double)n_vec * meta->a_bytes_slot[j] + 2.0 * groups * meta->b_bytes_col[j];
+            groups = std::min(2.0 * groups, (double)live);
+        }
+        if (memo >= plain) meta = nullptr;
     }
     const unsigned gs = (unsigned)((n_samp + TPB - 1) / TPB);
     sample_init<<<std::max(gs, (unsigned)((n_vec + TPB - 1) / TPB)), TPB, 0, s>>>(

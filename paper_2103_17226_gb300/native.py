@@ -298,7 +298,8 @@ def sample(ac: AC, seeds, shots, max_shots: int, out=None, stream=None, total_sh
 
 
 def set_sampler(ac: AC, mode: int, memo_budget_bytes: int = 0):
-    """qkc_set_sampler: 1 memoised (default), 0 one column per prefix group for every node;
+    """qkc_set_sampler: 1 memoised when estimated cheaper (default), 2 memoised whenever it fits,
+    0 one column per prefix group for every node;
     memo_budget_bytes caps the memoised values' device memory (0: automatic)."""
     _check(lib().qkc_set_sampler(ac._h, mode, memo_budget_bytes))
 

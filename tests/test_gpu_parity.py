@@ -466,7 +466,7 @@ def test_memoised_sampler_equals_per_group_sampler(cuda_ctx, prec, name):
     seeds = t(I.vector_seeds(V, 17).astype(np.int64))
     shots = t(np.array([S, S // 3, 1, S - 7, 64][:V], dtype=np.int32))
     outs = []
-    for mode in (0, 1):
+    for mode in (0, 2):  # per group, memoised whenever it fits
         ac = N().load_ac(cuda_ctx, b, precision=prec)
         N().set_sampler(ac, mode)
         N().set_params(ac, t(angs))
