@@ -15,6 +15,10 @@ vectors; there is no collective on the data path).
 about 2.35M nodes): 256 vectors x 16 Z-string terms, <H> + gradient over 192
 angles; value = gradient columns/s.
 
+--workload vqe25 / vqe9: the paper's 2D-Ising VQE (5x5 noise-free, one layer; 3x3 with
+depolarising noise after every gate, two layers): 256 vectors x 1000 samples + <H> and
+its gradient per step; value = samples/s.
+
 --impl reference times the oracle (plain FP64 C evaluator, one host core) on a
 bounded sample of the same workload.
 """
@@ -42,15 +46,18 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["qaoa32", "hea16", "serve", "gibbs_kl"], default="qaoa32")
+    ap.add_argument("--workload", choices=["qaoa32", "hea16", "vqe25", "vqe9", "serve", "gibbs_kl"],
+                    default="qaoa32")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: Poisson arrivals per second")
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
-    ap.add_argument("--shots", type=int, default=10000)
+    ap.add_argument("--shots", type=int, default=None, help="samples per vector (qaoa32: 10000, vqe: 1000)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", choices=["step", "uppass", "gradpass"], default="step",
                     help="uppass: only the upward pass over --columns sampling-prefix columns; gradpass: "
                          "upward + downward pass (gradient) over --columns Z-string columns (profiling cases)")
     ap.add_argument("--columns", type=int, default=2048)
+    ap.add_argument("--tile", type=int, default=0, help="cap the column tile (0: library default)")
+    ap.add_argument("--memo-budget-gb", type=float, default=0.0, help="memoised-slot budget (0: library default)")
     ap.add_argument("--sampler", choices=["memo", "plain"], default="memo",
                     help="memo: memoised chain-rule passes (automatic fallback); plain: every node per group")
     return ap.parse_args()
@@ -69,9 +76,22 @@ def make_workload(name, shots):
         for k, (i, j) in enumerate(edges):
             sup[k, i] = sup[k, j] = True
         coef = np.full(len(edges), -0.5)
-        return dict(name="qaoa32_3reg_p1_ideal", circuit=c, V=V, angles=angles, sup=sup, coef=coef, shots=shots,
+        return dict(name="qaoa32_3reg_p1_ideal", circuit=c, V=V, angles=angles, sup=sup, coef=coef,
+                    shots=10000 if shots is None else shots,
                     seeds=I.vector_seeds(V, 5), unit="samples/s", metric="samples/s (chain-rule sampling, "
                     "with <C> + gradient, of a 32-qubit QAOA density AC)")
+    if name in ("vqe25", "vqe9"):
+        # the paper's second workload: VQE for the 2D Ising model (Sec. 4.1; Table 7 sizes): 5x5 grid
+        # noise-free with one ansatz layer, or 3x3 grid with depolarising noise after every gate and
+        # two layers; <H> + gradient of H = sum_<ij> Z_i Z_j + 0.5 sum_i Z_i, and 1000 samples per vector
+        wl, (r, cl) = ("vqe_ising_5x5_ideal", (5, 5)) if name == "vqe25" else ("vqe_ising_3x3_noisy", (3, 3))
+        c = I.workload(wl)
+        V = 256
+        sup, coef = I.ising_hamiltonian(r, cl)
+        return dict(name=wl, circuit=c, V=V, angles=I.uniform_angles(V, c.n_angles, seed=7), sup=sup, coef=coef,
+                    shots=1000 if shots is None else shots, seeds=I.vector_seeds(V, 7), unit="samples/s",
+                    metric=f"samples/s (chain-rule sampling, with <H> + gradient, of a {c.n_qubits}-qubit "
+                           f"2D-Ising VQE density AC)")
     c = I.workload("hea16_l6")
     V = 256
     sup, coef = I.z_string_hamiltonian(16, 16, seed=3)
@@ -232,7 +252,9 @@ def run_ours(args):
     ac_bytes = N.compile(W["circuit"], N.QKC_AC_DENSITY)
     ctx = N.Context(local)
     ac = N.load_ac(ctx, ac_bytes, precision=32)
-    N.set_sampler(ac, 1 if args.sampler == "memo" else 0)
+    N.set_sampler(ac, 1 if args.sampler == "memo" else 0, int(args.memo_budget_gb * 2 ** 30))
+    if args.tile:
+        N.set_tile_limit(ac, args.tile)
     V, S = W["V"], W["shots"]
     ev, cv, w = hamiltonian_columns(W)
     n_cols = len(cv)
@@ -358,7 +380,12 @@ def run_ours(args):
                          "frac": (ach / hbm) if ach else None, "peak_source": peak_src,
                          "bytes_per_pass": per_launch_bytes, "traffic": None,
                          "up_pass_gbs": up_gbs, "down_pass_gbs": dn_gbs, "memo_pass_gbs": memo_gbs,
-                         "time_ms": {k: stats[k + "_ms"] for k in ("up", "down", "memo")}},
+                         "memo_tier_a_gbs": (stats["memo_a_bytes"] / (stats["memo_a_ms"] * 1e6)
+                                             if stats["memo_a_ms"] > 0 else None),
+                         "memo_tier_b_gbs": ((stats["memo_bytes"] - stats["memo_a_bytes"])
+                                             / ((stats["memo_ms"] - stats["memo_a_ms"]) * 1e6)
+                                             if stats["memo_ms"] > stats["memo_a_ms"] else None),
+                         "time_ms": {k: stats[k + "_ms"] for k in ("up", "down", "memo", "memo_a")}},
             "gpu_launches": stats["launches"],
             "edge_evals_per_s": edge_evals * world / (ms_max / 1e3),
             "clocks": clk,

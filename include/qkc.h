@@ -172,7 +172,7 @@ qkc_status qkc_reserve(qkc_ac *ac, int64_t max_vectors, int64_t max_columns);
 
 /*
  * qkc_set_tile_limit -- cap the column tile of this AC (0 = default: values and
- * adjoints each within 35% of the device memory; otherwise >= 64, rounded down
+ * adjoints each within 25% of the device memory; otherwise >= 64, rounded down
  * to a multiple of 64).  Calls with more columns than the tile process them in
  * tiles.  Lets many resident ACs share one device (serving).  Takes effect on
  * the next scratch growth; set it before the first query.
@@ -273,8 +273,8 @@ qkc_status qkc_gibbs(qkc_ac *ac, const int32_t *col_vec_dev, const uint64_t *see
  * a small such support are evaluated once per (vector, key) instead of once
  * per prefix group (same results), when estimated cheaper than mode 0.
  * mode 2: memoised whenever the slots fit.  mode 0: every node once per group.
- * memo_budget_bytes caps the device memory of the memoised values (0: 15% of
- * the device memory and at most half of what is free); the sampler picks the
+ * memo_budget_bytes caps the device memory of the memoised values (0: 40% of
+ * the device memory and at most 60% of what is free); the sampler picks the
  * largest key width that fits, and falls back to mode 0 when none does or when
  * the memoised passes are estimated to cost more than the per-group ones.
  */
@@ -336,7 +336,8 @@ typedef struct {
     int64_t down_passes, down_columns, down_launches;
     double down_ms, down_bytes;
     int64_t memo_passes, memo_columns;  /* memoised sampling passes (qkc_set_sampler mode 1) */
-    double memo_ms, memo_bytes;
+    double memo_ms, memo_bytes;         /* both tiers */
+    double memo_a_ms, memo_a_bytes;     /* tier A alone (the per-slot part of memo_ms / memo_bytes) */
 } qkc_stats;
 qkc_status qkc_stats_enable(qkc_ac *ac, int32_t enable, int64_t max_records);
 qkc_status qkc_get_stats(qkc_ac *ac, qkc_stats *out);

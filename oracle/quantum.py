@@ -232,13 +232,14 @@ def z_expectation(probs: np.ndarray, support) -> float:
     return density_evidence(probs, ev).real
 
 
-def hamiltonian_value_and_gradient(circuit, angles, supports, coefs):
-    """<H> = sum_t c_t <Z_{S_t}> and its exact gradient in every angle (forward mode)."""
+def hamiltonian_value_and_gradient(circuit, angles, supports, coefs, angle_slots=None):
+    """<H> = sum_t c_t <Z_{S_t}> and its exact gradient (forward mode) in every angle, or in
+    the listed angle slots only (the other entries stay 0)."""
     n = circuit.n_qubits
     probs = probabilities(circuit, angles)
     val = sum(c * z_expectation(probs, s) for s, c in zip(supports, coefs))
     grad = np.zeros(circuit.n_angles)
-    for k in range(circuit.n_angles):
+    for k in (range(circuit.n_angles) if angle_slots is None else angle_slots):
         _, drho = density_matrix_and_derivative(circuit, angles, k)
         dprobs = np.real(np.diag(drho))
         grad[k] = sum(c * z_expectation(dprobs, s) for s, c in zip(supports, coefs))

@@ -69,7 +69,7 @@ enum : uint8_t { OP_IND = 0, OP_PARAM = 1, OP_CONST = 2, OP_ADD = 3, OP_MUL = 4 
 constexpr int NB = 8;          // nodes per warp item
 constexpr int TPB = 256;       // threads per block
 constexpr int OBS_EMPTY = -1000;
-constexpr int MEMO_MARGIN = 3;  // memoise a node when its key space is >= 8x smaller than its group count
+constexpr int MEMO_MARGIN = 2;  // early steps: memoise a node when its key space is >= 4x smaller than V 2^j
 
 // ------------------------------------------------------------------ device helpers
 __device__ __forceinline__ float pow2f(int k) {
@@ -527,6 +527,17 @@ __global__ void __launch_bounds__(TPB) down_heavy_f64(DevAC ac, DownArgs a, cons
 }
 
 // ------------------------------------------------------------------ memoised sampling
+// How a tier-B node finds a tier-A child's slot from a group's prefix (bit q = x_q): the
+// child's key is the prefix bits at the child's support m, packed into the low bits, computed
+// by the mask-compress of Warren (Hacker's Delight, 2nd ed., Sec. 7-4) with its six
+// shift masks mv[i] (bits moving right by 2^i in round i) precomputed on the host.
+struct KeyPlan {
+    int64_t off;     // the child's tier-A block (units)
+    uint64_t m;      // the child's support among the qubits < j
+    uint64_t mv[6];  // compress masks of m
+    uint32_t k, pad; // |m|
+};
+
 // At sampling step j a group's evidence fixes qubits < j to its prefix and qubit j to 0, so a
 // node's value depends only on the vector and on the prefix bits of the qubits < j in the
 // node's indicator support sigma(n).  With k = |sigma(n) & jmask| such bits, a node needs at
@@ -546,8 +557,28 @@ struct MemoDesc {
     const int64_t *offu;  // per node: start of its tier-A block in units (x V slots), -1 for tier B
     const uint64_t *sigma;
     const uint32_t *emask;  // per child edge of a tier-A node: the child's key bits in the parent's key
-    const uint32_t *eoff;   // per child edge of a tier-B node: 1 + the child's tier-A block (units), 0 if tier B
+    const uint32_t *eoff;   // per child edge of a tier-B node: 1 + the child's key plan, 0 if tier B
+    const KeyPlan *kplan;  // per tier-A child of a tier-B node (this step)
 };
+
+__device__ __forceinline__ uint32_t plan_key(const KeyPlan *kp, uint64_t x, bool narrow) {
+    if (narrow) {  // every qubit < j < 32: 32-bit words, five rounds
+        uint32_t y = (uint32_t)x & (uint32_t)__ldg(&kp->m);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const uint32_t t = y & (uint32_t)__ldg(&kp->mv[i]);
+            y = (y ^ t) | (t >> (1 << i));
+        }
+        return y;
+    }
+    uint64_t y = x & __ldg(&kp->m);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const uint64_t t = y & __ldg(&kp->mv[i]);
+        y = (y ^ t) | (t >> (1 << i));
+    }
+    return (uint32_t)y;
+}
 __global__ void set_memo_desc(MemoDesc *dst, MemoDesc v) { *dst = v; }
 
 // bits of x selected by mask m, packed into the low bits in order (contiguous runs take a shift)
@@ -586,75 +617,79 @@ __device__ __forceinline__ C memo_leaf(const DevAC &ac, const MemoDesc &md, uint
     return r;
 }
 
-// One level of tier A: a thread per slot of the level's tier-A blocks.
+// Tier-A nodes of one level, grouped by key width: the group's nodes are nodes[nb ..] and
+// their unit blocks (2^k units each, one unit = one key of one vector) start t0 units into the
+// level, in the same order, so a unit index gives its node and key by a shift.
+struct MemoAGroup {
+    uint32_t t0, nb, k;
+};
+
+// One level of tier A: a thread per slot (vector, node, key) of the level's tier-A blocks.
 template <typename C>
 __global__ void __launch_bounds__(TPB) memoA_level(DevAC ac, const MemoDesc *mdp, const uint32_t *nodes,
-                                                    const int64_t *ustart, int64_t count, int64_t u0, int64_t u1) {
+                                                    const MemoAGroup *grp, int ng, int64_t u0, uint32_t U) {
+    if (U == 0 || ng <= 0) return;
     const MemoDesc md = *mdp;
     C *VA = static_cast<C *>(md.VA);
-    const int64_t total = md.V * (u1 - u0);
-    const int lane = threadIdx.x & 31;
-    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = wid * 32; base < total; base += nw * 32) {
-        // one binary search per warp (largest i with V * ustart[i] <= first slot), then each lane
-        // steps over the few node boundaries inside the warp's 32 slots
-        int64_t lo0 = 0;
-        if (lane == 0) {
-            const int64_t sl0 = md.V * u0 + base;
-            int64_t l = 0, h = count - 1;
-            while (l < h) {
-                const int64_t mid = (l + h + 1) >> 1;
-                if (md.V * ustart[mid] <= sl0) l = mid;
-                else h = mid - 1;
-            }
-            lo0 = l;
-        }
-        lo0 = __shfl_sync(0xffffffffu, lo0, 0);
-        const int64_t t = base + lane;
-        if (t >= total) continue;
-        const int64_t sl = md.V * u0 + t;
-        int64_t lo = lo0;
-        while (lo + 1 < count && md.V * ustart[lo + 1] <= sl) ++lo;
-        const uint32_t n = nodes[lo];
-        const int64_t local = sl - md.V * ustart[lo];
-        const uint64_t rn = md.sigma[n] & md.jmask;
-        const int k = __popcll(rn);
-        const int64_t vec = local >> k;
-        const uint32_t key = (uint32_t)(local & ((1ll << k) - 1));
-        C r;
-        const uint8_t o = ac.op[n];
-        if (o <= OP_CONST) {
-            r = memo_leaf<C>(ac, md, n, vec, key);
-        } else {
-            const uint32_t e0 = ac.child_off[n], e1 = ac.child_off[n + 1];
-            r.x = (o == OP_MUL) ? 1 : 0;
-            r.y = 0;
-            const uint32_t full = (uint32_t)((1ll << k) - 1);
-            for (uint32_t e = e0; e < e1; ++e) {
-                const uint32_t c = ac.child[e];
-                const uint32_t me = md.emask[e];  // the child's key bits inside this node's key
-                int64_t cs;
-                if (me == full) cs = local;  // same key space: same slot layout
-                else cs = (vec << __popc(me)) | (int64_t)extract_bits(key, me);
-                const C v = VA[md.V * md.offu[c] + cs];
-                if (o == OP_MUL) {
-                    C m;
-                    m.x = r.x * v.x - r.y * v.y;
-                    m.y = r.x * v.y + r.y * v.x;
-                    r = m;
-                } else {
-                    r.x += v.x;
-                    r.y += v.y;
+    const uint32_t nblk = (U + TPB - 1) / TPB;
+    const int64_t items = md.V * (int64_t)nblk;
+    // block item b covers vector b / nblk and units (b % nblk) * TPB + thread; quotient and
+    // remainder are stepped along the grid-stride loop rather than divided every time
+    int64_t vec = blockIdx.x / nblk;
+    uint32_t rb = blockIdx.x % nblk;
+    const uint32_t dq = gridDim.x / nblk, dr = gridDim.x % nblk;
+    for (int64_t b = blockIdx.x; b < items; b += gridDim.x) {
+        const uint32_t t = rb * TPB + threadIdx.x;
+        if (t < U) {
+            int gi = 0;
+            while (gi + 1 < ng && __ldg(&grp[gi + 1].t0) <= t) ++gi;
+            const uint32_t t0 = __ldg(&grp[gi].t0), nb = __ldg(&grp[gi].nb);
+            const int k = (int)__ldg(&grp[gi].k);
+            const uint32_t rel = t - t0;
+            const uint32_t nl = rel >> k;
+            const uint32_t key = rel & ((1u << k) - 1u);
+            const uint32_t n = nodes[nb + nl];
+            const int64_t local = (vec << k) | (int64_t)key;
+            C r;
+            const uint8_t o = ac.op[n];
+            if (o <= OP_CONST) {
+                r = memo_leaf<C>(ac, md, n, vec, key);
+            } else {
+                const uint32_t e0 = ac.child_off[n], e1 = ac.child_off[n + 1];
+                r.x = (o == OP_MUL) ? 1 : 0;
+                r.y = 0;
+                const uint32_t full = (1u << k) - 1u;
+                for (uint32_t e = e0; e < e1; ++e) {
+                    const uint32_t c = ac.child[e];
+                    const uint32_t me = md.emask[e];  // the child's key bits inside this node's key
+                    int64_t cs;
+                    if (me == full) cs = local;  // same key space: same slot layout
+                    else cs = (vec << __popc(me)) | (int64_t)extract_bits(key, me);
+                    const C v = VA[md.V * md.offu[c] + cs];
+                    if (o == OP_MUL) {
+                        C m;
+                        m.x = r.x * v.x - r.y * v.y;
+                        m.y = r.x * v.y + r.y * v.x;
+                        r = m;
+                    } else {
+                        r.x += v.x;
+                        r.y += v.y;
+                    }
                 }
             }
+            VA[md.V * (u0 + t0 + ((int64_t)nl << k)) + local] = r;
         }
-        VA[md.V * ustart[lo] + local] = r;
+        rb += dr;
+        vec += dq;
+        if (rb >= nblk) {
+            rb -= nblk;
+            ++vec;
+        }
     }
 }
 
 // One level of tier B (FP32): as up_level_f32 over a node list, tier-A children read by key.
-__global__ void __launch_bounds__(TPB) memoB_level_f32(DevAC ac, LevelArgs a, const uint32_t *nodes, int64_t count,
+__global__ void __launch_bounds__(TPB, 4) memoB_level_f32(DevAC ac, LevelArgs a, const uint32_t *nodes, int64_t count,
                                                         const PassDesc *pd, const MemoDesc *mdp,
                                                         float2 *__restrict__ V, const int *__restrict__ S,
                                                         int *__restrict__ obs) {
@@ -662,6 +697,7 @@ __global__ void __launch_bounds__(TPB) memoB_level_f32(DevAC ac, LevelArgs a, co
     if (ncols <= 0 || count <= 0) return;
     const MemoDesc md = *mdp;
     const float2 *VA = static_cast<const float2 *>(md.VA);
+    const bool narrow = md.j <= 32;
     const EvSrc es = pd->es;
     const int64_t col0 = pd->col0;
     const int lane = threadIdx.x & 31;
@@ -699,10 +735,11 @@ __global__ void __launch_bounds__(TPB) memoB_level_f32(DevAC ac, LevelArgs a, co
                 s0 = sc.x;
                 s1 = sc.y;
             } else {
-                const uint64_t rc = md.sigma[c] & md.jmask;
-                const int kc = __popcll(rc);
-                v0 = VA[md.V * off + ((vec0 << kc) | (int64_t)extract_bits(pre0, rc))];
-                v1 = VA[md.V * off + ((vec1 << kc) | (int64_t)extract_bits(pre1, rc))];
+                const KeyPlan *kp = md.kplan + off;
+                const int kc = (int)__ldg(&kp->k);
+                const int64_t base = md.V * __ldg(&kp->off);
+                v0 = VA[base + ((vec0 << kc) | (int64_t)plan_key(kp, pre0, narrow))];
+                v1 = VA[base + ((vec1 << kc) | (int64_t)plan_key(kp, pre1, narrow))];
                 s0 = s1 = 0;
             }
         };
@@ -747,6 +784,7 @@ __global__ void __launch_bounds__(TPB) memoB_level_f64(DevAC ac, LevelArgs a, co
     if (ncols <= 0 || count <= 0) return;
     const MemoDesc md = *mdp;
     const double2 *VA = static_cast<const double2 *>(md.VA);
+    const bool narrow = md.j <= 32;
     const EvSrc es = pd->es;
     const int64_t col0 = pd->col0;
     const int lane = threadIdx.x & 31;
@@ -775,8 +813,8 @@ __global__ void __launch_bounds__(TPB) memoB_level_f64(DevAC ac, LevelArgs a, co
                 if (eo == 0) {
                     v = __ldg(V + (int64_t)c * a.pitch + col);
                 } else {
-                    const uint64_t rc = md.sigma[c] & md.jmask;
-                    v = VA[md.V * off + ((vec << __popcll(rc)) | (int64_t)extract_bits(pre, rc))];
+                    const KeyPlan *kp = md.kplan + off;
+                    v = VA[md.V * __ldg(&kp->off) + ((vec << (int)__ldg(&kp->k)) | (int64_t)plan_key(kp, pre, narrow))];
                 }
                 if (o == OP_MUL) r = cmul(r, v);
                 else { r.x += v.x; r.y += v.y; }
@@ -1151,14 +1189,17 @@ struct qkc_ac {
     struct MemoMeta {
         int cap = 0;
         int64_t max_units = 0;
-        std::vector<std::vector<int64_t>> a_lvl, u_lvl, b_lvl;  // per step, [D + 1]
+        std::vector<std::vector<int64_t>> a_lvl, u_lvl, b_lvl, g_lvl;  // per step, [D + 1]
         std::vector<std::vector<uint8_t>> floor0;               // per step, [D]
-        std::vector<int64_t> a_base, b_base, offu_base;          // per step
+        std::vector<int64_t> a_base, b_base, offu_base, g_base;  // per step
         std::vector<double> a_bytes_slot, b_bytes_col;           // per step: algorithmic bytes per slot unit / column
         uint32_t *d_a_nodes = nullptr, *d_b_nodes = nullptr;
-        int64_t *d_a_ustart = nullptr, *d_offu = nullptr;
+        MemoAGroup *d_a_grp = nullptr;  // tier-A key-width groups, per step and level
+        int64_t *d_offu = nullptr;
         uint32_t *d_emask = nullptr;    // [step][edge]: a child's key bits inside its tier-A parent's key
-        uint32_t *d_eoff = nullptr;     // [step][edge]: 1 + a tier-A child's block, for tier-B parents
+        uint32_t *d_eoff = nullptr;     // [step][edge]: 1 + a tier-A child's key plan, for tier-B parents
+        KeyPlan *d_kplan = nullptr;     // key plans of the tier-A children of tier-B nodes, per step
+        std::vector<int64_t> kp_base;   // per step: first key plan
         std::vector<GraphSlot> gA, gB;  // captured launch sequences per step
     };
     std::vector<MemoMeta *> memo;  // indexed by cap
@@ -1172,7 +1213,7 @@ struct qkc_ac {
     // every chain of level kernels with the number of columns it processed
     int64_t launches = 0;
     bool timing = false;
-    struct Rec { cudaEvent_t e0, e1; int kind; double fixed_bytes, col_bytes; };  // kind 0 up, 1 down, 2 memo
+    struct Rec { cudaEvent_t e0, e1; int kind; double fixed_bytes, col_bytes; };  // 0 up, 1 down, 2/3 memo tier B/A
     std::vector<Rec> recs;
     int64_t *d_statcols = nullptr;
     int64_t statcap = 0;
@@ -1247,8 +1288,8 @@ extern "C" void qkc_free_ac(qkc_ac *a) {
     cudaFree(a->d_VA);
     for (auto *m : a->memo) {
         if (!m) continue;
-        cudaFree(m->d_a_nodes); cudaFree(m->d_b_nodes); cudaFree(m->d_a_ustart); cudaFree(m->d_offu);
-        cudaFree(m->d_emask); cudaFree(m->d_eoff);
+        cudaFree(m->d_a_nodes); cudaFree(m->d_b_nodes); cudaFree(m->d_a_grp); cudaFree(m->d_offu);
+        cudaFree(m->d_emask); cudaFree(m->d_eoff); cudaFree(m->d_kplan);
         for (auto &g : m->gA) if (g.exec) cudaGraphExecDestroy(g.exec);
         for (auto &g : m->gB) if (g.exec) cudaGraphExecDestroy(g.exec);
         delete m;
@@ -1486,12 +1527,12 @@ static qkc_status ensure_vectors(qkc_ac *a, int64_t nvec) {
 
 // Column tile: values for `cols` columns, rounded up to 64, capped so that the
 // value buffer (and, when a downward pass needs it, the adjoint buffer of the
-// same shape) each stay within 35% of the device memory.
+// same shape) each stay within 25% of the device memory.
 static qkc_status ensure_tile(qkc_ac *a, int64_t cols) {
     int64_t want = (cols + 63) / 64 * 64;
     if (want < 64) want = 64;
     const int64_t per_col = (int64_t)a->N * (int64_t)a->elem() + 8LL * a->D;
-    int64_t cap = (int64_t)((double)a->ctx->total_mem * 0.35) / std::max<int64_t>(1, per_col);
+    int64_t cap = (int64_t)((double)a->ctx->total_mem * 0.25) / std::max<int64_t>(1, per_col);
     if (const char *env = std::getenv("QKC_MAX_TILE_COLUMNS")) {  // smaller tiles (tests of the tiled path)
         const long long lim = std::atoll(env);
         if (lim > 0) cap = std::min<int64_t>(cap, lim);
@@ -1884,6 +1925,25 @@ static qkc_status ensure_sampling(qkc_ac *a, int64_t n_samples, int64_t n_groups
 
 
 // ---- memoised sampling (host side)
+// The six shift masks of Warren's mask-compress (Hacker's Delight, 2nd ed., Sec. 7-4): round i
+// moves the bits of mv[i] right by 2^i; the count of mask zeros to the right of each bit is
+// formed by a parallel prefix XOR.
+static void compress_masks(uint64_t m, uint64_t mv[6]) {
+    uint64_t mk = ~m << 1;
+    for (int i = 0; i < 6; ++i) {
+        uint64_t mp = mk ^ (mk << 1);
+        mp ^= mp << 2;
+        mp ^= mp << 4;
+        mp ^= mp << 8;
+        mp ^= mp << 16;
+        mp ^= mp << 32;
+        const uint64_t v = mp & m;
+        mv[i] = v;
+        m = (m ^ v) | (v >> (1 << i));
+        mk &= ~mp;
+    }
+}
+
 static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
     *st = QKC_OK;
     if ((int)a->memo.size() <= cap) a->memo.resize(cap + 1, nullptr);
@@ -1893,62 +1953,93 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
     const int nq = (int)a->n_qubits;
     const uint32_t N = a->N, D = a->D;
     std::vector<uint32_t> an, bn, emask, eoff;
-    std::vector<int64_t> au, offu;
+    std::vector<int64_t> offu;
+    std::vector<MemoAGroup> grp;
+    std::vector<KeyPlan> kplan;
+    std::vector<int32_t> plan_of;  // per node: its key plan in this step, -1 if none yet
     emask.assign((size_t)nq * a->E, 0u);
     eoff.assign((size_t)nq * a->E, 0u);
     const std::vector<uint32_t> &child_off = a->h_child_off, &child = a->h_child;
     m->a_lvl.assign(nq, std::vector<int64_t>(D + 1, 0));
     m->u_lvl = m->a_lvl;
     m->b_lvl = m->a_lvl;
+    m->g_lvl = m->a_lvl;
     m->floor0.assign(nq, std::vector<uint8_t>(D, 0));
+    std::vector<std::pair<int, uint32_t>> al;  // (key width, node) of one level's tier A
     for (int j = 0; j < nq; ++j) {
         const uint64_t jmask = j == 0 ? 0ull : (j >= 64 ? ~0ull : ((1ull << j) - 1ull));
-        // a node is memoised when its key space is at least 2^MEMO_MARGIN times smaller than the
-        // groups it would otherwise be evaluated for (early steps have at most V 2^j groups)
+        // a node is memoised when its key has at most t bits: early steps have at most V 2^j
+        // groups, so t = j - MEMO_MARGIN keeps the key space 2^MEMO_MARGIN times smaller; later
+        // steps stop at the cap, about half the shots per vector
         const int t = std::min(cap, std::max(0, j - MEMO_MARGIN));
         m->a_base.push_back((int64_t)an.size());
         m->b_base.push_back((int64_t)bn.size());
+        m->g_base.push_back((int64_t)grp.size());
+        m->kp_base.push_back((int64_t)kplan.size());
+        plan_of.assign(N, -1);
         m->offu_base.push_back((int64_t)offu.size());
         const size_t ob = offu.size();
         offu.resize(ob + N, -1);
         int64_t units = 0;
         double abytes = 0.0, bbytes = 0.0;
         for (uint32_t L = 0; L < D; ++L) {
+            // leaves are always memoised (at most one key bit, V * 2 slots): the memoised pass
+            // binds no leaf per group, so every leaf a per-group node reads must be here
+            al.clear();
             for (uint32_t n = a->level_off[L]; n < a->level_off[L + 1]; ++n) {
                 const int k = __builtin_popcountll(a->sigma[n] & jmask);
+                if (k <= t || n < a->n_leaves) al.push_back({k, n});
+            }
+            // widest keys first; within a width, node order
+            std::stable_sort(al.begin(), al.end(), [](const std::pair<int, uint32_t> &x,
+                                                      const std::pair<int, uint32_t> &y) { return x.first > y.first; });
+            const int64_t u0 = units, i0 = (int64_t)an.size();
+            for (size_t i = 0; i < al.size(); ++i) {
+                const int k = al[i].first;
+                const uint32_t n = al[i].second;
+                if (i == 0 || k != al[i - 1].first)
+                    grp.push_back(MemoAGroup{(uint32_t)(units - u0), (uint32_t)((int64_t)an.size() - i0), (uint32_t)k});
+                offu[ob + n] = units;
+                an.push_back(n);
+                units += 1ll << k;
                 const double deg = (double)(child_off[n + 1] - child_off[n]);
-                // leaves are always memoised (at most one key bit, V * 2 slots): the memoised pass
-                // binds no leaf per group, so every leaf a per-group node reads must be here
-                if (k <= t || n < a->n_leaves) {
-                    offu[ob + n] = units;
-                    an.push_back(n);
-                    au.push_back(units);
-                    units += 1ll << k;
-                    abytes += (double)(1ll << k) * (deg + 1.0);
-                    const uint64_t rn = a->sigma[n] & jmask;
-                    for (uint32_t e = child_off[n]; e < child_off[n + 1]; ++e) {
-                        const uint64_t rc = a->sigma[child[e]] & jmask;
-                        uint32_t me = 0;  // positions of rc's qubits among rn's, in qubit order
-                        int pos = 0;
-                        for (uint64_t r = rn; r; r &= r - 1, ++pos)
-                            if (rc & (r & (~r + 1))) me |= 1u << pos;
-                        emask[(size_t)j * a->E + e] = me;
-                    }
-                } else {
-                    bn.push_back(n);
-                    bbytes += deg + 1.0;
-                    for (uint32_t e = child_off[n]; e < child_off[n + 1]; ++e) {
-                        const int64_t oc = offu[ob + child[e]];
-                        if (oc >= 0) {
-                            m->floor0[j][L] = 1;
-                            eoff[(size_t)j * a->E + e] = (uint32_t)(oc + 1);
+                abytes += (double)(1ll << k) * (deg + 1.0);
+                const uint64_t rn = a->sigma[n] & jmask;
+                for (uint32_t e = child_off[n]; e < child_off[n + 1]; ++e) {
+                    const uint64_t rc = a->sigma[child[e]] & jmask;
+                    uint32_t me = 0;  // positions of rc's qubits among rn's, in qubit order
+                    int pos = 0;
+                    for (uint64_t r = rn; r; r &= r - 1, ++pos)
+                        if (rc & (r & (~r + 1))) me |= 1u << pos;
+                    emask[(size_t)j * a->E + e] = me;
+                }
+            }
+            for (uint32_t n = a->level_off[L]; n < a->level_off[L + 1]; ++n) {
+                if (offu[ob + n] >= 0) continue;
+                bn.push_back(n);
+                bbytes += (double)(child_off[n + 1] - child_off[n]) + 1.0;
+                for (uint32_t e = child_off[n]; e < child_off[n + 1]; ++e) {
+                    const uint32_t c = child[e];
+                    const int64_t oc = offu[ob + c];
+                    if (oc >= 0) {
+                        m->floor0[j][L] = 1;
+                        if (plan_of[c] < 0) {
+                            KeyPlan kp{};
+                            kp.off = oc;
+                            kp.m = a->sigma[c] & jmask;
+                            compress_masks(kp.m, kp.mv);
+                            kp.k = (uint32_t)__builtin_popcountll(kp.m);
+                            plan_of[c] = (int32_t)((int64_t)kplan.size() - m->kp_base[j]);
+                            kplan.push_back(kp);
                         }
+                        eoff[(size_t)j * a->E + e] = (uint32_t)plan_of[c] + 1u;
                     }
                 }
             }
             m->a_lvl[j][L + 1] = (int64_t)an.size() - m->a_base[j];
             m->u_lvl[j][L + 1] = units;
             m->b_lvl[j][L + 1] = (int64_t)bn.size() - m->b_base[j];
+            m->g_lvl[j][L + 1] = (int64_t)grp.size() - m->g_base[j];
         }
         m->a_bytes_slot.push_back(abytes * (double)a->elem());
         m->b_bytes_col.push_back(bbytes * (double)a->elem());
@@ -1961,13 +2052,14 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
     }
     int64_t dummy = 0;
     if ((*st = upload(&m->d_a_nodes, an.data(), an.size(), dummy)) ||
-        (*st = upload(&m->d_a_ustart, au.data(), au.size(), dummy)) ||
+        (*st = upload(&m->d_a_grp, grp.data(), grp.size(), dummy)) ||
         (*st = upload(&m->d_b_nodes, bn.data(), bn.size(), dummy)) ||
         (*st = upload(&m->d_offu, offu.data(), offu.size(), dummy)) ||
         (*st = upload(&m->d_emask, emask.data(), emask.size(), dummy)) ||
-        (*st = upload(&m->d_eoff, eoff.data(), eoff.size(), dummy))) {
-        cudaFree(m->d_a_nodes); cudaFree(m->d_a_ustart); cudaFree(m->d_b_nodes); cudaFree(m->d_offu);
-        cudaFree(m->d_emask); cudaFree(m->d_eoff);
+        (*st = upload(&m->d_eoff, eoff.data(), eoff.size(), dummy)) ||
+        (*st = upload(&m->d_kplan, kplan.data(), kplan.size(), dummy))) {
+        cudaFree(m->d_a_nodes); cudaFree(m->d_a_grp); cudaFree(m->d_b_nodes); cudaFree(m->d_offu);
+        cudaFree(m->d_emask); cudaFree(m->d_eoff); cudaFree(m->d_kplan);
         delete m;
         return nullptr;
     }
@@ -1986,9 +2078,12 @@ static void launch_memoA_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
         if (i1 == i0) continue;
         const int64_t u0 = m->u_lvl[j][L], u1 = m->u_lvl[j][L + 1];
         const uint32_t *nodes = m->d_a_nodes + m->a_base[j] + i0;
-        const int64_t *us = m->d_a_ustart + m->a_base[j] + i0;
-        if (a->prec == 32) memoA_level<float2><<<g, TPB, 0, s>>>(d, a->d_mdesc, nodes, us, i1 - i0, u0, u1);
-        else memoA_level<double2><<<g, TPB, 0, s>>>(d, a->d_mdesc, nodes, us, i1 - i0, u0, u1);
+        const MemoAGroup *gp = m->d_a_grp + m->g_base[j] + m->g_lvl[j][L];
+        const int ng = (int)(m->g_lvl[j][L + 1] - m->g_lvl[j][L]);
+        if (a->prec == 32)
+            memoA_level<float2><<<g, TPB, 0, s>>>(d, a->d_mdesc, nodes, gp, ng, u0, (uint32_t)(u1 - u0));
+        else
+            memoA_level<double2><<<g, TPB, 0, s>>>(d, a->d_mdesc, nodes, gp, ng, u0, (uint32_t)(u1 - u0));
     }
 }
 static int64_t memoA_launches(const qkc_ac *a, const qkc_ac::MemoMeta *m, int j) {
@@ -2075,17 +2170,19 @@ static qkc_status memo_pass(qkc_ac *a, qkc_ac::MemoMeta *m, int j, int clamp, in
     cudaGraphExec_t gA, gB;
     if ((st = memo_graph(a, m, j, false, &gA)) || (st = memo_graph(a, m, j, true, &gB))) return st;
     MemoDesc md{n_vec,    j,         clamp, jmask, a->d_pv, a->vec_cap, a->d_VA, m->d_offu + m->offu_base[j],
-                a->d_sigma, m->d_emask + (size_t)j * a->E, m->d_eoff + (size_t)j * a->E};
+                a->d_sigma, m->d_emask + (size_t)j * a->E, m->d_eoff + (size_t)j * a->E,
+                m->d_kplan + m->kp_base[j]};
     set_memo_desc<<<1, 1, 0, s>>>(a->d_mdesc, md);
     ++a->launches;
-    const size_t ri = a->recs.size();
-    if ((st = rec_begin(a, 2, n_active, 0, bound, s))) return st;
-    if (ri < a->recs.size()) {
-        a->recs[ri].fixed_bytes = (double)n_vec * m->a_bytes_slot[j];
-        a->recs[ri].col_bytes = m->b_bytes_col[j];
-    }
+    const size_t ra = a->recs.size();
+    if ((st = rec_begin(a, 3, nullptr, 0, 0, s))) return st;
+    if (ra < a->recs.size()) a->recs[ra].fixed_bytes = (double)n_vec * m->a_bytes_slot[j];
     QKC_CUDA(cudaGraphLaunch(gA, s));  // tier A: once per step
     a->launches += memoA_launches(a, m, j);
+    if ((st = rec_end(a, ra, s))) return st;
+    const size_t ri = a->recs.size();
+    if ((st = rec_begin(a, 2, n_active, 0, bound, s))) return st;
+    if (ri < a->recs.size()) a->recs[ri].col_bytes = m->b_bytes_col[j];
     const int64_t pitch = a->tile;
     for (int64_t c0 = 0; c0 < bound; c0 += pitch) {  // tier B and the roots, per tile of groups
         const int64_t nc = std::min<int64_t>(pitch, bound - c0);
@@ -2128,7 +2225,7 @@ extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t
     // tile sized for the largest step (bounded by the sample count), roots for every group
     if ((st = ensure_tile(a, std::max(n_samp, n_vec))) || (st = ensure_roots(a, std::max(n_samp, n_vec)))) return st;
     // memoised passes: the largest cap (bits per node key) whose tier-A slots fit the budget
-    // (the caller's, else 15% of the device memory and half of what is free); if the slots
+    // (the caller's, else 40% of the device memory and 60% of what is free); if the slots
     // cannot be allocated, smaller caps, then the per-group sampler
     qkc_ac::MemoMeta *meta = nullptr;
     if (a->sampler >= 1 && nq <= 63) {
@@ -2142,9 +2239,9 @@ extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t
         size_t fr = 0, tot = 0;
         if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); fr = 0; }
         double budget = a->memo_budget > 0 ? (double)a->memo_budget
-                                            : std::min(0.15 * (double)a->ctx->total_mem,
-                                                       0.5 * (double)(fr + (size_t)a->va_bytes));
-        for (int cap = ks - MEMO_MARGIN; cap >= 1 && !meta; --cap) {
+                                            : std::min(0.40 * (double)a->ctx->total_mem,
+                                                       0.6 * (double)(fr + (size_t)a->va_bytes));
+        for (int cap = ks - 1; cap >= 1 && !meta; --cap) {
             qkc_ac::MemoMeta *m = memo_meta(a, cap, &st);
             if (st) return st;
             if (!m) continue;
@@ -2167,12 +2264,12 @@ extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t
     if (meta && a->sampler == 1) {
         // keep the memoised passes only when they are estimated cheaper than evaluating every
         // node per group: bytes weighted by the measured cost per byte of each kernel kind
-        // (per-slot tier-A evaluation ~8x, per-group tier-B ~2x the plain upward pass)
+        // (per-slot tier-A evaluation ~3x, per-group tier-B ~2x the plain upward pass)
         double plain = 0.0, memo = 0.0, groups = (double)n_vec;
         const double per_col = (double)a->elem() * ((double)a->E + (double)(a->N - a->n_leaves));
         for (int j = 0; j < nq; ++j) {
             plain += groups * per_col;
-            memo += 8.0 * (double)n_vec * meta->a_bytes_slot[j] + 2.0 * groups * meta->b_bytes_col[j];
+            memo += 3.0 * (double)n_vec * meta->a_bytes_slot[j] + 2.0 * groups * meta->b_bytes_col[j];
             groups = std::min(2.0 * groups, (double)live);
         }
         if (memo >= plain) meta = nullptr;
@@ -2328,11 +2425,16 @@ extern "C" qkc_status qkc_get_stats(qkc_ac *a, qkc_stats *o) {
             float ms = 0.f;
             QKC_CUDA(cudaEventSynchronize(a->recs[i].e1));
             QKC_CUDA(cudaEventElapsedTime(&ms, a->recs[i].e0, a->recs[i].e1));
-            if (a->recs[i].kind == 2) {  // memoised sampling pass: tier-A slots + tier-B columns
+            if (a->recs[i].kind == 2) {  // memoised sampling pass, tier B: per group column
                 o->memo_passes += 1;
                 o->memo_columns += cols[i];
                 o->memo_ms += ms;
-                o->memo_bytes += a->recs[i].fixed_bytes + a->recs[i].col_bytes * (double)cols[i];
+                o->memo_bytes += a->recs[i].col_bytes * (double)cols[i];
+            } else if (a->recs[i].kind == 3) {  // memoised sampling pass, tier A: per slot
+                o->memo_ms += ms;
+                o->memo_bytes += a->recs[i].fixed_bytes;
+                o->memo_a_ms += ms;
+                o->memo_a_bytes += a->recs[i].fixed_bytes;
             } else if (a->recs[i].kind == 0) {
                 o->up_passes += 1;
                 o->up_columns += cols[i];

@@ -218,6 +218,62 @@ def hardware_efficient_ansatz(n: int, layers: int, noise=None, name="") -> Circu
     return c
 
 
+def grid_edges(rows: int, cols: int):
+    """Nearest-neighbour couplings of a rows x cols grid, qubit r * cols + c, sorted (i < j)."""
+    e = []
+    for r in range(rows):
+        for c in range(cols):
+            q = r * cols + c
+            if c + 1 < cols:
+                e.append((q, q + 1))
+            if r + 1 < rows:
+                e.append((q, q + cols))
+    return sorted(e)
+
+
+def vqe_ising_2d(rows: int, cols: int, layers: int, noise=None, name="") -> Circuit:
+    """Variational ansatz for the 2D Ising model (the paper's VQE workload: a qubit per grid
+    point, two-qubit gates along the couplings): H on every qubit, then per layer RY(theta_{l,q})
+    on every qubit and ZZ(phi_l) = CNOT RZ(phi_l) CNOT on every grid coupling.  Angle slots:
+    per layer n qubit angles then one coupling angle."""
+    n = rows * cols
+    edges = grid_edges(rows, cols)
+    c = Circuit(n, layers * (n + 1), name=name or f"vqe_ising_{rows}x{cols}_l{layers}")
+    for q in range(n):
+        c.add("H", q)
+        _noise_after(c, "H", (q,), noise)
+    for layer in range(layers):
+        base = layer * (n + 1)
+        for q in range(n):
+            c.add("RY", q, angle=base + q)
+            _noise_after(c, "RY", (q,), noise)
+        for (i, j) in edges:
+            c.add("CNOT", (i, j))
+            _noise_after(c, "CNOT", (i, j), noise)
+            c.add("RZ", j, angle=base + n)
+            _noise_after(c, "RZ", (j,), noise)
+            c.add("CNOT", (i, j))
+            _noise_after(c, "CNOT", (i, j), noise)
+    return c
+
+
+def ising_hamiltonian(rows: int, cols: int, J: float = 1.0, h: float = 0.5):
+    """H = J sum_<ij> Z_i Z_j + h sum_i Z_i on the grid, as Z-string supports and coefficients."""
+    n = rows * cols
+    sup, coef = [], []
+    for (i, j) in grid_edges(rows, cols):
+        row = np.zeros(n, dtype=bool)
+        row[i] = row[j] = True
+        sup.append(row)
+        coef.append(J)
+    for q in range(n):
+        row = np.zeros(n, dtype=bool)
+        row[q] = True
+        sup.append(row)
+        coef.append(h)
+    return np.array(sup), np.array(coef, dtype=np.float64)
+
+
 def random_circuit(n: int, n_ops: int, seed: int, noise_prob: float = 0.3, n_angles: int = 3) -> Circuit:
     """Random small noisy circuit over every gate and channel kind (test input)."""
     rng = SplitMix(seed)
@@ -313,6 +369,10 @@ def workload(name: str):
         return hardware_efficient_ansatz(16, 6, NOISE_CFG3, name=name)
     if name == "qaoa32_3reg_p1_ideal":
         return qaoa_maxcut(32, random_regular_graph(32, 3, seed=5), 1, None, name=name)
+    if name == "vqe_ising_3x3_noisy":
+        return vqe_ising_2d(3, 3, 2, [("DEP1", 0.005, "all")], name=name)
+    if name == "vqe_ising_5x5_ideal":
+        return vqe_ising_2d(5, 5, 1, None, name=name)
     if name.startswith("serve_qaoa"):
         # serve_qaoa{n}_p{p}
         body = name[len("serve_qaoa"):]

@@ -212,3 +212,20 @@ def test_ctx_create_fails_cleanly_without_gpu():
     with pytest.raises(N.QKCError) as e:
         N.Context(0)
     assert e.value.status in (1, 4)
+
+
+def test_vqe_ising_density_ac_equals_density_matrix():
+    """The 2D-Ising VQE family (3x3 grid, 2 layers, depolarising 0.5% after every gate):
+    outcome probabilities and <H> through the compiled density AC vs the density matrix."""
+    c = I.workload("vqe_ising_3x3_noisy")
+    sup, coef = I.ising_hamiltonian(3, 3)
+    r = R.ACRef(compile_ac(c, kind=1))
+    for a in I.uniform_angles(2, c.n_angles, seed=23):
+        P = Q.probabilities(c, a)
+        rng = I.SplitMix(23)
+        for _ in range(12):
+            x = rng.randint(2 ** 9)
+            assert abs(r.up(a, outcome_ev(x, 9)) - P[x]) < 1e-13
+        val = sum(w * Q.z_expectation(P, s) for s, w in zip(sup, coef))
+        got = sum(r.gradient(a, [-2 if b else -1 for b in s], w)[0] for s, w in zip(sup, coef))
+        assert abs(got - val) < 1e-12

@@ -479,3 +479,26 @@ def test_memoised_sampler_equals_per_group_sampler(cuda_ctx, prec, name):
         for v in range(V):
             ref = Q.chain_rule_samples(Q.probabilities(c, angs[v]), int(I.vector_seeds(V, 17)[v]), int(sh[v]))
             assert (outs[1][v, :sh[v]].astype(np.uint64) != ref).sum() <= (0 if prec == 64 else 2)
+
+
+def test_vqe_ising_gradient(cuda_ctx):
+    """2D-Ising VQE (3x3 grid, 2 layers, depolarising 0.5%): <H> of two vectors and the gradient in
+    four of the 20 angles (a qubit angle and the coupling angle of each layer) in FP32 against the
+    density-matrix oracle's forward-mode derivative."""
+    c = I.workload("vqe_ising_3x3_noisy")
+    sup, coef = I.ising_hamiltonian(3, 3)
+    V, T = 2, len(coef)
+    angs = I.uniform_angles(V, c.n_angles, seed=29)
+    ac = N().load_ac(cuda_ctx, compiled("vqe_ising_3x3_noisy"), precision=32)
+    N().set_params(ac, t(angs))
+    ev = np.array([[-2 if b else -1 for b in sup[tt]] for _ in range(V) for tt in range(T)], dtype=np.int8)
+    cv = np.repeat(np.arange(V, dtype=np.int32), T)
+    val, grad = N().gradient(ac, t(cv), t(ev), t(np.tile(coef, V)), V)
+    val, grad = val.cpu().numpy(), grad.cpu().numpy()
+    scale = np.abs(coef).sum()
+    slots = [4, 9, 13, 19]
+    for v in range(V):
+        rv, rg = Q.hamiltonian_value_and_gradient(c, angs[v], sup, coef, angle_slots=slots if v == 0 else [])
+        assert abs(val[v] - rv) < 1e-5 * scale
+        if v == 0:
+            assert np.abs(grad[v][slots] - rg[slots]).max() < 1e-5 * scale * 10
