@@ -69,6 +69,7 @@ enum : uint8_t { OP_IND = 0, OP_PARAM = 1, OP_CONST = 2, OP_ADD = 3, OP_MUL = 4 
 constexpr int NB = 8;          // nodes per warp item
 constexpr int TPB = 256;       // threads per block
 constexpr int OBS_EMPTY = -1000;
+constexpr int MEMO_APLANS = 7;  // log2 of the compress plans per step for scattered tier-A key masks
 constexpr int MEMO_MARGIN = 2;  // early steps: memoise a node when its key space is >= 4x smaller than V 2^j
 
 // ------------------------------------------------------------------ device helpers
@@ -556,9 +557,11 @@ struct MemoDesc {
     void *VA;             // tier-A values
     const int64_t *offu;  // per node: start of its tier-A block in units (x V slots), -1 for tier B
     const uint64_t *sigma;
-    const uint32_t *emask;  // per child edge of a tier-A node: the child's key bits in the parent's key
+    const uint32_t *emask;  // per child edge of a tier-A node: the child's key bits in the parent's key,
+                            // or (bit 31 set) the index of a key plan in aplan for a scattered mask
     const uint32_t *eoff;   // per child edge of a tier-B node: 1 + the child's key plan, 0 if tier B
     const KeyPlan *kplan;  // per tier-A child of a tier-B node (this step)
+    const KeyPlan *aplan;  // per distinct scattered child-key mask of tier-A parents (this step)
 };
 
 __device__ __forceinline__ uint32_t plan_key(const KeyPlan *kp, uint64_t x, bool narrow) {
@@ -663,8 +666,14 @@ __global__ void __launch_bounds__(TPB) memoA_level(DevAC ac, const MemoDesc *mdp
                     const uint32_t c = ac.child[e];
                     const uint32_t me = md.emask[e];  // the child's key bits inside this node's key
                     int64_t cs;
-                    if (me == full) cs = local;  // same key space: same slot layout
-                    else cs = (vec << __popc(me)) | (int64_t)extract_bits(key, me);
+                    if (me == full) {
+                        cs = local;  // same key space: same slot layout
+                    } else if (me & 0x80000000u) {
+                        const KeyPlan *kp = md.aplan + (me & 0x7fffffffu);
+                        cs = (vec << (int)__ldg(&kp->k)) | (int64_t)plan_key(kp, key, true);
+                    } else {
+                        cs = (vec << __popc(me)) | (int64_t)extract_bits(key, me);
+                    }
                     const C v = VA[md.V * md.offu[c] + cs];
                     if (o == OP_MUL) {
                         C m;
@@ -1199,7 +1208,8 @@ struct qkc_ac {
         uint32_t *d_emask = nullptr;    // [step][edge]: a child's key bits inside its tier-A parent's key
         uint32_t *d_eoff = nullptr;     // [step][edge]: 1 + a tier-A child's key plan, for tier-B parents
         KeyPlan *d_kplan = nullptr;     // key plans of the tier-A children of tier-B nodes, per step
-        std::vector<int64_t> kp_base;   // per step: first key plan
+        KeyPlan *d_aplan = nullptr;     // key plans of scattered child-key masks of tier-A nodes, per step
+        std::vector<int64_t> kp_base, ap_base;  // per step: first key plan of each kind
         std::vector<GraphSlot> gA, gB;  // captured launch sequences per step
     };
     std::vector<MemoMeta *> memo;  // indexed by cap
@@ -1289,7 +1299,7 @@ extern "C" void qkc_free_ac(qkc_ac *a) {
     for (auto *m : a->memo) {
         if (!m) continue;
         cudaFree(m->d_a_nodes); cudaFree(m->d_b_nodes); cudaFree(m->d_a_grp); cudaFree(m->d_offu);
-        cudaFree(m->d_emask); cudaFree(m->d_eoff); cudaFree(m->d_kplan);
+        cudaFree(m->d_emask); cudaFree(m->d_eoff); cudaFree(m->d_kplan); cudaFree(m->d_aplan);
         for (auto &g : m->gA) if (g.exec) cudaGraphExecDestroy(g.exec);
         for (auto &g : m->gB) if (g.exec) cudaGraphExecDestroy(g.exec);
         delete m;
@@ -1955,7 +1965,7 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
     std::vector<uint32_t> an, bn, emask, eoff;
     std::vector<int64_t> offu;
     std::vector<MemoAGroup> grp;
-    std::vector<KeyPlan> kplan;
+    std::vector<KeyPlan> kplan, aplan;
     std::vector<int32_t> plan_of;  // per node: its key plan in this step, -1 if none yet
     emask.assign((size_t)nq * a->E, 0u);
     eoff.assign((size_t)nq * a->E, 0u);
@@ -1976,6 +1986,7 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
         m->b_base.push_back((int64_t)bn.size());
         m->g_base.push_back((int64_t)grp.size());
         m->kp_base.push_back((int64_t)kplan.size());
+        m->ap_base.push_back((int64_t)aplan.size());
         plan_of.assign(N, -1);
         m->offu_base.push_back((int64_t)offu.size());
         const size_t ob = offu.size();
@@ -2011,6 +2022,21 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
                     int pos = 0;
                     for (uint64_t r = rn; r; r &= r - 1, ++pos)
                         if (rc & (r & (~r + 1))) me |= 1u << pos;
+                    const uint32_t run = me ? me >> __builtin_ctz(me) : 0u;
+                    if (run & (run + 1u)) {  // scattered: a compress plan (at most 2^MEMO_APLANS per step)
+                        int64_t idx = -1;
+                        for (int64_t i = m->ap_base[j]; i < (int64_t)aplan.size() && idx < 0; ++i)
+                            if (aplan[i].m == me) idx = i - m->ap_base[j];
+                        if (idx < 0 && (int64_t)aplan.size() - m->ap_base[j] < (1 << MEMO_APLANS)) {
+                            KeyPlan kp{};
+                            kp.m = me;
+                            compress_masks(me, kp.mv);
+                            kp.k = (uint32_t)__builtin_popcount(me);
+                            idx = (int64_t)aplan.size() - m->ap_base[j];
+                            aplan.push_back(kp);
+                        }
+                        if (idx >= 0) me = 0x80000000u | (uint32_t)idx;
+                    }
                     emask[(size_t)j * a->E + e] = me;
                 }
             }
@@ -2057,9 +2083,10 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
         (*st = upload(&m->d_offu, offu.data(), offu.size(), dummy)) ||
         (*st = upload(&m->d_emask, emask.data(), emask.size(), dummy)) ||
         (*st = upload(&m->d_eoff, eoff.data(), eoff.size(), dummy)) ||
-        (*st = upload(&m->d_kplan, kplan.data(), kplan.size(), dummy))) {
+        (*st = upload(&m->d_kplan, kplan.data(), kplan.size(), dummy)) ||
+        (*st = upload(&m->d_aplan, aplan.data(), aplan.size(), dummy))) {
         cudaFree(m->d_a_nodes); cudaFree(m->d_a_grp); cudaFree(m->d_b_nodes); cudaFree(m->d_offu);
-        cudaFree(m->d_emask); cudaFree(m->d_eoff); cudaFree(m->d_kplan);
+        cudaFree(m->d_emask); cudaFree(m->d_eoff); cudaFree(m->d_kplan); cudaFree(m->d_aplan);
         delete m;
         return nullptr;
     }
@@ -2171,7 +2198,7 @@ static qkc_status memo_pass(qkc_ac *a, qkc_ac::MemoMeta *m, int j, int clamp, in
     if ((st = memo_graph(a, m, j, false, &gA)) || (st = memo_graph(a, m, j, true, &gB))) return st;
     MemoDesc md{n_vec,    j,         clamp, jmask, a->d_pv, a->vec_cap, a->d_VA, m->d_offu + m->offu_base[j],
                 a->d_sigma, m->d_emask + (size_t)j * a->E, m->d_eoff + (size_t)j * a->E,
-                m->d_kplan + m->kp_base[j]};
+                m->d_kplan + m->kp_base[j], m->d_aplan + m->ap_base[j]};
     set_memo_desc<<<1, 1, 0, s>>>(a->d_mdesc, md);
     ++a->launches;
     const size_t ra = a->recs.size();
