@@ -69,6 +69,7 @@ enum : uint8_t { OP_IND = 0, OP_PARAM = 1, OP_CONST = 2, OP_ADD = 3, OP_MUL = 4 
 constexpr int NB = 8;          // nodes per warp item
 constexpr int TPB = 256;       // threads per block
 constexpr int OBS_EMPTY = -1000;
+constexpr int MEMO_BKEYS = 32;  // per step, the distinct tier-A child supports whose group keys are tabled
 constexpr int MEMO_APLANS = 7;  // log2 of the compress plans per step for scattered tier-A key masks
 constexpr int MEMO_MARGIN = 2;  // early steps: memoise a node when its key space is >= 4x smaller than V 2^j
 
@@ -536,7 +537,8 @@ struct KeyPlan {
     int64_t off;     // the child's tier-A block (units)
     uint64_t m;      // the child's support among the qubits < j
     uint64_t mv[6];  // compress masks of m
-    uint32_t k, pad; // |m|
+    uint32_t k;      // |m|
+    int32_t mid;     // row of the step's group-key table holding this support's keys, -1 if none
 };
 
 // At sampling step j a group's evidence fixes qubits < j to its prefix and qubit j to 0, so a
@@ -562,6 +564,10 @@ struct MemoDesc {
     const uint32_t *eoff;   // per child edge of a tier-B node: 1 + the child's key plan, 0 if tier B
     const KeyPlan *kplan;  // per tier-A child of a tier-B node (this step)
     const KeyPlan *aplan;  // per distinct scattered child-key mask of tier-A parents (this step)
+    const KeyPlan *bplan;  // the step's tabled supports (nbm of them) ...
+    int32_t nbm;
+    uint32_t *keys;        // ... and their keys per group column of the tile: keys[row * kpitch + column]
+    int64_t kpitch;
 };
 
 __device__ __forceinline__ uint32_t plan_key(const KeyPlan *kp, uint64_t x, bool narrow) {
@@ -697,6 +703,20 @@ __global__ void __launch_bounds__(TPB) memoA_level(DevAC ac, const MemoDesc *mdp
     }
 }
 
+// The group-key table of one tile: for every group column and tabled support, the column's
+// prefix bits on that support, packed (read by tier-B nodes for their tier-A children).  Only
+// columns below the tile's group count are written.
+__global__ void memo_keys(const PassDesc *pd, const MemoDesc *mdp) {
+    const int64_t ncols = desc_cols(*pd);
+    const int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (col >= ncols) return;
+    const MemoDesc md = *mdp;
+    const int64_t g = pd->col0 + col;
+    const uint64_t pre = md.j ? __brevll(pd->es.prefix[g] << (64 - md.j)) : 0ull;  // qubit order
+    const bool narrow = md.j <= 32;
+    for (int r = 0; r < md.nbm; ++r) md.keys[(int64_t)r * md.kpitch + col] = plan_key(md.bplan + r, pre, narrow);
+}
+
 // One level of tier B (FP32): as up_level_f32 over a node list, tier-A children read by key.
 __global__ void __launch_bounds__(TPB, 4) memoB_level_f32(DevAC ac, LevelArgs a, const uint32_t *nodes, int64_t count,
                                                         const PassDesc *pd, const MemoDesc *mdp,
@@ -746,9 +766,19 @@ __global__ void __launch_bounds__(TPB, 4) memoB_level_f32(DevAC ac, LevelArgs a,
             } else {
                 const KeyPlan *kp = md.kplan + off;
                 const int kc = (int)__ldg(&kp->k);
+                const int mid = __ldg(&kp->mid);
                 const int64_t base = md.V * __ldg(&kp->off);
-                v0 = VA[base + ((vec0 << kc) | (int64_t)plan_key(kp, pre0, narrow))];
-                v1 = VA[base + ((vec1 << kc) | (int64_t)plan_key(kp, pre1, narrow))];
+                uint32_t key0, key1;
+                if (mid >= 0) {  // tabled: this column pair's keys (col is even, the pitch a multiple of 64)
+                    const uint2 kk = *reinterpret_cast<const uint2 *>(md.keys + (int64_t)mid * md.kpitch + col);
+                    key0 = kk.x;
+                    key1 = two ? kk.y : kk.x;  // the table holds no key past the last column
+                } else {
+                    key0 = plan_key(kp, pre0, narrow);
+                    key1 = plan_key(kp, pre1, narrow);
+                }
+                v0 = VA[base + ((vec0 << kc) | (int64_t)key0)];
+                v1 = VA[base + ((vec1 << kc) | (int64_t)key1)];
                 s0 = s1 = 0;
             }
         };
@@ -823,7 +853,9 @@ __global__ void __launch_bounds__(TPB) memoB_level_f64(DevAC ac, LevelArgs a, co
                     v = __ldg(V + (int64_t)c * a.pitch + col);
                 } else {
                     const KeyPlan *kp = md.kplan + off;
-                    v = VA[md.V * __ldg(&kp->off) + ((vec << (int)__ldg(&kp->k)) | (int64_t)plan_key(kp, pre, narrow))];
+                    const int mid = __ldg(&kp->mid);
+                    const uint32_t key = mid >= 0 ? md.keys[(int64_t)mid * md.kpitch + col] : plan_key(kp, pre, narrow);
+                    v = VA[md.V * __ldg(&kp->off) + ((vec << (int)__ldg(&kp->k)) | (int64_t)key)];
                 }
                 if (o == OP_MUL) r = cmul(r, v);
                 else { r.x += v.x; r.y += v.y; }
@@ -1177,6 +1209,7 @@ struct qkc_ac {
     void *d_A = nullptr;      // [N][tile], allocated by the first downward pass
     bool adj_ok = false;
     int *d_S = nullptr, *d_obs = nullptr;  // [D][tile]
+    uint32_t *d_keys = nullptr;            // [MEMO_BKEYS][tile]: the memoised sampler's group-key table
     double2 *d_root = nullptr;  // [root_cap]
     int64_t root_cap = 0;
     // sampling scratch
@@ -1210,6 +1243,8 @@ struct qkc_ac {
         KeyPlan *d_kplan = nullptr;     // key plans of the tier-A children of tier-B nodes, per step
         KeyPlan *d_aplan = nullptr;     // key plans of scattered child-key masks of tier-A nodes, per step
         std::vector<int64_t> kp_base, ap_base;  // per step: first key plan of each kind
+        KeyPlan *d_bplan = nullptr;     // per step: the tabled supports (group-key table rows)
+        std::vector<int64_t> bp_base, bp_cnt;
         std::vector<GraphSlot> gA, gB;  // captured launch sequences per step
     };
     std::vector<MemoMeta *> memo;  // indexed by cap
@@ -1266,6 +1301,7 @@ static void free_scratch(qkc_ac *a) {
     cudaFree(a->d_A); a->d_A = nullptr; a->adj_ok = false;
     cudaFree(a->d_S); a->d_S = nullptr;
     cudaFree(a->d_obs); a->d_obs = nullptr;
+    cudaFree(a->d_keys); a->d_keys = nullptr;
     cudaFree(a->d_root); a->d_root = nullptr;
     cudaFree(a->d_s_group); cudaFree(a->d_flag); cudaFree(a->d_pos); cudaFree(a->d_bsum);
     cudaFree(a->d_gcount); cudaFree(a->d_s_bits);
@@ -1299,7 +1335,7 @@ extern "C" void qkc_free_ac(qkc_ac *a) {
     for (auto *m : a->memo) {
         if (!m) continue;
         cudaFree(m->d_a_nodes); cudaFree(m->d_b_nodes); cudaFree(m->d_a_grp); cudaFree(m->d_offu);
-        cudaFree(m->d_emask); cudaFree(m->d_eoff); cudaFree(m->d_kplan); cudaFree(m->d_aplan);
+        cudaFree(m->d_emask); cudaFree(m->d_eoff); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
         for (auto &g : m->gA) if (g.exec) cudaGraphExecDestroy(g.exec);
         for (auto &g : m->gB) if (g.exec) cudaGraphExecDestroy(g.exec);
         delete m;
@@ -1541,7 +1577,7 @@ static qkc_status ensure_vectors(qkc_ac *a, int64_t nvec) {
 static qkc_status ensure_tile(qkc_ac *a, int64_t cols) {
     int64_t want = (cols + 63) / 64 * 64;
     if (want < 64) want = 64;
-    const int64_t per_col = (int64_t)a->N * (int64_t)a->elem() + 8LL * a->D;
+    const int64_t per_col = (int64_t)a->N * (int64_t)a->elem() + 8LL * a->D + 4LL * MEMO_BKEYS;
     int64_t cap = (int64_t)((double)a->ctx->total_mem * 0.25) / std::max<int64_t>(1, per_col);
     if (const char *env = std::getenv("QKC_MAX_TILE_COLUMNS")) {  // smaller tiles (tests of the tiled path)
         const long long lim = std::atoll(env);
@@ -1553,14 +1589,15 @@ static qkc_status ensure_tile(qkc_ac *a, int64_t cols) {
     want = std::min(want, cap);
     if (want <= a->tile) return QKC_OK;
     QKC_CUDA(cudaDeviceSynchronize());
-    cudaFree(a->d_V); cudaFree(a->d_A); cudaFree(a->d_S); cudaFree(a->d_obs);
-    a->d_V = a->d_A = nullptr; a->d_S = a->d_obs = nullptr; a->tile = 0; a->adj_ok = false;
+    cudaFree(a->d_V); cudaFree(a->d_A); cudaFree(a->d_S); cudaFree(a->d_obs); cudaFree(a->d_keys);
+    a->d_V = a->d_A = nullptr; a->d_S = a->d_obs = nullptr; a->d_keys = nullptr; a->tile = 0; a->adj_ok = false;
     cudaError_t e1 = cudaMalloc(&a->d_V, (size_t)a->N * want * a->elem());
     cudaError_t e3 = cudaMalloc((void **)&a->d_S, sizeof(int) * (size_t)a->D * want);
     cudaError_t e4 = cudaMalloc((void **)&a->d_obs, sizeof(int) * (size_t)a->D * want);
-    if (e1 || e3 || e4) {
-        cudaFree(a->d_V); cudaFree(a->d_S); cudaFree(a->d_obs);
-        a->d_V = nullptr; a->d_S = a->d_obs = nullptr;
+    cudaError_t e5 = cudaMalloc((void **)&a->d_keys, sizeof(uint32_t) * (size_t)MEMO_BKEYS * want);
+    if (e1 || e3 || e4 || e5) {
+        cudaFree(a->d_V); cudaFree(a->d_S); cudaFree(a->d_obs); cudaFree(a->d_keys);
+        a->d_V = nullptr; a->d_S = a->d_obs = nullptr; a->d_keys = nullptr;
         cudaGetLastError();
         return fail(QKC_ERR_NOMEM, "qkc: cannot allocate a %lld-column tile", (long long)want);
     }
@@ -1965,7 +2002,7 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
     std::vector<uint32_t> an, bn, emask, eoff;
     std::vector<int64_t> offu;
     std::vector<MemoAGroup> grp;
-    std::vector<KeyPlan> kplan, aplan;
+    std::vector<KeyPlan> kplan, aplan, bplan;
     std::vector<int32_t> plan_of;  // per node: its key plan in this step, -1 if none yet
     emask.assign((size_t)nq * a->E, 0u);
     eoff.assign((size_t)nq * a->E, 0u);
@@ -1987,6 +2024,7 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
         m->g_base.push_back((int64_t)grp.size());
         m->kp_base.push_back((int64_t)kplan.size());
         m->ap_base.push_back((int64_t)aplan.size());
+        m->bp_base.push_back((int64_t)bplan.size());
         plan_of.assign(N, -1);
         m->offu_base.push_back((int64_t)offu.size());
         const size_t ob = offu.size();
@@ -2055,6 +2093,13 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
                             kp.m = a->sigma[c] & jmask;
                             compress_masks(kp.m, kp.mv);
                             kp.k = (uint32_t)__builtin_popcountll(kp.m);
+                            kp.mid = -1;  // a row of the group-key table for this support, when there is room
+                            for (int64_t i = m->bp_base[j]; i < (int64_t)bplan.size() && kp.mid < 0; ++i)
+                                if (bplan[i].m == kp.m) kp.mid = (int32_t)(i - m->bp_base[j]);
+                            if (kp.mid < 0 && (int64_t)bplan.size() - m->bp_base[j] < MEMO_BKEYS) {
+                                kp.mid = (int32_t)((int64_t)bplan.size() - m->bp_base[j]);
+                                bplan.push_back(kp);
+                            }
                             plan_of[c] = (int32_t)((int64_t)kplan.size() - m->kp_base[j]);
                             kplan.push_back(kp);
                         }
@@ -2067,6 +2112,7 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
             m->b_lvl[j][L + 1] = (int64_t)bn.size() - m->b_base[j];
             m->g_lvl[j][L + 1] = (int64_t)grp.size() - m->g_base[j];
         }
+        m->bp_cnt.push_back((int64_t)bplan.size() - m->bp_base[j]);
         m->a_bytes_slot.push_back(abytes * (double)a->elem());
         m->b_bytes_col.push_back(bbytes * (double)a->elem());
         m->max_units = std::max(m->max_units, units);
@@ -2084,9 +2130,10 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
         (*st = upload(&m->d_emask, emask.data(), emask.size(), dummy)) ||
         (*st = upload(&m->d_eoff, eoff.data(), eoff.size(), dummy)) ||
         (*st = upload(&m->d_kplan, kplan.data(), kplan.size(), dummy)) ||
-        (*st = upload(&m->d_aplan, aplan.data(), aplan.size(), dummy))) {
+        (*st = upload(&m->d_aplan, aplan.data(), aplan.size(), dummy)) ||
+        (*st = upload(&m->d_bplan, bplan.data(), bplan.size(), dummy))) {
         cudaFree(m->d_a_nodes); cudaFree(m->d_a_grp); cudaFree(m->d_b_nodes); cudaFree(m->d_offu);
-        cudaFree(m->d_emask); cudaFree(m->d_eoff); cudaFree(m->d_kplan); cudaFree(m->d_aplan);
+        cudaFree(m->d_emask); cudaFree(m->d_eoff); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
         delete m;
         return nullptr;
     }
@@ -2125,6 +2172,7 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
     const int64_t pitch = a->tile;
     if (m->b_lvl[j][D] > 0) {
         const unsigned gs = (unsigned)((pitch + TPB - 1) / TPB);
+        if (m->bp_cnt[j] > 0) memo_keys<<<gs, TPB, 0, s>>>(a->d_desc, a->d_mdesc);
         if (a->prec == 32) level_scale_kernel<<<gs, TPB, 0, s>>>(d, 0, pitch, 0, a->d_S, a->d_obs);
         for (uint32_t L = 1; L < D; ++L) {
             const int64_t b0 = m->b_lvl[j][L], b1 = m->b_lvl[j][L + 1];
@@ -2150,6 +2198,7 @@ static int64_t memoB_launches(const qkc_ac *a, const qkc_ac::MemoMeta *m, int j)
     int64_t n = 1;
     if (m->b_lvl[j][a->D] > 0) {
         n += a->prec == 32 ? (int64_t)a->D : 0;
+        n += m->bp_cnt[j] > 0;
         for (uint32_t L = 1; L < a->D; ++L) n += m->b_lvl[j][L + 1] > m->b_lvl[j][L];
     }
     return n;
@@ -2198,7 +2247,8 @@ static qkc_status memo_pass(qkc_ac *a, qkc_ac::MemoMeta *m, int j, int clamp, in
     if ((st = memo_graph(a, m, j, false, &gA)) || (st = memo_graph(a, m, j, true, &gB))) return st;
     MemoDesc md{n_vec,    j,         clamp, jmask, a->d_pv, a->vec_cap, a->d_VA, m->d_offu + m->offu_base[j],
                 a->d_sigma, m->d_emask + (size_t)j * a->E, m->d_eoff + (size_t)j * a->E,
-                m->d_kplan + m->kp_base[j], m->d_aplan + m->ap_base[j]};
+                m->d_kplan + m->kp_base[j], m->d_aplan + m->ap_base[j], m->d_bplan + m->bp_base[j],
+                (int32_t)m->bp_cnt[j], a->d_keys, a->tile};
     set_memo_desc<<<1, 1, 0, s>>>(a->d_mdesc, md);
     ++a->launches;
     const size_t ra = a->recs.size();
