@@ -68,7 +68,7 @@ typedef struct {
     double p;
 } qkc_op;
 
-enum { QKC_AC_AMPLITUDE = 0, QKC_AC_DENSITY = 1 };
+enum { QKC_AC_AMPLITUDE = 0, QKC_AC_DENSITY = 1, QKC_AC_DENSITY_STEPS = 2 };
 enum { QKC_ORDER_AUTO = 0, QKC_ORDER_MINFILL = 1, QKC_ORDER_MINWEIGHT = 2, QKC_ORDER_CREATION = 3 };
 
 /*
@@ -93,6 +93,13 @@ enum { QKC_ORDER_AUTO = 0, QKC_ORDER_MINFILL = 1, QKC_ORDER_MINWEIGHT = 2, QKC_O
  *   f(lambda) = sum_x prod_j lambda_{x_j} <x| rho |x>,
  * so partial evidence gives marginal probabilities exactly (this construction
  * is this library's reading of Sec. 3.3; the paper itself enumerates r).
+ * kind QKC_AC_DENSITY_STEPS: one density AC per sampling step j = 0..n-1,
+ * compiled into one node set (equal sub-ACs shared), each from the operations
+ * in the backward light cone of qubits 0..j only.  Root j gives the marginal of
+ * qubits <= j exactly, so the chain-rule sampler (Sec. 3.3) evaluates at step
+ * j only the part of the circuit that can affect it.  The paper has no such
+ * construction; it is this library's answer to its sampling cost.  Supported
+ * by qkc_evaluate (the last root: the whole circuit) and qkc_sample only.
  *
  * `order` is one of QKC_ORDER_*; `max_nodes` bounds the AC (0 = 2^31-1), above
  * it QKC_ERR_TOO_LARGE.  On success *out_bytes is a malloc'd buffer in the
@@ -117,7 +124,8 @@ qkc_status qkc_plan(const qkc_op *ops, int32_t n_ops, int32_t n_qubits, int32_t 
  * Compiled-AC byte format (little endian, version 1).  Header of 16 uint32:
  *   [0] magic 0x43414B51 ("QKAC")  [1] version = 1  [2] kind  [3] n_qubits
  *   [4] n_angles  [5] n_vars  [6] n_nodes  [7] n_edges  [8] n_levels
- *   [9] n_leaves  [10] root  [11] n_ind  [12..15] 0
+ *   [9] n_leaves  [10] root  [11] n_ind  [12] n_roots (kind
+ *   QKC_AC_DENSITY_STEPS: n_qubits, else 0)  [13..15] 0
  * then these arrays, each starting on an 8-byte boundary:
  *   var_card[n_vars] u32      cardinality of each indicator variable
  *   var_tag[n_vars]  i32      qubit index of an output variable, or -1-k for
@@ -131,6 +139,8 @@ qkc_status qkc_plan(const qkc_op *ops, int32_t n_ops, int32_t n_qubits, int32_t 
  *                             1 sin(t/2), 2 exp(-i t/2), 3 exp(+i t/2)); CONST: 0
  *   leaf_coef[n_leaves][2] f64 PARAM: complex coefficient c (leaf = c g(t));
  *                             CONST: the value; IND: (1, 0)
+ *   roots[n_roots] u32        (light-cone steps only) root of step j; the
+ *                             last is the header's root
  * Level 0 holds exactly the leaves.  Nodes 0 .. n_ind-1 are the indicator
  * leaves lambda_{v=k} in (variable, value) order, one per value of every
  * variable.  MUL nodes have exactly two children; ADD nodes two or more.

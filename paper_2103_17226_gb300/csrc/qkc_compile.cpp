@@ -708,7 +708,8 @@ extern "C" qkc_status qkc_compile(const qkc_op *ops, int32_t n_ops, int32_t n_qu
                                   int32_t kind, int32_t order, int64_t max_nodes, uint8_t **out_bytes,
                                   uint64_t *out_len) {
     if (!out_bytes || !out_len || n_qubits <= 0 || n_qubits > 64 || n_ops < 0 || (n_ops > 0 && !ops) ||
-        n_angles < 0 || (kind != QKC_AC_AMPLITUDE && kind != QKC_AC_DENSITY) || order < 0 || order > 3) {
+        n_angles < 0 || (kind != QKC_AC_AMPLITUDE && kind != QKC_AC_DENSITY && kind != QKC_AC_DENSITY_STEPS) ||
+        order < 0 || order > 3) {
         qkc_set_error_("qkc_compile: invalid argument");
         return QKC_ERR_ARG;
     }
@@ -730,38 +731,78 @@ extern "C" qkc_status qkc_compile(const qkc_op *ops, int32_t n_ops, int32_t n_qu
     if (max_nodes <= 0 || max_nodes > 0x7fffffffLL) max_nodes = 0x7fffffffLL;
     try {
         NodeStore ns(max_nodes);
-        Builder bld(ns, n_qubits, kind);
-        for (int32_t i = 0; i < n_ops; ++i) bld.op(ops[i]);
-        bld.finish();
-        Network &net = bld.net;
-
-        // elimination order
-        std::vector<int32_t> ord;
-        if (order == QKC_ORDER_AUTO) {
-            double c1 = 0, c2 = 0;
-            auto o1 = elimination_order(net, QKC_ORDER_MINFILL, &c1);
-            auto o2 = elimination_order(net, QKC_ORDER_MINWEIGHT, &c2);
-            ord = (c2 < c1) ? o2 : o1;
+        // The circuits to compile: the whole circuit, or (light-cone steps) for every j the
+        // operations in the backward light cone of qubits 0..j -- walking the circuit from its
+        // end, an operation is kept when it touches a qubit of the growing set, which it then
+        // joins.  A dropped operation acts only on qubits traced out at the end and never
+        // coupled to qubits <= j afterwards, and is trace preserving, so the marginal of qubits
+        // <= j is unchanged.  All circuits share the node store (equal sub-ACs are shared).
+        std::vector<std::vector<qkc_op>> circuits;
+        if (kind == QKC_AC_DENSITY_STEPS) {
+            for (int32_t j = 0; j < n_qubits; ++j) {
+                std::vector<char> act(n_qubits, 0);
+                for (int32_t q = 0; q <= j; ++q) act[q] = 1;
+                std::vector<qkc_op> kept;
+                for (int32_t i = n_ops - 1; i >= 0; --i) {
+                    const qkc_op &o = ops[i];
+                    const bool two = (o.kind == 7 || o.kind == 8 || o.kind == 17);
+                    if (act[o.q0] || (two && act[o.q1])) {
+                        kept.push_back(o);
+                        act[o.q0] = 1;
+                        if (two) act[o.q1] = 1;
+                    }
+                }
+                std::reverse(kept.begin(), kept.end());
+                circuits.push_back(std::move(kept));
+            }
         } else {
-            ord = elimination_order(net, order, nullptr);
+            circuits.emplace_back(ops, ops + n_ops);
         }
-        std::vector<std::vector<int32_t>> var_factors(net.vars.size());
-        for (size_t fi = 0; fi < net.factors.size(); ++fi)
-            for (int32_t v : net.factors[fi].vars) var_factors[v].push_back((int32_t)fi);
-        for (int32_t x : ord) eliminate(net, x, var_factors);
+        const int32_t bkind = kind == QKC_AC_DENSITY_STEPS ? QKC_AC_DENSITY : kind;
+        std::vector<int32_t> roots;
+        std::vector<int32_t> ind_vars_tag;
+        std::vector<uint32_t> ind_card_out;
+        for (const auto &circ : circuits) {
+            Builder bld(ns, n_qubits, bkind);
+            for (const qkc_op &o : circ) bld.op(o);
+            bld.finish();
+            Network &net = bld.net;
 
-        // root = product of the remaining scalar factors
-        int32_t root = REF_ONE;
-        for (auto &f : net.factors)
-            if (f.alive) root = ns.mul(root, f.tab.empty() ? REF_ZERO : f.tab[0]);
-        if (root == REF_ONE) root = ns.cst_one_leaf();
-        if (root == REF_ZERO) root = ns.cst_zero_leaf();
+            // elimination order
+            std::vector<int32_t> ord;
+            if (order == QKC_ORDER_AUTO) {
+                double c1 = 0, c2 = 0;
+                auto o1 = elimination_order(net, QKC_ORDER_MINFILL, &c1);
+                auto o2 = elimination_order(net, QKC_ORDER_MINWEIGHT, &c2);
+                ord = (c2 < c1) ? o2 : o1;
+            } else {
+                ord = elimination_order(net, order, nullptr);
+            }
+            std::vector<std::vector<int32_t>> var_factors(net.vars.size());
+            for (size_t fi = 0; fi < net.factors.size(); ++fi)
+                for (int32_t v : net.factors[fi].vars) var_factors[v].push_back((int32_t)fi);
+            for (int32_t x : ord) eliminate(net, x, var_factors);
+
+            // root = product of the remaining scalar factors
+            int32_t root = REF_ONE;
+            for (auto &f : net.factors)
+                if (f.alive) root = ns.mul(root, f.tab.empty() ? REF_ZERO : f.tab[0]);
+            if (root == REF_ONE) root = ns.cst_one_leaf();
+            if (root == REF_ZERO) root = ns.cst_zero_leaf();
+            roots.push_back(root);
+            // indicator variables (the same for every circuit: outputs in qubit order, then the
+            // noise variables of the amplitude kind)
+            ind_vars_tag = bld.ind_tag;
+            ind_card_out.assign(bld.ind_card.begin(), bld.ind_card.end());
+        }
+        const int32_t root = roots.back();
 
         // reachable nodes + the full indicator set
         const int32_t nall = ns.size();
         std::vector<char> keep(nall, 0);
-        std::vector<int32_t> stack{root};
-        keep[root] = 1;
+        std::vector<int32_t> stack;
+        for (int32_t r : roots)
+            if (!keep[r]) { keep[r] = 1; stack.push_back(r); }
         while (!stack.empty()) {
             int32_t v = stack.back();
             stack.pop_back();
@@ -837,16 +878,13 @@ extern "C" qkc_status qkc_compile(const qkc_op *ops, int32_t n_ops, int32_t n_qu
             kids.insert(kids.end(), ch.begin(), ch.end());
             coff[i + 1] = (uint32_t)kids.size();
         }
-        std::vector<uint32_t> var_card;
-        std::vector<int32_t> var_tag;
-        for (size_t i = 0; i < bld.ind_vars.size(); ++i) {
-            var_card.push_back((uint32_t)bld.ind_card[i]);
-            var_tag.push_back(bld.ind_tag[i]);
-        }
+        std::vector<uint32_t> var_card(ind_card_out);
+        std::vector<int32_t> var_tag(ind_vars_tag);
+        const uint32_t n_roots = kind == QKC_AC_DENSITY_STEPS ? (uint32_t)roots.size() : 0u;
         std::vector<uint8_t> out;
         const uint32_t hdr[16] = {0x43414B51u, 1u, (uint32_t)kind, (uint32_t)n_qubits, (uint32_t)n_angles,
                                   (uint32_t)var_card.size(), N, (uint32_t)kids.size(), D, n_leaves,
-                                  (uint32_t)newid[root], n_ind, 0, 0, 0, 0};
+                                  (uint32_t)newid[root], n_ind, n_roots, 0, 0, 0};
         for (uint32_t h : hdr) put_u32(out, h);
         put_arr(out, var_card);
         put_arr(out, var_tag);
@@ -857,6 +895,11 @@ extern "C" qkc_status qkc_compile(const qkc_op *ops, int32_t n_ops, int32_t n_qu
         put_arr(out, la);
         put_arr(out, lb);
         put_arr(out, lc);
+        if (n_roots) {
+            std::vector<uint32_t> rr;
+            for (int32_t r : roots) rr.push_back((uint32_t)newid[r]);
+            put_arr(out, rr);
+        }
         pad8(out);
         uint8_t *buf = (uint8_t *)std::malloc(out.size());
         if (!buf) {
@@ -881,8 +924,8 @@ extern "C" void qkc_free_bytes(uint8_t *bytes) { std::free(bytes); }
 extern "C" qkc_status qkc_plan(const qkc_op *ops, int32_t n_ops, int32_t n_qubits, int32_t n_angles,
                                int32_t kind, int32_t order, double *table_entries, double *max_log2_table) {
     if (!table_entries || !max_log2_table || n_qubits <= 0 || n_qubits > 64 || n_ops < 0 ||
-        (n_ops > 0 && !ops) || (kind != QKC_AC_AMPLITUDE && kind != QKC_AC_DENSITY) || order < 0 ||
-        order > 3) {
+        (n_ops > 0 && !ops) || (kind != QKC_AC_AMPLITUDE && kind != QKC_AC_DENSITY && kind != QKC_AC_DENSITY_STEPS) ||
+        order < 0 || order > 3) {
         qkc_set_error_("qkc_plan: invalid argument");
         return QKC_ERR_ARG;
     }
@@ -898,7 +941,8 @@ extern "C" qkc_status qkc_plan(const qkc_op *ops, int32_t n_ops, int32_t n_qubit
     }
     try {
         NodeStore ns(0x7fffffffLL);
-        Builder bld(ns, n_qubits, kind);
+        // light-cone steps: the last step is the whole circuit, the largest of them
+        Builder bld(ns, n_qubits, kind == QKC_AC_DENSITY_STEPS ? QKC_AC_DENSITY : kind);
         for (int32_t i = 0; i < n_ops; ++i) bld.op(ops[i]);
         bld.finish();
         double c1 = 0, w1 = 0, c2 = 0, w2 = 0;

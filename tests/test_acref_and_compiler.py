@@ -229,3 +229,72 @@ def test_vqe_ising_density_ac_equals_density_matrix():
         val = sum(w * Q.z_expectation(P, s) for s, w in zip(sup, coef))
         got = sum(r.gradient(a, [-2 if b else -1 for b in s], w)[0] for s, w in zip(sup, coef))
         assert abs(got - val) < 1e-12
+
+
+def steps_roots(b: bytes):
+    """The roots table of a light-cone-steps AC (its layout is documented in include/qkc.h)."""
+    h = np.frombuffer(b[:64], dtype="<u4")
+    nv, N, E, D, nl = int(h[5]), int(h[6]), int(h[7]), int(h[8]), int(h[9])
+    off = 64
+    for nbytes in (4 * nv, 4 * nv, 4 * (D + 1), N, 4 * (N + 1), 4 * E, 4 * nl, 4 * nl, 16 * nl):
+        off = (off + nbytes + 7) & ~7
+    return np.frombuffer(b, dtype="<u4", count=int(h[12]), offset=off), int(h[10])
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_light_cone_step_roots_are_marginals(seed):
+    """Root j of a light-cone-steps AC, evaluated with qubits < j fixed, qubit j fixed and the rest
+    free, equals the marginal of qubits <= j of the density matrix of the whole circuit."""
+    n = 4 + seed % 3
+    c = (I.workload("qaoa4_ring_p1") if seed == 0 else
+         I.random_circuit(n, 14 + 3 * seed, seed=900 + seed, noise_prob=0.4))
+    n = c.n_qubits
+    ang = I.uniform_angles(1, c.n_angles, seed=seed + 3)[0]
+    P = Q.probabilities(c, ang)
+    b = compile_ac(c, kind=2)
+    roots, root = steps_roots(b)
+    assert len(roots) == n and roots[-1] == root
+    r = R.ACRef(b)
+    full = R.ACRef(compile_ac(c, kind=1))
+    rng = I.SplitMix(seed + 11)
+    for j in range(n):
+        for _ in range(4):
+            ev = [rng.randint(2) for _ in range(j + 1)] + [-1] * (n - j - 1)
+            r.up(ang, ev)
+            got = r.values()[roots[j]]
+            assert abs(got - Q.density_evidence(P, ev)) < 1e-13
+        # the last root is the whole circuit's AC value
+        ev = [rng.randint(2) for _ in range(n)]
+        assert abs(r.up(ang, ev) - full.up(ang, ev)) < 1e-13
+
+
+def test_light_cone_steps_shrink_early_steps():
+    """On the 32-qubit QAOA the early steps' light cones give much smaller ACs than the whole circuit."""
+    b = compile_ac(I.workload("qaoa32_3reg_p1_ideal"), kind=2)
+    roots, _ = steps_roots(b)
+    h = np.frombuffer(b[:64], dtype="<u4")
+    N, E, D, nv = int(h[6]), int(h[7]), int(h[8]), int(h[5])
+    off = 64
+    offs = []
+    for nbytes in (4 * nv, 4 * nv, 4 * (D + 1), N, 4 * (N + 1), 4 * E):
+        offs.append(off)
+        off = (off + nbytes + 7) & ~7
+    coff = np.frombuffer(b, dtype="<u4", count=N + 1, offset=offs[4])
+    child = np.frombuffer(b, dtype="<u4", count=E, offset=offs[5])
+
+    def reach(r0):
+        seen = np.zeros(N, dtype=bool)
+        st = [int(r0)]
+        seen[r0] = True
+        while st:
+            v = st.pop()
+            for e in range(coff[v], coff[v + 1]):
+                cc = int(child[e])
+                if not seen[cc]:
+                    seen[cc] = True
+                    st.append(cc)
+        return int(seen.sum())
+
+    sizes = [reach(roots[j]) for j in (0, 8, 14, 31)]
+    assert sizes[0] < sizes[1] < sizes[2] < sizes[3]
+    assert sizes[2] * 10 < sizes[3]
