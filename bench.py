@@ -58,8 +58,9 @@ def parse():
     ap.add_argument("--columns", type=int, default=2048)
     ap.add_argument("--tile", type=int, default=0, help="cap the column tile (0: library default)")
     ap.add_argument("--memo-budget-gb", type=float, default=0.0, help="memoised-slot budget (0: library default)")
-    ap.add_argument("--sampler", choices=["memo", "plain"], default="memo",
-                    help="memo: memoised chain-rule passes (automatic fallback); plain: every node per group")
+    ap.add_argument("--sampler", choices=["memo", "plain", "lightcone"], default="memo",
+                    help="memo: memoised chain-rule passes (automatic fallback); plain: every node per group; "
+                         "lightcone: memoised passes on the light-cone step AC (one AC per sampling step)")
     return ap.parse_args()
 
 
@@ -252,13 +253,19 @@ def run_ours(args):
     ac_bytes = N.compile(W["circuit"], N.QKC_AC_DENSITY)
     ctx = N.Context(local)
     ac = N.load_ac(ctx, ac_bytes, precision=32)
-    N.set_sampler(ac, 1 if args.sampler == "memo" else 0, int(args.memo_budget_gb * 2 ** 30))
-    if args.tile:
-        N.set_tile_limit(ac, args.tile)
+    N.set_sampler(ac, 0 if args.sampler == "plain" else 1, int(args.memo_budget_gb * 2 ** 30))
     V, S = W["V"], W["shots"]
     ev, cv, w = hamiltonian_columns(W)
     n_cols = len(cv)
-    N.reserve(ac, V, max(n_cols, V * max(S, 1)))
+    # the AC that samples: the density AC itself, or the light-cone step AC beside it
+    sac = ac
+    if args.sampler == "lightcone" and S:
+        sac = N.load_ac(ctx, N.compile(W["circuit"], N.QKC_AC_DENSITY_STEPS), precision=32)
+        N.set_sampler(sac, 1, int(args.memo_budget_gb * 2 ** 30))
+    if args.tile:
+        N.set_tile_limit(ac, args.tile)
+        N.set_tile_limit(sac, args.tile)
+    N.reserve(ac, V, n_cols if sac is not ac else max(n_cols, V * max(S, 1)))
     info = ac.info()
 
     # device inputs (kernel-only timing) -- a few angle sets, rotated per step
@@ -272,13 +279,16 @@ def run_ours(args):
     d_grad = torch.empty((V, W["circuit"].n_angles), dtype=torch.float64, device=dev)
 
     def step(k, angles=None, ev_t=None, cv_t=None, w_t=None, seeds=None, shots=None):
-        N.set_params(ac, angles if angles is not None else d_angles[k % 4])
+        a_k = angles if angles is not None else d_angles[k % 4]
+        N.set_params(ac, a_k)
+        if sac is not ac:
+            N.set_params(sac, a_k)
         val, grad = N.gradient(ac, cv_t if cv_t is not None else d_cv, ev_t if ev_t is not None else d_ev,
                                w_t if w_t is not None else d_w, V)
         bits = None
         if S:
-            bits = N.sample(ac, seeds if seeds is not None else d_seeds, shots if shots is not None else d_shots, S,
-                            out=d_bits)
+            bits = N.sample(sac, seeds if seeds is not None else d_seeds, shots if shots is not None else d_shots,
+                            S, out=d_bits)
         return val, grad, bits
 
     def barrier():
@@ -289,7 +299,9 @@ def run_ours(args):
     for k in range(args.warmup):
         step(k)
     barrier()
-    N.stats_enable(ac, True, 1 << 20)
+    acs = [ac] if sac is ac else [ac, sac]
+    for x in acs:
+        N.stats_enable(x, True, 1 << 20)
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
@@ -303,7 +315,11 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     stats = N.get_stats(ac)
-    N.stats_enable(ac, False, 0)
+    if sac is not ac:  # both ACs' launches and passes
+        st2 = N.get_stats(sac)
+        stats = {k: stats[k] + st2[k] for k in stats}
+    for x in acs:
+        N.stats_enable(x, False, 0)
     ms_max = max_over_ranks(ms, world, dev)
     units_per_step = V * S if S else n_cols
     value = whole_job_rate(units_per_step, world, args.steps, ms_max / 1e3)

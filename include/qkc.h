@@ -238,7 +238,9 @@ qkc_status qkc_gradient(qkc_ac *ac, const int32_t *col_vec_dev, const int8_t *ev
  * qkc_sample -- exact qubit-by-qubit conditional sampling of the output
  * distribution (Sec. 3.3.2 gives the sampling task; the paper's own sampler
  * is Gibbs MCMC, this one is the exact chain rule it compares against,
- * "ideal sampling").  Needs a DENSITY AC.
+ * "ideal sampling").  Needs a DENSITY AC, or a DENSITY_STEPS AC, whose step j
+ * takes p0 and P from root j (the light cone of qubits <= j) and otherwise runs
+ * the same way (same draws, same decisions up to rounding).
  * For vector v, sample s, qubit j: u = (SplitMix64_k(seeds[v]) >> 11) 2^-53
  * with k = s*n_qubits + j + 1 (the k-th output of a SplitMix64 stream);
  * p0 = P(x_<j, X_j = 0), P = P(x_<j); x_j = 1 iff u * P >= p0, in float64.

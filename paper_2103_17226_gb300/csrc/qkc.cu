@@ -755,9 +755,9 @@ __global__ void __launch_bounds__(TPB, 4) memoB_level_f32(DevAC ac, LevelArgs a,
             const uint32_t c = ac.child[e];
             const uint32_t eo = md.eoff[e];  // loaded alongside the child index
             const int64_t off = (int64_t)eo - 1;
-            if (eo == 0) {
+            if (eo & 0x80000000u) {  // tier B: the child's row of the tile
                 const int lc = ac.node_level[c];
-                const float4 v = __ldg(V4 + (int64_t)c * hp + (col >> 1));
+                const float4 v = __ldg(V4 + (int64_t)(eo & 0x7fffffffu) * hp + (col >> 1));
                 const int2 sc = __ldg(reinterpret_cast<const int2 *>(S + (int64_t)lc * a.pitch + col));
                 v0 = make_float2(v.x, v.y);
                 v1 = make_float2(v.z, v.w);
@@ -806,7 +806,7 @@ __global__ void __launch_bounds__(TPB, 4) memoB_level_f32(DevAC ac, LevelArgs a,
                     r1.x += v1.x * f1; r1.y += v1.y * f1;
                 }
             }
-            V4[(int64_t)n * hp + (col >> 1)] = make_float4(r0.x, r0.y, r1.x, r1.y);
+            V4[(int64_t)(a.lo + kk) * hp + (col >> 1)] = make_float4(r0.x, r0.y, r1.x, r1.y);
             m0 = max(m0, exp_of(r0));
             m1 = max(m1, exp_of(r1));
         }
@@ -849,8 +849,8 @@ __global__ void __launch_bounds__(TPB) memoB_level_f64(DevAC ac, LevelArgs a, co
                 const uint32_t eo = md.eoff[e];
                 const int64_t off = (int64_t)eo - 1;
                 double2 v;
-                if (eo == 0) {
-                    v = __ldg(V + (int64_t)c * a.pitch + col);
+                if (eo & 0x80000000u) {  // tier B: the child's row of the tile
+                    v = __ldg(V + (int64_t)(eo & 0x7fffffffu) * a.pitch + col);
                 } else {
                     const KeyPlan *kp = md.kplan + off;
                     const int mid = __ldg(&kp->mid);
@@ -860,14 +860,14 @@ __global__ void __launch_bounds__(TPB) memoB_level_f64(DevAC ac, LevelArgs a, co
                 if (o == OP_MUL) r = cmul(r, v);
                 else { r.x += v.x; r.y += v.y; }
             }
-            V[(int64_t)n * a.pitch + col] = r;
+            V[(int64_t)(a.lo + kk) * a.pitch + col] = r;
         }
     }
 }
 
 // Root value of every active group column: from the tier-A slots or the tier-B tile.
-__global__ void memo_root(const MemoDesc *mdp, const PassDesc *pd, uint32_t root, int Lroot, const void *Vb,
-                          const int *S, int64_t pitch, int prec32, double2 *out) {
+__global__ void memo_root(const MemoDesc *mdp, const PassDesc *pd, uint32_t root, int Lroot, int64_t rrow,
+                          const void *Vb, const int *S, int64_t pitch, int prec32, double2 *out) {
     const int64_t ncols = desc_cols(*pd);
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= ncols) return;
@@ -885,12 +885,12 @@ __global__ void memo_root(const MemoDesc *mdp, const PassDesc *pd, uint32_t root
         } else {
             r = static_cast<const double2 *>(md.VA)[sl];
         }
-    } else if (prec32) {
-        const float2 m = static_cast<const float2 *>(Vb)[(int64_t)root * pitch + c];
+    } else if (prec32) {  // tier B: the root's row of the tile
+        const float2 m = static_cast<const float2 *>(Vb)[rrow * pitch + c];
         const int sc = S[(int64_t)Lroot * pitch + c];
         r = make_double2(ldexp((double)m.x, sc), ldexp((double)m.y, sc));
     } else {
-        r = static_cast<const double2 *>(Vb)[(int64_t)root * pitch + c];
+        r = static_cast<const double2 *>(Vb)[rrow * pitch + c];
     }
     out[g] = r;
 }
@@ -1209,6 +1209,10 @@ struct qkc_ac {
     void *d_A = nullptr;      // [N][tile], allocated by the first downward pass
     bool adj_ok = false;
     int *d_S = nullptr, *d_obs = nullptr;  // [D][tile]
+    uint32_t vrows = 0;                    // node rows of the value buffer d_V (N, or fewer for step ACs)
+    std::vector<uint32_t> roots;           // per sampling step: its root (all the root but for step ACs)
+    std::vector<int> root_lev;             // per step: the root's level
+    int root_L = 0;                        // level of the root
     uint32_t *d_keys = nullptr;            // [MEMO_BKEYS][tile]: the memoised sampler's group-key table
     double2 *d_root = nullptr;  // [root_cap]
     int64_t root_cap = 0;
@@ -1239,7 +1243,10 @@ struct qkc_ac {
         MemoAGroup *d_a_grp = nullptr;  // tier-A key-width groups, per step and level
         int64_t *d_offu = nullptr;
         uint32_t *d_emask = nullptr;    // [step][edge]: a child's key bits inside its tier-A parent's key
-        uint32_t *d_eoff = nullptr;     // [step][edge]: 1 + a tier-A child's key plan, for tier-B parents
+        uint32_t *d_eoff = nullptr;     // [step][edge], tier-B parents: 1 + a tier-A child's key plan, or
+                                        // bit 31 + a tier-B child's row in the value tile
+        std::vector<int64_t> root_row;  // per step: the root's tier-B row, -1 when the root is tier A
+        int64_t max_rows = 0;           // tier-B nodes of the largest step (rows of the value tile)
         KeyPlan *d_kplan = nullptr;     // key plans of the tier-A children of tier-B nodes, per step
         KeyPlan *d_aplan = nullptr;     // key plans of scattered child-key masks of tier-A nodes, per step
         std::vector<int64_t> kp_base, ap_base;  // per step: first key plan of each kind
@@ -1376,13 +1383,16 @@ extern "C" qkc_status qkc_load_ac(qkc_ctx *ctx, const uint8_t *bytes, uint64_t l
     if (h[0] != 0x43414B51u || h[1] != 1u) return fail(QKC_ERR_FORMAT, "qkc_load_ac: bad magic or version");
     const uint32_t kind = h[2], nq = h[3], na = h[4], nv = h[5], N = h[6], E = h[7], D = h[8], nl = h[9],
                    root = h[10], nind = h[11];
-    if (kind > 1 || nq == 0 || nq > 64 || N == 0 || D == 0 || D > 65535 || nl > N || root >= N || nind > nl)
+    if (kind > 2 || nq == 0 || nq > 64 || N == 0 || D == 0 || D > 65535 || nl > N || root >= N || nind > nl ||
+        h[12] != (kind == QKC_AC_DENSITY_STEPS ? nq : 0u))
         return fail(QKC_ERR_FORMAT, "qkc_load_ac: inconsistent header");
     uint64_t off = 64, s_card, s_tag, s_lo, s_op, s_coff, s_child, s_la, s_lb, s_lc;
     bool ok = take(off, len, 4ull * nv, s_card) && take(off, len, 4ull * nv, s_tag) &&
               take(off, len, 4ull * (D + 1), s_lo) && take(off, len, 1ull * N, s_op) &&
               take(off, len, 4ull * (N + 1), s_coff) && take(off, len, 4ull * E, s_child) &&
               take(off, len, 4ull * nl, s_la) && take(off, len, 4ull * nl, s_lb) && take(off, len, 16ull * nl, s_lc);
+    uint64_t s_roots = 0;
+    if (ok && kind == QKC_AC_DENSITY_STEPS) ok = take(off, len, 4ull * nq, s_roots);
     if (!ok) return fail(QKC_ERR_FORMAT, "qkc_load_ac: buffer too short for its arrays");
     auto rd = [&](uint64_t s, size_t i, size_t w) {
         uint64_t v = 0;
@@ -1442,7 +1452,15 @@ extern "C" qkc_status qkc_load_ac(qkc_ctx *ctx, const uint8_t *bytes, uint64_t l
         }
     }
     if (n_ind != nind) return fail(QKC_ERR_FORMAT, "qkc_load_ac: indicator leaves missing");
-    if (lev[root] != D - 1 || lo[D - 1] + 1 != lo[D]) return fail(QKC_ERR_FORMAT, "qkc_load_ac: root is not alone on the top level");
+    std::vector<uint32_t> roots(nq, root);  // the root of every sampling step
+    if (kind == QKC_AC_DENSITY_STEPS) {
+        std::memcpy(roots.data(), bytes + s_roots, 4ull * nq);
+        for (uint32_t j = 0; j < nq; ++j)
+            if (roots[j] >= N) return fail(QKC_ERR_FORMAT, "qkc_load_ac: step root %u out of range", j);
+        if (roots[nq - 1] != root) return fail(QKC_ERR_FORMAT, "qkc_load_ac: the last step root is not the root");
+    } else if (lev[root] != D - 1 || lo[D - 1] + 1 != lo[D]) {
+        return fail(QKC_ERR_FORMAT, "qkc_load_ac: root is not alone on the top level");
+    }
     // transposed CSR of (parent, sibling)
     std::vector<uint32_t> poff(N + 1, 0);
     for (uint32_t e = 0; e < E; ++e) poff[child[e] + 1]++;
@@ -1501,6 +1519,9 @@ extern "C" qkc_status qkc_load_ac(qkc_ctx *ctx, const uint8_t *bytes, uint64_t l
     if (!a) return fail(QKC_ERR_NOMEM, "qkc_load_ac: out of host memory");
     a->ctx = ctx; a->prec = precision; a->kind = kind; a->n_qubits = nq; a->n_angles = na; a->n_vars = nv;
     a->N = N; a->E = E; a->D = D; a->n_leaves = nl; a->root = root; a->n_ind = nind; a->n_param = n_param;
+    a->roots = roots;
+    a->root_L = (int)lev[root];
+    for (uint32_t j = 0; j < nq; ++j) a->root_lev.push_back((int)lev[roots[j]]);
     a->n_const = nl - nind - n_param; a->level_off = lo;
     a->var_card = card;
     for (uint32_t i = nl; i < N; ++i)
@@ -1526,7 +1547,7 @@ extern "C" qkc_status qkc_load_ac(qkc_ctx *ctx, const uint8_t *bytes, uint64_t l
         qkc_free_ac(a);
         return st;
     }
-    if (kind == QKC_AC_DENSITY) {  // indicator support of every node (sampling memoisation)
+    if (kind == QKC_AC_DENSITY || kind == QKC_AC_DENSITY_STEPS) {  // indicator supports (memoised sampling)
         a->sigma.assign(N, 0ull);
         for (uint32_t i = 0; i < nind; ++i) a->sigma[i] = 1ull << (uint32_t)ind_var[i];
         for (uint32_t i = nl; i < N; ++i)
@@ -1574,10 +1595,13 @@ static qkc_status ensure_vectors(qkc_ac *a, int64_t nvec) {
 // Column tile: values for `cols` columns, rounded up to 64, capped so that the
 // value buffer (and, when a downward pass needs it, the adjoint buffer of the
 // same shape) each stay within 25% of the device memory.
-static qkc_status ensure_tile(qkc_ac *a, int64_t cols) {
+// The value tile: `rows` node rows (0: every node; the memoised passes of a step AC need only
+// the largest step's tier-B rows) x a multiple of 64 columns, at least `cols` when it fits.
+static qkc_status ensure_tile(qkc_ac *a, int64_t cols, uint32_t rows = 0) {
+    if (rows == 0) rows = a->N;
     int64_t want = (cols + 63) / 64 * 64;
     if (want < 64) want = 64;
-    const int64_t per_col = (int64_t)a->N * (int64_t)a->elem() + 8LL * a->D + 4LL * MEMO_BKEYS;
+    const int64_t per_col = (int64_t)rows * (int64_t)a->elem() + 8LL * a->D + 4LL * MEMO_BKEYS;
     int64_t cap = (int64_t)((double)a->ctx->total_mem * 0.25) / std::max<int64_t>(1, per_col);
     if (const char *env = std::getenv("QKC_MAX_TILE_COLUMNS")) {  // smaller tiles (tests of the tiled path)
         const long long lim = std::atoll(env);
@@ -1587,11 +1611,11 @@ static qkc_status ensure_tile(qkc_ac *a, int64_t cols) {
     cap = cap / 64 * 64;
     if (cap < 64) return fail(QKC_ERR_NOMEM, "qkc: AC too large for one 64-column tile");
     want = std::min(want, cap);
-    if (want <= a->tile) return QKC_OK;
+    if (want <= a->tile && rows <= a->vrows) return QKC_OK;
     QKC_CUDA(cudaDeviceSynchronize());
     cudaFree(a->d_V); cudaFree(a->d_A); cudaFree(a->d_S); cudaFree(a->d_obs); cudaFree(a->d_keys);
     a->d_V = a->d_A = nullptr; a->d_S = a->d_obs = nullptr; a->d_keys = nullptr; a->tile = 0; a->adj_ok = false;
-    cudaError_t e1 = cudaMalloc(&a->d_V, (size_t)a->N * want * a->elem());
+    cudaError_t e1 = cudaMalloc(&a->d_V, (size_t)rows * want * a->elem());
     cudaError_t e3 = cudaMalloc((void **)&a->d_S, sizeof(int) * (size_t)a->D * want);
     cudaError_t e4 = cudaMalloc((void **)&a->d_obs, sizeof(int) * (size_t)a->D * want);
     cudaError_t e5 = cudaMalloc((void **)&a->d_keys, sizeof(uint32_t) * (size_t)MEMO_BKEYS * want);
@@ -1602,6 +1626,7 @@ static qkc_status ensure_tile(qkc_ac *a, int64_t cols) {
         return fail(QKC_ERR_NOMEM, "qkc: cannot allocate a %lld-column tile", (long long)want);
     }
     a->tile = want;
+    a->vrows = rows;
     return QKC_OK;
 }
 
@@ -1821,13 +1846,16 @@ static qkc_status run_up(qkc_ac *a, const EvSrc &es, int64_t col0, int64_t ncols
     return QKC_OK;
 }
 
-static qkc_status run_roots(qkc_ac *a, int64_t col0, int64_t ncols, const int32_t *n_active, cudaStream_t s) {
+// Root values of a tile's columns: the AC's root, or (step >= 0) the root of that sampling step.
+static qkc_status run_roots(qkc_ac *a, int64_t col0, int64_t ncols, const int32_t *n_active, cudaStream_t s,
+                            int step = -1) {
     const unsigned g = (unsigned)((ncols + TPB - 1) / TPB);
+    const uint32_t r = step < 0 ? a->root : a->roots[step];
+    const int Lr = step < 0 ? a->root_L : a->root_lev[step];
     if (a->prec == 32)
-        root_f32<<<g, TPB, 0, s>>>((const float2 *)a->d_V, a->d_S, a->tile, a->root, (int)a->D - 1, ncols, n_active,
-                                   col0, a->d_root);
+        root_f32<<<g, TPB, 0, s>>>((const float2 *)a->d_V, a->d_S, a->tile, r, Lr, ncols, n_active, col0, a->d_root);
     else
-        root_f64<<<g, TPB, 0, s>>>((const double2 *)a->d_V, a->tile, a->root, ncols, n_active, col0, a->d_root);
+        root_f64<<<g, TPB, 0, s>>>((const double2 *)a->d_V, a->tile, r, ncols, n_active, col0, a->d_root);
     ++a->launches;
     QKC_LAUNCH_CHECK();
     return QKC_OK;
@@ -1883,6 +1911,8 @@ extern "C" qkc_status qkc_marginals(qkc_ac *a, const int32_t *col_vec, const int
                                     double *root_out, double *marg_out, void *stream) {
     qkc_status st = check_query(a, col_vec, ev, n_cols, "qkc_marginals");
     if (st) return st;
+    if (a->kind == QKC_AC_DENSITY_STEPS)  // the downward pass needs the root alone on the top level
+        return fail(QKC_ERR_UNSUPPORTED, "qkc_marginals: not on a DENSITY_STEPS AC (use its DENSITY AC)");
     if (n_cols == 0) return QKC_OK;
     if (!marg_out) return fail(QKC_ERR_ARG, "qkc_marginals: marg_out is null");
     QKC_CUDA(cudaSetDevice(a->ctx->device));
@@ -1913,6 +1943,8 @@ extern "C" qkc_status qkc_gradient(qkc_ac *a, const int32_t *col_vec, const int8
                                    int64_t n_cols, int64_t n_vectors, double *value, double *grad, void *stream) {
     qkc_status st = check_query(a, col_vec, ev, n_cols, "qkc_gradient");
     if (st) return st;
+    if (a->kind == QKC_AC_DENSITY_STEPS)
+        return fail(QKC_ERR_UNSUPPORTED, "qkc_gradient: not on a DENSITY_STEPS AC (use its DENSITY AC)");
     if (!col_vec || !weight || !value || !grad || n_vectors <= 0 || n_vectors > a->n_vec)
         return fail(QKC_ERR_ARG, "qkc_gradient: needs col_vec, weight, value, grad and 0 < n_vectors <= bound vectors");
     if (!a->last_angles) return fail(QKC_ERR_ARG, "qkc_gradient: qkc_set_params has not been called");
@@ -2004,6 +2036,9 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
     std::vector<MemoAGroup> grp;
     std::vector<KeyPlan> kplan, aplan, bplan;
     std::vector<int32_t> plan_of;  // per node: its key plan in this step, -1 if none yet
+    std::vector<int64_t> row_of;   // per node: its tier-B row in this step
+    std::vector<char> reach;       // per node: reachable from this step's root
+    std::vector<uint32_t> dfs;
     emask.assign((size_t)nq * a->E, 0u);
     eoff.assign((size_t)nq * a->E, 0u);
     const std::vector<uint32_t> &child_off = a->h_child_off, &child = a->h_child;
@@ -2026,6 +2061,20 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
         m->ap_base.push_back((int64_t)aplan.size());
         m->bp_base.push_back((int64_t)bplan.size());
         plan_of.assign(N, -1);
+        row_of.assign(N, -1);
+        // the step's nodes: those its root reaches (all of a single-root AC's computed nodes)
+        reach.assign(N, 0);
+        dfs.assign(1, a->roots[j]);
+        reach[a->roots[j]] = 1;
+        while (!dfs.empty()) {
+            const uint32_t v = dfs.back();
+            dfs.pop_back();
+            for (uint32_t e = child_off[v]; e < child_off[v + 1]; ++e)
+                if (!reach[child[e]]) {
+                    reach[child[e]] = 1;
+                    dfs.push_back(child[e]);
+                }
+        }
         m->offu_base.push_back((int64_t)offu.size());
         const size_t ob = offu.size();
         offu.resize(ob + N, -1);
@@ -2036,6 +2085,7 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
             // binds no leaf per group, so every leaf a per-group node reads must be here
             al.clear();
             for (uint32_t n = a->level_off[L]; n < a->level_off[L + 1]; ++n) {
+                if (!reach[n]) continue;
                 const int k = __builtin_popcountll(a->sigma[n] & jmask);
                 if (k <= t || n < a->n_leaves) al.push_back({k, n});
             }
@@ -2079,13 +2129,16 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
                 }
             }
             for (uint32_t n = a->level_off[L]; n < a->level_off[L + 1]; ++n) {
-                if (offu[ob + n] >= 0) continue;
+                if (!reach[n] || offu[ob + n] >= 0) continue;
+                row_of[n] = (int64_t)bn.size() - m->b_base[j];  // tier-B values are stored by row
                 bn.push_back(n);
                 bbytes += (double)(child_off[n + 1] - child_off[n]) + 1.0;
                 for (uint32_t e = child_off[n]; e < child_off[n + 1]; ++e) {
                     const uint32_t c = child[e];
                     const int64_t oc = offu[ob + c];
-                    if (oc >= 0) {
+                    if (oc < 0) {  // a tier-B child: its row
+                        eoff[(size_t)j * a->E + e] = 0x80000000u | (uint32_t)row_of[c];
+                    } else {
                         m->floor0[j][L] = 1;
                         if (plan_of[c] < 0) {
                             KeyPlan kp{};
@@ -2113,6 +2166,8 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
             m->g_lvl[j][L + 1] = (int64_t)grp.size() - m->g_base[j];
         }
         m->bp_cnt.push_back((int64_t)bplan.size() - m->bp_base[j]);
+        m->root_row.push_back(row_of[a->roots[j]]);
+        m->max_rows = std::max<int64_t>(m->max_rows, (int64_t)bn.size() - m->b_base[j]);
         m->a_bytes_slot.push_back(abytes * (double)a->elem());
         m->b_bytes_col.push_back(bbytes * (double)a->elem());
         m->max_units = std::max(m->max_units, units);
@@ -2179,7 +2234,7 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
             if (a->prec == 32)
                 level_scale_kernel<<<gs, TPB, 0, s>>>(d, (int)L, pitch, m->floor0[j][L], a->d_S, a->d_obs);
             if (b1 == b0) continue;
-            LevelArgs la{0, 0, (int)L, pitch};
+            LevelArgs la{(uint32_t)b0, 0, (int)L, pitch};  // lo: the level's first tier-B row
             const uint32_t *nodes = m->d_b_nodes + m->b_base[j] + b0;
             const int64_t cw = a->prec == 32 ? 64 : 32;
             const int64_t items = ((b1 - b0 + NB - 1) / NB) * ((pitch + cw - 1) / cw);
@@ -2191,7 +2246,8 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
                 memoB_level_f64<<<g, TPB, 0, s>>>(d, la, nodes, b1 - b0, a->d_desc, a->d_mdesc, (double2 *)a->d_V);
         }
     }
-    memo_root<<<(unsigned)((pitch + TPB - 1) / TPB), TPB, 0, s>>>(a->d_mdesc, a->d_desc, a->root, (int)D - 1, a->d_V,
+    memo_root<<<(unsigned)((pitch + TPB - 1) / TPB), TPB, 0, s>>>(a->d_mdesc, a->d_desc, a->roots[j], a->root_lev[j],
+                                                                  m->root_row[j], a->d_V,
                                                                   a->d_S, pitch, a->prec == 32, a->d_root);
 }
 static int64_t memoB_launches(const qkc_ac *a, const qkc_ac::MemoMeta *m, int j) {
@@ -2287,7 +2343,8 @@ extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t
                                  int64_t max_shots, int64_t total_shots, uint64_t *bits, void *stream) {
     if (!a || !seeds || !shots || !bits || n_vec <= 0 || max_shots < 0)
         return fail(QKC_ERR_ARG, "qkc_sample: bad argument");
-    if (a->kind != QKC_AC_DENSITY) return fail(QKC_ERR_UNSUPPORTED, "qkc_sample: needs a DENSITY AC");
+    if (a->kind != QKC_AC_DENSITY && a->kind != QKC_AC_DENSITY_STEPS)
+        return fail(QKC_ERR_UNSUPPORTED, "qkc_sample: needs a DENSITY or DENSITY_STEPS AC");
     if (n_vec > a->n_vec && a->n_param > 0) return fail(QKC_ERR_ARG, "qkc_sample: more vectors than bound");
     if (max_shots == 0) return QKC_OK;
     if (n_vec * max_shots > (int64_t)INT32_MAX / 2) return fail(QKC_ERR_ARG, "qkc_sample: too many samples");
@@ -2299,8 +2356,12 @@ extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t
     const int nq = (int)a->n_qubits;
     qkc_status st;
     if ((st = ensure_sampling(a, n_samp, std::max(n_samp, n_vec)))) return st;
-    // tile sized for the largest step (bounded by the sample count), roots for every group
-    if ((st = ensure_tile(a, std::max(n_samp, n_vec))) || (st = ensure_roots(a, std::max(n_samp, n_vec)))) return st;
+    // tile sized for the largest step (bounded by the sample count), roots for every group; a step
+    // AC sizes its tile once the memoised passes (whose rows it holds) are chosen
+    const bool steps = a->kind == QKC_AC_DENSITY_STEPS;
+    if ((!steps && (st = ensure_tile(a, std::max(n_samp, n_vec)))) ||
+        (st = ensure_roots(a, std::max(n_samp, n_vec))))
+        return st;
     // memoised passes: the largest cap (bits per node key) whose tier-A slots fit the budget
     // (the caller's, else 40% of the device memory and 60% of what is free); if the slots
     // cannot be allocated, smaller caps, then the per-group sampler
@@ -2351,6 +2412,9 @@ extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t
         }
         if (memo >= plain) meta = nullptr;
     }
+    if (steps && (st = ensure_tile(a, std::max(n_samp, n_vec),
+                                   meta ? (uint32_t)std::max<int64_t>(1, meta->max_rows) : 0u)))
+        return st;
     const unsigned gs = (unsigned)((n_samp + TPB - 1) / TPB);
     sample_init<<<std::max(gs, (unsigned)((n_vec + TPB - 1) / TPB)), TPB, 0, s>>>(
         n_vec, max_shots, shots, a->d_s_group, a->d_s_bits, a->d_g_vec[0], a->d_g_prefix[0], a->d_gcount);
@@ -2384,7 +2448,7 @@ extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t
                 const int64_t nc = std::min<int64_t>(a->tile, bound - c0);
                 EvSrc es{nullptr, a->d_g_prefix[cur], j, 1, a->d_g_vec[cur], gcount, std::max<int64_t>(1, a->n_vec)};
                 if ((st = run_up(a, es, c0, nc, s))) return st;
-                if ((st = run_roots(a, c0, nc, gcount, s))) return st;
+                if ((st = run_roots(a, c0, nc, gcount, s, j))) return st;
             }
         }
         const int64_t nflag = 2 * bound;
@@ -2601,7 +2665,7 @@ extern "C" qkc_status qkc_evaluate_static(qkc_ac *a, const int32_t *col_vec, con
         launch_up_sequence(a, s, V, S, obs, tile);
         const unsigned gr = (unsigned)((nc + TPB - 1) / TPB);
         if (a->prec == 32)
-            root_f32<<<gr, TPB, 0, s>>>((const float2 *)V, S, tile, a->root, (int)a->D - 1, nc, nullptr, c0, o);
+            root_f32<<<gr, TPB, 0, s>>>((const float2 *)V, S, tile, a->root, a->root_L, nc, nullptr, c0, o);
         else
             root_f64<<<gr, TPB, 0, s>>>((const double2 *)V, tile, a->root, nc, nullptr, c0, o);
         a->launches += 2 + up_sequence_launches(a);

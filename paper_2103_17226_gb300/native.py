@@ -20,6 +20,7 @@ _lib = None
 
 QKC_AC_AMPLITUDE = 0
 QKC_AC_DENSITY = 1
+QKC_AC_DENSITY_STEPS = 2  # one density AC per sampling step (backward light cones), qkc_sample and qkc_evaluate only
 STATUS = {0: "QKC_OK", 1: "QKC_ERR_ARG", 2: "QKC_ERR_FORMAT", 3: "QKC_ERR_NOMEM", 4: "QKC_ERR_CUDA",
           5: "QKC_ERR_TIMEOUT", 6: "QKC_ERR_UNSUPPORTED", 7: "QKC_ERR_TOO_LARGE"}
 

@@ -502,3 +502,67 @@ def test_vqe_ising_gradient(cuda_ctx):
         assert abs(val[v] - rv) < 1e-5 * scale
         if v == 0:
             assert np.abs(grad[v][slots] - rg[slots]).max() < 1e-5 * scale * 10
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("name", ["qaoa4_ring_p1", "random6", "qaoa32_3reg_p1_ideal"])
+def test_light_cone_step_sampler(cuda_ctx, prec, name):
+    """A light-cone step AC (root j: the density AC of the backward light cone of qubits <= j)
+    gives the chain rule the same conditionals as the whole circuit's density AC: its samples,
+    per group (mode 0) and memoised (mode 2), match the density AC's memoised samples and the
+    oracle's, with differences only at decisions inside the tie margin."""
+    if name == "random6":
+        c = I.random_circuit(6, 24, seed=903, noise_prob=0.4)
+        b1 = N().compile(c, 1)
+    else:
+        c = I.workload(name)
+        b1 = compiled(name)
+    b2 = N().compile(c, N().QKC_AC_DENSITY_STEPS)
+    n = c.n_qubits
+    V, S = (5, 700) if n < 32 else (4, 400)
+    angs = I.uniform_angles(V, c.n_angles, seed=19)
+    seeds_h = I.vector_seeds(V, 19)
+    seeds = t(seeds_h.astype(np.int64))
+    shots = t(np.array([S, S // 3, 1, S - 7, 64][:V], dtype=np.int32))
+    outs = {}
+    for key, b, mode in (("whole", b1, 2), ("steps_plain", b2, 0), ("steps_memo", b2, 2)):
+        if n == 32 and key == "steps_plain" and prec == 32:
+            continue  # every node of every step per group: covered in FP64
+        ac = N().load_ac(cuda_ctx, b, precision=prec)
+        N().set_sampler(ac, mode)
+        N().set_params(ac, t(angs))
+        outs[key] = N().sample(ac, seeds, shots, S).cpu().numpy()
+        N().check_status(ac)
+    sh = shots.cpu().numpy()
+    allowed = 0 if prec == 64 else 3
+    for key in outs:
+        if key == "whole":
+            continue
+        diff = sum(int((outs[key][v, :sh[v]] != outs["whole"][v, :sh[v]]).sum()) for v in range(V))
+        assert diff <= allowed, (key, diff)
+        if n <= 6:
+            for v in range(V):
+                ref = Q.chain_rule_samples(Q.probabilities(c, angs[v]), int(seeds_h[v]), int(sh[v]))
+                assert (outs[key][v, :sh[v]].astype(np.uint64) != ref).sum() <= (0 if prec == 64 else 2)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_light_cone_step_ac_evaluate_and_unsupported_calls(cuda_ctx, prec):
+    """qkc_evaluate on a step AC is the whole circuit's AC (its last root); the downward-pass
+    calls are refused with an error status."""
+    c = I.random_circuit(5, 20, seed=904, noise_prob=0.4)
+    V = 3
+    angs = I.uniform_angles(V, c.n_angles, seed=23)
+    ev = np.array([[(x >> (4 - j)) & 1 if (x + j) % 3 else -1 for j in range(5)] for x in range(32)], dtype=np.int8)
+    cv = np.arange(32, dtype=np.int32) % V
+    vals = []
+    for kind in (1, N().QKC_AC_DENSITY_STEPS):
+        ac = N().load_ac(cuda_ctx, N().compile(c, kind), precision=prec)
+        N().set_params(ac, t(angs))
+        vals.append(N().evaluate(ac, t(cv), t(ev)).cpu().numpy())
+        if kind == 2:
+            with pytest.raises(Exception):
+                N().marginals(ac, t(cv), t(ev))
+            with pytest.raises(Exception):
+                N().gradient(ac, t(cv), t(ev), t(np.ones(32)), V)
+    assert np.abs(vals[0] - vals[1]).max() < TOL[prec]
