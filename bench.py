@@ -7,7 +7,9 @@ step, per GPU, is a variational iteration over 64 parameter vectors --
   bind the angles (upward-pass leaves),
   <C> and its angle gradient for the Max-Cut cost C = sum_edges (1 - Z_i Z_j)/2
     (48 Z-string evidence columns per vector: upward + downward pass),
-  10000 chain-rule samples per vector (qubit-by-qubit conditional sampling).
+  10000 chain-rule samples per vector (qubit-by-qubit conditional sampling),
+  drawn from the light-cone step AC (step j's density AC holds only the operations
+  that can affect qubits <= j; --sampler memo uses the whole density AC).
 `value` is samples/s over all GPUs (weak scaling: every GPU runs its own 64
 vectors; there is no collective on the data path).
 
@@ -58,7 +60,7 @@ def parse():
     ap.add_argument("--columns", type=int, default=2048)
     ap.add_argument("--tile", type=int, default=0, help="cap the column tile (0: library default)")
     ap.add_argument("--memo-budget-gb", type=float, default=0.0, help="memoised-slot budget (0: library default)")
-    ap.add_argument("--sampler", choices=["memo", "plain", "lightcone"], default="memo",
+    ap.add_argument("--sampler", choices=["memo", "plain", "lightcone"], default="lightcone",
                     help="memo: memoised chain-rule passes (automatic fallback); plain: every node per group; "
                          "lightcone: memoised passes on the light-cone step AC (one AC per sampling step)")
     return ap.parse_args()
