@@ -54,9 +54,11 @@ def parse():
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
     ap.add_argument("--shots", type=int, default=None, help="samples per vector (qaoa32: 10000, vqe: 1000)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["step", "uppass", "gradpass"], default="step",
+    ap.add_argument("--mode", choices=["step", "uppass", "gradpass", "samplepass"], default="step",
                     help="uppass: only the upward pass over --columns sampling-prefix columns; gradpass: "
-                         "upward + downward pass (gradient) over --columns Z-string columns (profiling cases)")
+                         "upward + downward pass (gradient) over --columns Z-string columns; samplepass: one "
+                         "sampling call over --vectors vectors x --shots shots (profiling cases)")
+    ap.add_argument("--vectors", type=int, default=16, help="samplepass: parameter vectors")
     ap.add_argument("--columns", type=int, default=2048)
     ap.add_argument("--tile", type=int, default=0, help="cap the column tile (0: library default)")
     ap.add_argument("--memo-budget-gb", type=float, default=0.0, help="memoised-slot budget (0: library default)")
@@ -444,6 +446,35 @@ def run_gradpass(args):
           flush=True)
 
 
+def run_samplepass(args):
+    """Small profiling case: one qkc_sample call (the --sampler's AC and passes) over --vectors
+    vectors x --shots shots of the workload, with the tier-A / tier-B rates of its memoised passes."""
+    import torch
+    from paper_2103_17226_gb300.build import build_library
+    build_library()
+    from paper_2103_17226_gb300 import inputs as I, native as N
+    W = make_workload(args.workload, args.shots)
+    c, V, S = W["circuit"], args.vectors, W["shots"]
+    kind = N.QKC_AC_DENSITY_STEPS if args.sampler == "lightcone" else N.QKC_AC_DENSITY
+    ac = N.load_ac(N.Context(0), N.compile(c, kind), precision=32)
+    if args.tile:
+        N.set_tile_limit(ac, args.tile)
+    N.set_sampler(ac, 0 if args.sampler == "plain" else 2, int(args.memo_budget_gb * 2 ** 30))
+    N.set_params(ac, torch.tensor(I.uniform_angles(V, c.n_angles, seed=5), device="cuda"))
+    seeds = torch.tensor(I.vector_seeds(V, 11).astype(np.int64), device="cuda")
+    shots = torch.full((V,), S, dtype=torch.int32, device="cuda")
+    N.stats_enable(ac, True, 1 << 16)
+    N.sample(ac, seeds, shots, S, total_shots=V * S)
+    torch.cuda.synchronize()
+    st = N.get_stats(ac)
+    b_ms = st["memo_ms"] - st["memo_a_ms"]
+    print(json.dumps({"mode": "samplepass", "workload": W["name"], "sampler": args.sampler, "vectors": V, "shots": S,
+                      "launches": st["launches"], "memo_ms": st["memo_ms"], "memo_a_ms": st["memo_a_ms"],
+                      "tier_a_gbs": st["memo_a_bytes"] / (st["memo_a_ms"] * 1e6) if st["memo_a_ms"] > 0 else None,
+                      "tier_b_gbs": (st["memo_bytes"] - st["memo_a_bytes"]) / (b_ms * 1e6) if b_ms > 0 else None,
+                      "up_ms": st["up_ms"]}), flush=True)
+
+
 def run_uppass(args):
     """Small profiling case: the upward pass alone over `--columns` columns whose
     evidence fixes a random prefix of the qubits (the sampler's column shape)."""
@@ -578,6 +609,9 @@ def main():
         return
     if args.mode == "gradpass":
         run_gradpass(args)
+        return
+    if args.mode == "samplepass":
+        run_samplepass(args)
         return
     if args.impl == "reference":
         run_reference(args)

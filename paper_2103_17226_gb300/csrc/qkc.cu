@@ -630,69 +630,98 @@ __device__ __forceinline__ C memo_leaf(const DevAC &ac, const MemoDesc &md, uint
 // their unit blocks (2^k units each, one unit = one key of one vector) start t0 units into the
 // level, in the same order, so a unit index gives its node and key by a shift.
 struct MemoAGroup {
-    uint32_t t0, nb, k;
+    uint32_t t0, nb, k, u0;  // first thread, first node, key width, first unit (within the level)
 };
 
-// One level of tier A: a thread per slot (vector, node, key) of the level's tier-A blocks.
+// Key widths from which a thread evaluates four slots of one node (keys key0 + 32 r, r < 4, with
+// bits 5-6 of key0 clear): the node and its children are looked up once, and since the packing
+// of bits is OR-linear, a child key is ck(key0) | ck(32 r), two per-child constants.
+constexpr int MEMO_QUAD_K = 7;
+
+// One level of tier A: a thread per slot, or per four slots of one node, of the level's tier-A
+// blocks (vector, node, key).
 template <typename C>
 __global__ void __launch_bounds__(TPB) memoA_level(DevAC ac, const MemoDesc *mdp, const uint32_t *nodes,
-                                                    const MemoAGroup *grp, int ng, int64_t u0, uint32_t U) {
-    if (U == 0 || ng <= 0) return;
+                                                    const MemoAGroup *grp, int ng, int64_t u0, uint32_t T) {
+    if (T == 0 || ng <= 0) return;
     const MemoDesc md = *mdp;
     C *VA = static_cast<C *>(md.VA);
-    const uint32_t nblk = (U + TPB - 1) / TPB;
+    const uint32_t nblk = (T + TPB - 1) / TPB;
     const int64_t items = md.V * (int64_t)nblk;
-    // block item b covers vector b / nblk and units (b % nblk) * TPB + thread; quotient and
+    // block item b covers vector b / nblk and threads (b % nblk) * TPB + thread; quotient and
     // remainder are stepped along the grid-stride loop rather than divided every time
     int64_t vec = blockIdx.x / nblk;
     uint32_t rb = blockIdx.x % nblk;
     const uint32_t dq = gridDim.x / nblk, dr = gridDim.x % nblk;
     for (int64_t b = blockIdx.x; b < items; b += gridDim.x) {
         const uint32_t t = rb * TPB + threadIdx.x;
-        if (t < U) {
+        if (t < T) {
             int gi = 0;
             while (gi + 1 < ng && __ldg(&grp[gi + 1].t0) <= t) ++gi;
-            const uint32_t t0 = __ldg(&grp[gi].t0), nb = __ldg(&grp[gi].nb);
+            const uint32_t t0 = __ldg(&grp[gi].t0), nb = __ldg(&grp[gi].nb), ug = __ldg(&grp[gi].u0);
             const int k = (int)__ldg(&grp[gi].k);
-            const uint32_t rel = t - t0;
+            const uint32_t q = t - t0;
+            const bool quad = k >= MEMO_QUAD_K;
+            const uint32_t rel = quad ? (((q >> 5) << 7) | (q & 31u)) : q;  // first unit within the group
             const uint32_t nl = rel >> k;
-            const uint32_t key = rel & ((1u << k) - 1u);
+            const uint32_t key0 = rel & ((1u << k) - 1u);
             const uint32_t n = nodes[nb + nl];
-            const int64_t local = (vec << k) | (int64_t)key;
-            C r;
+            C r[4];
             const uint8_t o = ac.op[n];
-            if (o <= OP_CONST) {
-                r = memo_leaf<C>(ac, md, n, vec, key);
+            if (o <= OP_CONST) {  // leaves have at most one key bit: one slot
+                r[0] = memo_leaf<C>(ac, md, n, vec, key0);
             } else {
                 const uint32_t e0 = ac.child_off[n], e1 = ac.child_off[n + 1];
-                r.x = (o == OP_MUL) ? 1 : 0;
-                r.y = 0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    r[i].x = (o == OP_MUL) ? 1 : 0;
+                    r[i].y = 0;
+                }
                 const uint32_t full = (1u << k) - 1u;
                 for (uint32_t e = e0; e < e1; ++e) {
                     const uint32_t c = ac.child[e];
                     const uint32_t me = md.emask[e];  // the child's key bits inside this node's key
-                    int64_t cs;
-                    if (me == full) {
-                        cs = local;  // same key space: same slot layout
+                    int kc;
+                    uint32_t ck0, m;
+                    if (me == full) {  // same key space: same key
+                        kc = k;
+                        ck0 = key0;
+                        m = full;
                     } else if (me & 0x80000000u) {
                         const KeyPlan *kp = md.aplan + (me & 0x7fffffffu);
-                        cs = (vec << (int)__ldg(&kp->k)) | (int64_t)plan_key(kp, key, true);
+                        kc = (int)__ldg(&kp->k);
+                        m = (uint32_t)__ldg(&kp->m);
+                        ck0 = plan_key(kp, key0, true);
                     } else {
-                        cs = (vec << __popc(me)) | (int64_t)extract_bits(key, me);
+                        kc = __popc(me);
+                        m = me;
+                        ck0 = extract_bits(key0, me);
                     }
-                    const C v = VA[md.V * md.offu[c] + cs];
-                    if (o == OP_MUL) {
-                        C m;
-                        m.x = r.x * v.x - r.y * v.y;
-                        m.y = r.x * v.y + r.y * v.x;
-                        r = m;
-                    } else {
-                        r.x += v.x;
-                        r.y += v.y;
+                    const uint32_t d1 = ((m >> 5) & 1u) ? 1u << __popc(m & 31u) : 0u;  // ck(32)
+                    const uint32_t d2 = ((m >> 6) & 1u) ? 1u << __popc(m & 63u) : 0u;  // ck(64)
+                    const C *src = VA + md.V * md.offu[c] + (vec << kc);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if (i > 0 && !quad) break;
+                        const C v = src[ck0 | ((i & 1) ? d1 : 0u) | ((i & 2) ? d2 : 0u)];
+                        if (o == OP_MUL) {
+                            C mm;
+                            mm.x = r[i].x * v.x - r[i].y * v.y;
+                            mm.y = r[i].x * v.y + r[i].y * v.x;
+                            r[i] = mm;
+                        } else {
+                            r[i].x += v.x;
+                            r[i].y += v.y;
+                        }
                     }
                 }
             }
-            VA[md.V * (u0 + t0 + ((int64_t)nl << k)) + local] = r;
+            C *dst = VA + md.V * (u0 + ug + ((int64_t)nl << k)) + (vec << k) + key0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (i > 0 && !quad) break;
+                dst[32 * i] = r[i];
+            }
         }
         rb += dr;
         vec += dq;
@@ -1236,6 +1265,7 @@ struct qkc_ac {
         int cap = 0;
         int64_t max_units = 0;
         std::vector<std::vector<int64_t>> a_lvl, u_lvl, b_lvl, g_lvl;  // per step, [D + 1]
+        std::vector<std::vector<int64_t>> t_lvl;                        // per step and level: tier-A threads
         std::vector<std::vector<uint8_t>> floor0;               // per step, [D]
         std::vector<int64_t> a_base, b_base, offu_base, g_base;  // per step
         std::vector<double> a_bytes_slot, b_bytes_col;           // per step: algorithmic bytes per slot unit / column
@@ -2046,6 +2076,7 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
     m->u_lvl = m->a_lvl;
     m->b_lvl = m->a_lvl;
     m->g_lvl = m->a_lvl;
+    m->t_lvl = m->a_lvl;
     m->floor0.assign(nq, std::vector<uint8_t>(D, 0));
     std::vector<std::pair<int, uint32_t>> al;  // (key width, node) of one level's tier A
     for (int j = 0; j < nq; ++j) {
@@ -2093,11 +2124,14 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
             std::stable_sort(al.begin(), al.end(), [](const std::pair<int, uint32_t> &x,
                                                       const std::pair<int, uint32_t> &y) { return x.first > y.first; });
             const int64_t u0 = units, i0 = (int64_t)an.size();
+            int64_t th = 0;  // threads of the level (one per slot, or per four slots from MEMO_QUAD_K)
             for (size_t i = 0; i < al.size(); ++i) {
                 const int k = al[i].first;
                 const uint32_t n = al[i].second;
                 if (i == 0 || k != al[i - 1].first)
-                    grp.push_back(MemoAGroup{(uint32_t)(units - u0), (uint32_t)((int64_t)an.size() - i0), (uint32_t)k});
+                    grp.push_back(MemoAGroup{(uint32_t)th, (uint32_t)((int64_t)an.size() - i0), (uint32_t)k,
+                                             (uint32_t)(units - u0)});
+                th += k >= MEMO_QUAD_K ? (1ll << k) / 4 : (1ll << k);
                 offu[ob + n] = units;
                 an.push_back(n);
                 units += 1ll << k;
@@ -2164,6 +2198,7 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
             m->u_lvl[j][L + 1] = units;
             m->b_lvl[j][L + 1] = (int64_t)bn.size() - m->b_base[j];
             m->g_lvl[j][L + 1] = (int64_t)grp.size() - m->g_base[j];
+            m->t_lvl[j][L] = th;
         }
         m->bp_cnt.push_back((int64_t)bplan.size() - m->bp_base[j]);
         m->root_row.push_back(row_of[a->roots[j]]);
@@ -2205,14 +2240,13 @@ static void launch_memoA_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
     for (uint32_t L = 0; L < a->D; ++L) {
         const int64_t i0 = m->a_lvl[j][L], i1 = m->a_lvl[j][L + 1];
         if (i1 == i0) continue;
-        const int64_t u0 = m->u_lvl[j][L], u1 = m->u_lvl[j][L + 1];
+        const int64_t u0 = m->u_lvl[j][L];
+        const uint32_t T = (uint32_t)m->t_lvl[j][L];
         const uint32_t *nodes = m->d_a_nodes + m->a_base[j] + i0;
         const MemoAGroup *gp = m->d_a_grp + m->g_base[j] + m->g_lvl[j][L];
         const int ng = (int)(m->g_lvl[j][L + 1] - m->g_lvl[j][L]);
-        if (a->prec == 32)
-            memoA_level<float2><<<g, TPB, 0, s>>>(d, a->d_mdesc, nodes, gp, ng, u0, (uint32_t)(u1 - u0));
-        else
-            memoA_level<double2><<<g, TPB, 0, s>>>(d, a->d_mdesc, nodes, gp, ng, u0, (uint32_t)(u1 - u0));
+        if (a->prec == 32) memoA_level<float2><<<g, TPB, 0, s>>>(d, a->d_mdesc, nodes, gp, ng, u0, T);
+        else memoA_level<double2><<<g, TPB, 0, s>>>(d, a->d_mdesc, nodes, gp, ng, u0, T);
     }
 }
 static int64_t memoA_launches(const qkc_ac *a, const qkc_ac::MemoMeta *m, int j) {
