@@ -246,7 +246,7 @@ __global__ void level_scale_kernel(DevAC ac, int L, int64_t pitch, int floor_zer
     for (uint32_t k = ac.cl_off[L]; k < ac.cl_off[L + 1]; ++k) {
         int Lp = ac.cl[k];
         int o = obs[(int64_t)Lp * pitch + c];
-        if (o == OBS_EMPTY) o = -127;
+        if (o == OBS_EMPTY) continue;  // no value of that level in this column (its scale is unused)
         int cand = S[(int64_t)Lp * pitch + c] + o;
         s = max(s, cand);
     }
@@ -254,6 +254,12 @@ __global__ void level_scale_kernel(DevAC ac, int L, int64_t pitch, int floor_zer
     if (floor_zero && s < 0) s = 0;  // the level also reads unscaled values (memoised sampling)
     S[(int64_t)L * pitch + c] = s;
     obs[(int64_t)L * pitch + c] = OBS_EMPTY;
+}
+
+// Every level's observed exponent back to empty (a memoised pass computes only some levels).
+__global__ void obs_reset(int *obs, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) obs[i] = OBS_EMPTY;
 }
 
 // ------------------------------------------------------------------ upward pass, one level
@@ -561,7 +567,8 @@ struct MemoDesc {
     const uint64_t *sigma;
     const uint32_t *emask;  // per child edge of a tier-A node: the child's key bits in the parent's key,
                             // or (bit 31 set) the index of a key plan in aplan for a scattered mask
-    const uint32_t *eoff;   // per child edge of a tier-B node: 1 + the child's key plan, 0 if tier B
+    const uint2 *brec;      // per child edge of a tier-B node, in node order: (bit 31 + the child's tile
+                            // row, or 1 + its key plan; the child's level)
     const KeyPlan *kplan;  // per tier-A child of a tier-B node (this step)
     const KeyPlan *aplan;  // per distinct scattered child-key mask of tier-A parents (this step)
     const KeyPlan *bplan;  // the step's tabled supports (nbm of them) ...
@@ -747,7 +754,7 @@ __global__ void memo_keys(const PassDesc *pd, const MemoDesc *mdp) {
 }
 
 // One level of tier B (FP32): as up_level_f32 over a node list, tier-A children read by key.
-__global__ void __launch_bounds__(TPB, 4) memoB_level_f32(DevAC ac, LevelArgs a, const uint32_t *nodes, int64_t count,
+__global__ void __launch_bounds__(TPB, 4) memoB_level_f32(LevelArgs a, const uint2 *bdesc, int64_t count,
                                                         const PassDesc *pd, const MemoDesc *mdp,
                                                         float2 *__restrict__ V, const int *__restrict__ S,
                                                         int *__restrict__ obs) {
@@ -765,10 +772,18 @@ __global__ void __launch_bounds__(TPB, 4) memoB_level_f32(DevAC ac, LevelArgs a,
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t hp = a.pitch >> 1;
     float4 *V4 = reinterpret_cast<float4 *>(V);
+    // item it = node block it / nchunks, column chunk it % nchunks, stepped without division
+    int64_t blk = wid / nchunks, chunk = wid % nchunks;
+    const int64_t dq = nw / nchunks, dr = nw % nchunks;
     for (int64_t it = wid; it < items; it += nw) {
-        const int64_t chunk = it % nchunks;
-        const int64_t blk = it / nchunks;
         const int64_t col = chunk * 64 + lane * 2;
+        const int64_t blk_i = blk;
+        chunk += dr;
+        blk += dq;
+        if (chunk >= nchunks) {
+            chunk -= nchunks;
+            ++blk;
+        }
         if (col >= ncols) continue;
         const bool two = col + 1 < ncols;
         const int64_t g0 = col0 + col, g1 = two ? g0 + 1 : g0;
@@ -778,22 +793,21 @@ __global__ void __launch_bounds__(TPB, 4) memoB_level_f32(DevAC ac, LevelArgs a,
         const uint64_t pre1 = md.j ? __brevll(es.prefix[g1] << (64 - md.j)) : 0ull;
         const int2 sL = *reinterpret_cast<const int2 *>(S + (int64_t)a.L * a.pitch + col);
         int m0 = -127, m1 = -127;
-        const int64_t k1 = min(count, (blk + 1) * NB);
-        // one child's two column values and scale exponents (tier A: unscaled, exponent 0)
-        auto child_vals = [&](uint32_t e, float2 &v0, float2 &v1, int &s0, int &s1) {
-            const uint32_t c = ac.child[e];
-            const uint32_t eo = md.eoff[e];  // loaded alongside the child index
-            const int64_t off = (int64_t)eo - 1;
+        const int64_t k1 = min(count, (blk_i + 1) * NB);
+        // one child's two column values and scale exponents (tier A: unscaled, exponent 0); the
+        // edge record holds the child's tile row or key plan, and its level
+        auto child_vals = [&](uint32_t r, float2 &v0, float2 &v1, int &s0, int &s1) {
+            const uint2 rec = __ldg(md.brec + r);
+            const uint32_t eo = rec.x;
             if (eo & 0x80000000u) {  // tier B: the child's row of the tile
-                const int lc = ac.node_level[c];
                 const float4 v = __ldg(V4 + (int64_t)(eo & 0x7fffffffu) * hp + (col >> 1));
-                const int2 sc = __ldg(reinterpret_cast<const int2 *>(S + (int64_t)lc * a.pitch + col));
+                const int2 sc = __ldg(reinterpret_cast<const int2 *>(S + (int64_t)rec.y * a.pitch + col));
                 v0 = make_float2(v.x, v.y);
                 v1 = make_float2(v.z, v.w);
                 s0 = sc.x;
                 s1 = sc.y;
             } else {
-                const KeyPlan *kp = md.kplan + off;
+                const KeyPlan *kp = md.kplan + (eo - 1u);
                 const int kc = (int)__ldg(&kp->k);
                 const int mid = __ldg(&kp->mid);
                 const int64_t base = md.V * __ldg(&kp->off);
@@ -811,33 +825,32 @@ __global__ void __launch_bounds__(TPB, 4) memoB_level_f32(DevAC ac, LevelArgs a,
                 s0 = s1 = 0;
             }
         };
-        for (int64_t kk = blk * NB; kk < k1; ++kk) {
-            const uint32_t n = nodes[kk];
-            const uint8_t o = ac.op[n];
-            const uint32_t e0 = ac.child_off[n], e1 = ac.child_off[n + 1];
-            float2 r0, r1;
+        for (int64_t kk = blk_i * NB; kk < k1; ++kk) {
+            const uint2 dsc = __ldg(bdesc + kk);  // (first edge record, degree | op << 24)
+            const uint32_t r0 = dsc.x, deg = dsc.y & 0xffffffu, o = dsc.y >> 24;
+            float2 q0, q1;
             if (o == OP_MUL) {
                 float2 a0, a1, b0, b1;
                 int sa0, sa1, sb0, sb1;
-                child_vals(e0, a0, a1, sa0, sa1);
-                child_vals(e0 + 1, b0, b1, sb0, sb1);
-                r0 = cscale(cmul(a0, b0), pow2f(sa0 + sb0 - sL.x));
-                r1 = cscale(cmul(a1, b1), pow2f(sa1 + sb1 - sL.y));
+                child_vals(r0, a0, a1, sa0, sa1);
+                child_vals(r0 + 1, b0, b1, sb0, sb1);
+                q0 = cscale(cmul(a0, b0), pow2f(sa0 + sb0 - sL.x));
+                q1 = cscale(cmul(a1, b1), pow2f(sa1 + sb1 - sL.y));
             } else {
-                r0 = make_float2(0.f, 0.f);
-                r1 = r0;
-                for (uint32_t e = e0; e < e1; ++e) {
+                q0 = make_float2(0.f, 0.f);
+                q1 = q0;
+                for (uint32_t e = 0; e < deg; ++e) {
                     float2 v0, v1;
                     int s0, s1;
-                    child_vals(e, v0, v1, s0, s1);
+                    child_vals(r0 + e, v0, v1, s0, s1);
                     const float f0 = pow2f(s0 - sL.x), f1 = pow2f(s1 - sL.y);
-                    r0.x += v0.x * f0; r0.y += v0.y * f0;
-                    r1.x += v1.x * f1; r1.y += v1.y * f1;
+                    q0.x += v0.x * f0; q0.y += v0.y * f0;
+                    q1.x += v1.x * f1; q1.y += v1.y * f1;
                 }
             }
-            V4[(int64_t)(a.lo + kk) * hp + (col >> 1)] = make_float4(r0.x, r0.y, r1.x, r1.y);
-            m0 = max(m0, exp_of(r0));
-            m1 = max(m1, exp_of(r1));
+            V4[(int64_t)(a.lo + kk) * hp + (col >> 1)] = make_float4(q0.x, q0.y, q1.x, q1.y);
+            m0 = max(m0, exp_of(q0));
+            m1 = max(m1, exp_of(q1));
         }
         atomicMax(obs + (int64_t)a.L * a.pitch + col, m0);
         if (two) atomicMax(obs + (int64_t)a.L * a.pitch + col + 1, m1);
@@ -845,7 +858,7 @@ __global__ void __launch_bounds__(TPB, 4) memoB_level_f32(DevAC ac, LevelArgs a,
 }
 
 // One level of tier B (FP64, unscaled).
-__global__ void __launch_bounds__(TPB) memoB_level_f64(DevAC ac, LevelArgs a, const uint32_t *nodes, int64_t count,
+__global__ void __launch_bounds__(TPB) memoB_level_f64(LevelArgs a, const uint2 *bdesc, int64_t count,
                                                         const PassDesc *pd, const MemoDesc *mdp,
                                                         double2 *__restrict__ V) {
     const int64_t ncols = desc_cols(*pd);
@@ -860,28 +873,33 @@ __global__ void __launch_bounds__(TPB) memoB_level_f64(DevAC ac, LevelArgs a, co
     const int64_t items = ((count + NB - 1) / NB) * nchunks;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t blk = wid / nchunks, chunk = wid % nchunks;
+    const int64_t dq = nw / nchunks, dr = nw % nchunks;
     for (int64_t it = wid; it < items; it += nw) {
-        const int64_t chunk = it % nchunks;
-        const int64_t blk = it / nchunks;
         const int64_t col = chunk * 32 + lane;
+        const int64_t blk_i = blk;
+        chunk += dr;
+        blk += dq;
+        if (chunk >= nchunks) {
+            chunk -= nchunks;
+            ++blk;
+        }
         if (col >= ncols) continue;
         const int64_t g = col0 + col;
         const int64_t vec = vec_of(es, g);
         const uint64_t pre = md.j ? __brevll(es.prefix[g] << (64 - md.j)) : 0ull;  // qubit order
-        const int64_t k1 = min(count, (blk + 1) * NB);
-        for (int64_t kk = blk * NB; kk < k1; ++kk) {
-            const uint32_t n = nodes[kk];
-            const uint8_t o = ac.op[n];
+        const int64_t k1 = min(count, (blk_i + 1) * NB);
+        for (int64_t kk = blk_i * NB; kk < k1; ++kk) {
+            const uint2 dsc = __ldg(bdesc + kk);
+            const uint32_t r0 = dsc.x, deg = dsc.y & 0xffffffu, o = dsc.y >> 24;
             double2 r = make_double2(o == OP_MUL ? 1.0 : 0.0, 0.0);
-            for (uint32_t e = ac.child_off[n]; e < ac.child_off[n + 1]; ++e) {
-                const uint32_t c = ac.child[e];
-                const uint32_t eo = md.eoff[e];
-                const int64_t off = (int64_t)eo - 1;
+            for (uint32_t e = 0; e < deg; ++e) {
+                const uint32_t eo = __ldg(md.brec + r0 + e).x;
                 double2 v;
                 if (eo & 0x80000000u) {  // tier B: the child's row of the tile
                     v = __ldg(V + (int64_t)(eo & 0x7fffffffu) * a.pitch + col);
                 } else {
-                    const KeyPlan *kp = md.kplan + off;
+                    const KeyPlan *kp = md.kplan + (eo - 1u);
                     const int mid = __ldg(&kp->mid);
                     const uint32_t key = mid >= 0 ? md.keys[(int64_t)mid * md.kpitch + col] : plan_key(kp, pre, narrow);
                     v = VA[md.V * __ldg(&kp->off) + ((vec << (int)__ldg(&kp->k)) | (int64_t)key)];
@@ -1258,6 +1276,7 @@ struct qkc_ac {
     std::vector<uint64_t> sigma;
     std::vector<uint32_t> var_card;               // cardinality of every indicator variable
     std::vector<uint32_t> h_child_off, h_child;  // host copy of the structure (density ACs)
+    std::vector<uint8_t> h_op;  // node ops (host copy, memoised-pass metadata)
     uint64_t *d_sigma = nullptr;
     MemoDesc *d_mdesc = nullptr;
     struct GraphSlot { cudaGraphExec_t exec = nullptr; const void *V = nullptr, *A = nullptr; int64_t pitch = 0; };
@@ -1273,8 +1292,11 @@ struct qkc_ac {
         MemoAGroup *d_a_grp = nullptr;  // tier-A key-width groups, per step and level
         int64_t *d_offu = nullptr;
         uint32_t *d_emask = nullptr;    // [step][edge]: a child's key bits inside its tier-A parent's key
-        uint32_t *d_eoff = nullptr;     // [step][edge], tier-B parents: 1 + a tier-A child's key plan, or
-                                        // bit 31 + a tier-B child's row in the value tile
+        uint2 *d_bdesc = nullptr;       // per step, per tier-B node (tier-B order): (first edge record,
+                                        // degree | op << 24)
+        uint2 *d_brec = nullptr;        // per step, per edge of a tier-B node: (bit 31 + a tier-B child's
+                                        // tile row, or 1 + a tier-A child's key plan; the child's level)
+        std::vector<int64_t> br_base;   // per step: first edge record
         std::vector<int64_t> root_row;  // per step: the root's tier-B row, -1 when the root is tier A
         int64_t max_rows = 0;           // tier-B nodes of the largest step (rows of the value tile)
         KeyPlan *d_kplan = nullptr;     // key plans of the tier-A children of tier-B nodes, per step
@@ -1372,7 +1394,7 @@ extern "C" void qkc_free_ac(qkc_ac *a) {
     for (auto *m : a->memo) {
         if (!m) continue;
         cudaFree(m->d_a_nodes); cudaFree(m->d_b_nodes); cudaFree(m->d_a_grp); cudaFree(m->d_offu);
-        cudaFree(m->d_emask); cudaFree(m->d_eoff); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
+        cudaFree(m->d_emask); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
         for (auto &g : m->gA) if (g.exec) cudaGraphExecDestroy(g.exec);
         for (auto &g : m->gB) if (g.exec) cudaGraphExecDestroy(g.exec);
         delete m;
@@ -1584,6 +1606,7 @@ extern "C" qkc_status qkc_load_ac(qkc_ctx *ctx, const uint8_t *bytes, uint64_t l
             for (uint32_t e = coff[i]; e < coff[i + 1]; ++e) a->sigma[i] |= a->sigma[child[e]];
         a->h_child_off = coff;
         a->h_child = child;
+        a->h_op = op;
         if ((st = upload(&a->d_sigma, a->sigma.data(), N, b))) {
             qkc_free_ac(a);
             return st;
@@ -2061,7 +2084,11 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
     m->cap = cap;
     const int nq = (int)a->n_qubits;
     const uint32_t N = a->N, D = a->D;
-    std::vector<uint32_t> an, bn, emask, eoff;
+    std::vector<uint32_t> an, bn, emask;
+    std::vector<uint2> bdesc, brec;
+    std::vector<uint16_t> lev(N);
+    for (uint32_t L = 0; L < D; ++L)
+        for (uint32_t n = a->level_off[L]; n < a->level_off[L + 1]; ++n) lev[n] = (uint16_t)L;
     std::vector<int64_t> offu;
     std::vector<MemoAGroup> grp;
     std::vector<KeyPlan> kplan, aplan, bplan;
@@ -2070,7 +2097,6 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
     std::vector<char> reach;       // per node: reachable from this step's root
     std::vector<uint32_t> dfs;
     emask.assign((size_t)nq * a->E, 0u);
-    eoff.assign((size_t)nq * a->E, 0u);
     const std::vector<uint32_t> &child_off = a->h_child_off, &child = a->h_child;
     m->a_lvl.assign(nq, std::vector<int64_t>(D + 1, 0));
     m->u_lvl = m->a_lvl;
@@ -2091,6 +2117,7 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
         m->kp_base.push_back((int64_t)kplan.size());
         m->ap_base.push_back((int64_t)aplan.size());
         m->bp_base.push_back((int64_t)bplan.size());
+        m->br_base.push_back((int64_t)brec.size());
         plan_of.assign(N, -1);
         row_of.assign(N, -1);
         // the step's nodes: those its root reaches (all of a single-root AC's computed nodes)
@@ -2166,12 +2193,19 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
                 if (!reach[n] || offu[ob + n] >= 0) continue;
                 row_of[n] = (int64_t)bn.size() - m->b_base[j];  // tier-B values are stored by row
                 bn.push_back(n);
+                const uint32_t deg = child_off[n + 1] - child_off[n];
+                if (deg > 0xffffffu) {  // a descriptor holds a 24-bit degree: no memoised passes
+                    delete m;
+                    return nullptr;
+                }
+                bdesc.push_back(make_uint2((uint32_t)((int64_t)brec.size() - m->br_base[j]),
+                                           deg | ((uint32_t)a->h_op[n] << 24)));
                 bbytes += (double)(child_off[n + 1] - child_off[n]) + 1.0;
                 for (uint32_t e = child_off[n]; e < child_off[n + 1]; ++e) {
                     const uint32_t c = child[e];
                     const int64_t oc = offu[ob + c];
                     if (oc < 0) {  // a tier-B child: its row
-                        eoff[(size_t)j * a->E + e] = 0x80000000u | (uint32_t)row_of[c];
+                        brec.push_back(make_uint2(0x80000000u | (uint32_t)row_of[c], lev[c]));
                     } else {
                         m->floor0[j][L] = 1;
                         if (plan_of[c] < 0) {
@@ -2190,7 +2224,7 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
                             plan_of[c] = (int32_t)((int64_t)kplan.size() - m->kp_base[j]);
                             kplan.push_back(kp);
                         }
-                        eoff[(size_t)j * a->E + e] = (uint32_t)plan_of[c] + 1u;
+                        brec.push_back(make_uint2((uint32_t)plan_of[c] + 1u, lev[c]));
                     }
                 }
             }
@@ -2218,12 +2252,13 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
         (*st = upload(&m->d_b_nodes, bn.data(), bn.size(), dummy)) ||
         (*st = upload(&m->d_offu, offu.data(), offu.size(), dummy)) ||
         (*st = upload(&m->d_emask, emask.data(), emask.size(), dummy)) ||
-        (*st = upload(&m->d_eoff, eoff.data(), eoff.size(), dummy)) ||
+        (*st = upload(&m->d_bdesc, bdesc.data(), bdesc.size(), dummy)) ||
+        (*st = upload(&m->d_brec, brec.data(), brec.size(), dummy)) ||
         (*st = upload(&m->d_kplan, kplan.data(), kplan.size(), dummy)) ||
         (*st = upload(&m->d_aplan, aplan.data(), aplan.size(), dummy)) ||
         (*st = upload(&m->d_bplan, bplan.data(), bplan.size(), dummy))) {
         cudaFree(m->d_a_nodes); cudaFree(m->d_a_grp); cudaFree(m->d_b_nodes); cudaFree(m->d_offu);
-        cudaFree(m->d_emask); cudaFree(m->d_eoff); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
+        cudaFree(m->d_emask); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
         delete m;
         return nullptr;
     }
@@ -2262,22 +2297,25 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
     if (m->b_lvl[j][D] > 0) {
         const unsigned gs = (unsigned)((pitch + TPB - 1) / TPB);
         if (m->bp_cnt[j] > 0) memo_keys<<<gs, TPB, 0, s>>>(a->d_desc, a->d_mdesc);
-        if (a->prec == 32) level_scale_kernel<<<gs, TPB, 0, s>>>(d, 0, pitch, 0, a->d_S, a->d_obs);
+        // FP32 scales: only levels with tier-B nodes are computed, so every level's observed
+        // exponent starts empty and the scale kernel runs for those levels alone
+        if (a->prec == 32)
+            obs_reset<<<(unsigned)(((int64_t)D * pitch + TPB - 1) / TPB), TPB, 0, s>>>(a->d_obs, (int64_t)D * pitch);
         for (uint32_t L = 1; L < D; ++L) {
             const int64_t b0 = m->b_lvl[j][L], b1 = m->b_lvl[j][L + 1];
+            if (b1 == b0) continue;
             if (a->prec == 32)
                 level_scale_kernel<<<gs, TPB, 0, s>>>(d, (int)L, pitch, m->floor0[j][L], a->d_S, a->d_obs);
-            if (b1 == b0) continue;
             LevelArgs la{(uint32_t)b0, 0, (int)L, pitch};  // lo: the level's first tier-B row
-            const uint32_t *nodes = m->d_b_nodes + m->b_base[j] + b0;
             const int64_t cw = a->prec == 32 ? 64 : 32;
             const int64_t items = ((b1 - b0 + NB - 1) / NB) * ((pitch + cw - 1) / cw);
             const unsigned g = grid_for(items * 32, TPB, (int64_t)sms * 8);
+            const uint2 *bd = m->d_bdesc + m->b_base[j] + b0;
             if (a->prec == 32)
-                memoB_level_f32<<<g, TPB, 0, s>>>(d, la, nodes, b1 - b0, a->d_desc, a->d_mdesc, (float2 *)a->d_V,
-                                                   a->d_S, a->d_obs);
+                memoB_level_f32<<<g, TPB, 0, s>>>(la, bd, b1 - b0, a->d_desc, a->d_mdesc, (float2 *)a->d_V, a->d_S,
+                                                   a->d_obs);
             else
-                memoB_level_f64<<<g, TPB, 0, s>>>(d, la, nodes, b1 - b0, a->d_desc, a->d_mdesc, (double2 *)a->d_V);
+                memoB_level_f64<<<g, TPB, 0, s>>>(la, bd, b1 - b0, a->d_desc, a->d_mdesc, (double2 *)a->d_V);
         }
     }
     memo_root<<<(unsigned)((pitch + TPB - 1) / TPB), TPB, 0, s>>>(a->d_mdesc, a->d_desc, a->roots[j], a->root_lev[j],
@@ -2287,9 +2325,9 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
 static int64_t memoB_launches(const qkc_ac *a, const qkc_ac::MemoMeta *m, int j) {
     int64_t n = 1;
     if (m->b_lvl[j][a->D] > 0) {
-        n += a->prec == 32 ? (int64_t)a->D : 0;
+        n += a->prec == 32 ? 1 : 0;
         n += m->bp_cnt[j] > 0;
-        for (uint32_t L = 1; L < a->D; ++L) n += m->b_lvl[j][L + 1] > m->b_lvl[j][L];
+        for (uint32_t L = 1; L < a->D; ++L) n += (m->b_lvl[j][L + 1] > m->b_lvl[j][L]) * (a->prec == 32 ? 2 : 1);
     }
     return n;
 }
@@ -2336,7 +2374,7 @@ static qkc_status memo_pass(qkc_ac *a, qkc_ac::MemoMeta *m, int j, int clamp, in
     cudaGraphExec_t gA, gB;
     if ((st = memo_graph(a, m, j, false, &gA)) || (st = memo_graph(a, m, j, true, &gB))) return st;
     MemoDesc md{n_vec,    j,         clamp, jmask, a->d_pv, a->vec_cap, a->d_VA, m->d_offu + m->offu_base[j],
-                a->d_sigma, m->d_emask + (size_t)j * a->E, m->d_eoff + (size_t)j * a->E,
+                a->d_sigma, m->d_emask + (size_t)j * a->E, m->d_brec + m->br_base[j],
                 m->d_kplan + m->kp_base[j], m->d_aplan + m->ap_base[j], m->d_bplan + m->bp_base[j],
                 (int32_t)m->bp_cnt[j], a->d_keys, a->tile};
     set_memo_desc<<<1, 1, 0, s>>>(a->d_mdesc, md);
