@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
     ap.add_argument("--shots", type=int, default=None, help="samples per vector (qaoa32: 10000, vqe: 1000)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["step", "uppass", "gradpass", "samplepass"], default="step",
+    ap.add_argument("--mode", choices=["step", "uppass", "gradpass", "samplepass", "reeval"], default="step",
                     help="uppass: only the upward pass over --columns sampling-prefix columns; gradpass: "
                          "upward + downward pass (gradient) over --columns Z-string columns; samplepass: one "
                          "sampling call over --vectors vectors x --shots shots (profiling cases)")
@@ -168,7 +168,32 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- oracle timing (CPU baseline / reference arm)
-def oracle_rate(W, ac_bytes, budget_s=12.0):
+def _oracle_sampler(job):
+    """One host process of the all-cores baseline: the oracle's chain-rule samples (vector 0 of the
+    workload) for `seconds`, from its own seed range; returns the number drawn."""
+    ac_bytes, angles, seed, seconds = job
+    from oracle import acref as R
+    ref = R.ACRef(ac_bytes)
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds or n == 0:
+        ref.sample(angles, seed + n, 4)
+        n += 4
+    return n, time.perf_counter() - t0
+
+
+def oracle_all_cores(W, ac_bytes, seconds=6.0):
+    """The oracle as it stands, one process per host core (a spawn-started pool: no process is
+    forked from one that holds a CUDA context); aggregate chain-rule samples per second."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    a = W["angles"][0]
+    jobs = [(ac_bytes, a, int(W["seeds"][0]) + (i << 32), seconds) for i in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_sampler, jobs)
+    return sum(n for n, _ in res) / max(t for _, t in res), cores
+
+
+def oracle_rate(W, ac_bytes, budget_s=12.0, all_cores=True):
     """Time the oracle as it stands (acref.c, FP64, one host core) on a bounded sample of
     the workload: the per-vector gradient columns, then samples until the budget."""
     from oracle import acref as R
@@ -189,10 +214,20 @@ def oracle_rate(W, ac_bytes, budget_s=12.0):
         n_s += 4
     t_s = (time.perf_counter() - t1) / n_s
     per_vec = t_grad + W["shots"] * t_s
-    return dict(value=W["shots"] / per_vec, unit=W["unit"], cores=1, kind="oracle",
-                sample=(f"1 vector: {T} gradient columns ({t_grad:.2f} s) + {n_s} chain-rule samples "
-                        f"({t_s * 1e3:.1f} ms each) on acref.c, FP64, one core; rate = {W['shots']} samples / "
-                        f"(gradient + {W['shots']} x per-sample time)"))
+    one_core = W["shots"] / per_vec
+    if not all_cores:
+        return dict(value=one_core, unit=W["unit"], cores=1, kind="oracle",
+                    sample=(f"1 vector: {T} gradient columns ({t_grad:.2f} s) + {n_s} chain-rule samples "
+                            f"({t_s * 1e3:.1f} ms each) on acref.c, FP64, one core; rate = {W['shots']} samples / "
+                            f"(gradient + {W['shots']} x per-sample time)"))
+    agg, cores = oracle_all_cores(W, ac_bytes)
+    # all cores: samples at the aggregate rate, the gradient columns split over the cores
+    per_vec_all = t_grad / cores + W["shots"] / agg
+    return dict(value=W["shots"] / per_vec_all, unit=W["unit"], cores=cores, kind="oracle",
+                sample=(f"1 vector: {T} gradient columns ({t_grad:.2f} s on one core, counted / {cores}) + "
+                        f"chain-rule samples on {cores} spawned processes ({agg:.1f} samples/s together) on "
+                        f"acref.c, FP64; one core alone: {one_core:.2f} samples/s "
+                        f"({t_s * 1e3:.1f} ms per sample)"))
 
 
 def run_reference(args):
@@ -214,7 +249,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": W["name"]},
-            "cpu_baseline": {"value": val, "unit": W["unit"], "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": val, "unit": W["unit"], "cores": rates[-1]["cores"], "kind": "oracle",
                              "sample": rates[-1]["sample"]},
             "e2e": {"value": val, "unit": W["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -376,12 +411,19 @@ def run_ours(args):
         def gbs(kind):
             return stats[kind + "_bytes"] / (stats[kind + "_ms"] * 1e6) if stats[kind + "_ms"] > 0 else None
 
+        # per-kind (algorithmic bytes, event ms, timed chains): the memoised pass splits into its tiers
+        kinds = {"up": (stats["up_bytes"], stats["up_ms"], stats["up_passes"]),
+                 "down": (stats["down_bytes"], stats["down_ms"], stats["down_passes"]),
+                 "memo_b": (stats["memo_bytes"] - stats["memo_a_bytes"], stats["memo_ms"] - stats["memo_a_ms"],
+                            stats["memo_passes"]),
+                 "memo_a": (stats["memo_a_bytes"], stats["memo_a_ms"], stats["memo_passes"])}
         names = {"up": "up_level_f32 (upward pass)", "down": "down_light_f32/down_heavy_f32 (downward pass)",
-                 "memo": "memoA_level/memoB_level_f32 (memoised sampling pass)"}
-        dom = max(("up", "down", "memo"), key=lambda k: stats[k + "_ms"])
-        ach = gbs(dom)
-        launches_dom = max(1, stats.get(dom + "_passes", 1))
-        per_launch_bytes = stats[dom + "_bytes"] / launches_dom
+                 "memo_b": "memoB_level_f32 (tier B of the memoised sampling pass: per group column; with its "
+                           "scale and group-key kernels)",
+                 "memo_a": "memoA_level<float2> (tier A of the memoised sampling pass: per (vector, key) slot)"}
+        dom = max(kinds, key=lambda k: kinds[k][1])
+        ach = kinds[dom][0] / (kinds[dom][1] * 1e6) if kinds[dom][1] > 0 else None
+        per_launch_bytes = kinds[dom][0] / max(1, kinds[dom][2])
         up_gbs, dn_gbs, memo_gbs = gbs("up"), gbs("down"), gbs("memo")
         # edge evaluations the per-column method would do for the same queries
         edge_evals = info["n_edges"] * (stats["up_columns"] + stats["down_columns"] + stats["memo_columns"])
@@ -394,11 +436,14 @@ def run_ours(args):
                        "ac_edges": info["n_edges"], "ac_levels": info["n_levels"],
                        "precision": "complex FP32 nodes, power-of-two scale per (level, column); FP64 decisions",
                        "sampler": args.sampler,
-                       "l2": "inputs larger than L2: node buffer = nodes x tile columns x 8 B "
-                             f"({info['n_nodes'] * info['reserved_columns'] * 8 / 1e9:.1f} GB)"},
+                       "l2": "inputs larger than L2: the sampling AC's value tile holds "
+                             f"{sac.info()['reserved_columns']} group columns of its tier-B nodes (GBs) and "
+                             "the tier-A slots of 64 vectors up to key width 12 are tens of GB"},
             "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": ach, "peak": hbm, "unit": "GB/s",
                          "frac": (ach / hbm) if ach else None, "peak_source": peak_src,
-                         "bytes_per_pass": per_launch_bytes, "traffic": None,
+                         "bytes_per_launch": per_launch_bytes, "launch": "one event-timed chain (all tiles of "
+                         "one sampling step for the memoised tiers, one column tile for up/down)",
+                         "traffic": None,
                          "up_pass_gbs": up_gbs, "down_pass_gbs": dn_gbs, "memo_pass_gbs": memo_gbs,
                          "memo_tier_a_gbs": (stats["memo_a_bytes"] / (stats["memo_a_ms"] * 1e6)
                                              if stats["memo_a_ms"] > 0 else None),
@@ -473,6 +518,61 @@ def run_samplepass(args):
                       "tier_a_gbs": st["memo_a_bytes"] / (st["memo_a_ms"] * 1e6) if st["memo_a_ms"] > 0 else None,
                       "tier_b_gbs": (st["memo_bytes"] - st["memo_a_bytes"]) / (b_ms * 1e6) if b_ms > 0 else None,
                       "up_ms": st["up_ms"]}), flush=True)
+
+
+def run_reeval(args):
+    """Incremental re-evaluation (qkc_reevaluate) against a full upward pass: the workload's
+    Z-string columns for 64 vectors are evaluated once; then every angle slot in turn is moved
+    (all vectors) and re-evaluated incrementally. Reports the time per slot update against a
+    full qkc_evaluate of the same columns, and checks the values against a full evaluation."""
+    import torch
+    from paper_2103_17226_gb300.build import build_library
+    build_library()
+    from paper_2103_17226_gb300 import native as N
+    W = make_workload(args.workload, args.shots)
+    c = W["circuit"]
+    V = min(64, W["V"])
+    ev, cv, w = hamiltonian_columns(dict(W, V=V))
+    ctx = N.Context(0)
+    ac = N.load_ac(ctx, N.compile(c, N.QKC_AC_DENSITY), precision=32)
+    N.reserve(ac, V, len(cv))
+    angles = W["angles"][:V].copy()
+    d_ev, d_cv = torch.tensor(ev, device="cuda"), torch.tensor(cv, device="cuda")
+    N.set_params(ac, torch.tensor(angles, device="cuda"))
+    for _ in range(3):
+        N.evaluate(ac, d_cv, d_ev)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        full = N.evaluate(ac, d_cv, d_ev)
+    e1.record()
+    torch.cuda.synchronize()
+    t_full = e0.elapsed_time(e1) / 5
+    slots = list(range(c.n_angles))
+    d_angles = []
+    for k in slots:  # angles after moving slots 0..k in turn
+        angles[:, k] += 0.25
+        d_angles.append(torch.tensor(angles, device="cuda"))
+    N.reevaluate(ac, 0, d_cv, len(cv))  # same angles as evaluated: builds slot 0's cone outside the timing
+    for k in slots[1:]:
+        N.reevaluate(ac, k, d_cv, len(cv))  # every slot's dirty cone, built once
+    torch.cuda.synchronize()
+    N.set_params(ac, torch.tensor(W["angles"][:V], device="cuda"))
+    N.evaluate(ac, d_cv, d_ev)
+    torch.cuda.synchronize()
+    e0.record()
+    for k in slots:
+        N.set_params(ac, d_angles[k])
+        out = N.reevaluate(ac, k, d_cv, len(cv))
+    e1.record()
+    torch.cuda.synchronize()
+    t_inc = e0.elapsed_time(e1) / len(slots)
+    ref = N.evaluate(ac, d_cv, d_ev)
+    err = float((out - ref).abs().max())
+    print(json.dumps({"mode": "reeval", "workload": W["name"], "columns": len(cv), "angle_slots": len(slots),
+                      "full_evaluate_ms": t_full, "reevaluate_ms_per_slot": t_inc, "speedup": t_full / t_inc,
+                      "max_abs_diff_vs_full": err}), flush=True)
 
 
 def run_uppass(args):
@@ -612,6 +712,9 @@ def main():
         return
     if args.mode == "samplepass":
         run_samplepass(args)
+        return
+    if args.mode == "reeval":
+        run_reeval(args)
         return
     if args.impl == "reference":
         run_reference(args)

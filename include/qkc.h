@@ -211,6 +211,26 @@ qkc_status qkc_evaluate(qkc_ac *ac, const int32_t *col_vec_dev, const int8_t *ev
                         int64_t n_cols, double *out_dev, void *stream);
 
 /*
+ * qkc_reevaluate -- incremental upward pass after a parameter update that
+ * touched one angle slot (memoisation across queries, Sec. 3.2.2: the AC is
+ * compiled once and re-evaluated as parameters change; here only the part that
+ * changed is recomputed).  Call it after qkc_set_params has bound new angles
+ * that differ from those of the preceding evaluation in slot angle_slot only;
+ * it binds that slot's parameter leaves again, recomputes their ancestors (the
+ * slot's "dirty cone", found on first use of the slot and kept) for the columns
+ * of the preceding qkc_evaluate, and writes out_dev[c] as qkc_evaluate would.
+ * Preconditions, checked where the library can: the previous call on this AC
+ * that touched its node values was qkc_evaluate or qkc_reevaluate with the same
+ * col_vec_dev pointer (same contents) and n_cols, and n_cols fits one tile
+ * (qkc_get_info's reserved columns; see qkc_reserve); else QKC_ERR_ARG.  The
+ * caller must not have changed any other angle slot.  FP64: the same values
+ * as a fresh qkc_evaluate; FP32: each level keeps the scale exponent of the
+ * preceding pass, so values agree with a fresh pass up to rounding.
+ */
+qkc_status qkc_reevaluate(qkc_ac *ac, int32_t angle_slot, const int32_t *col_vec_dev, int64_t n_cols,
+                          double *out_dev, void *stream);
+
+/*
  * qkc_marginals -- upward then downward pass (Sec. 3.3.2, the differential
  * approach the paper cites): marg_dev[c][i] = d f / d lambda_i for every
  * indicator leaf i (n_ind of them, (variable, value) order) as (re, im)

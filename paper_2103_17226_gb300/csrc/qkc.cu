@@ -368,6 +368,115 @@ __global__ void __launch_bounds__(TPB) up_level_f64(DevAC ac, LevelArgs a, const
     }
 }
 
+// ------------------------------------------------------------------ incremental upward pass
+// After qkc_set_params changed one angle slot: the slot's parameter leaves are bound again and
+// only their ancestors (the slot's dirty cone, by level) are recomputed over the tile of the
+// preceding evaluation, with the arithmetic of up_level_*; every other node keeps its value
+// and every level keeps its FP32 scale.
+template <typename C>
+__global__ void rebind_param_leaves(const uint32_t *leaves, int nleaves, const PassDesc *pd, int64_t pitch, C *V,
+                                    int n_ind) {
+    const PassDesc d = *pd;
+    const int64_t ncols = desc_cols(d);
+    const C *pv = static_cast<const C *>(d.pv);
+    const int64_t total = (int64_t)nleaves * ncols;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / ncols, c = t - i * ncols;
+        const uint32_t leaf = leaves[i];
+        V[(int64_t)leaf * pitch + c] = pv[(int64_t)(leaf - n_ind) * d.pv_pitch + vec_of(d.es, d.col0 + c)];
+    }
+}
+
+__global__ void __launch_bounds__(TPB) up_list_f32(DevAC ac, LevelArgs a, const uint32_t *nodes, int64_t count,
+                                                    const PassDesc *pd, float2 *__restrict__ V,
+                                                    const int *__restrict__ S) {
+    const int64_t ncols = desc_cols(*pd);
+    if (ncols <= 0 || count <= 0) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nchunks = (ncols + 63) >> 6;
+    const int64_t items = ((count + NB - 1) / NB) * nchunks;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t hp = a.pitch >> 1;
+    float4 *V4 = reinterpret_cast<float4 *>(V);
+    for (int64_t it = wid; it < items; it += nw) {
+        const int64_t chunk = it % nchunks;
+        const int64_t blk = it / nchunks;
+        const int64_t col = chunk * 64 + lane * 2;
+        if (col >= ncols) continue;
+        const int2 sL = *reinterpret_cast<const int2 *>(S + (int64_t)a.L * a.pitch + col);
+        const int64_t k1 = min(count, (blk + 1) * NB);
+        for (int64_t kk = blk * NB; kk < k1; ++kk) {
+            const uint32_t n = nodes[kk];
+            const uint8_t o = ac.op[n];
+            const uint32_t e0 = ac.child_off[n], e1 = ac.child_off[n + 1];
+            float4 r;
+            if (o == OP_MUL) {
+                const uint32_t ca = ac.child[e0], cb = ac.child[e0 + 1];
+                const int la = ac.node_level[ca], lb = ac.node_level[cb];
+                const float4 va = __ldg(V4 + (int64_t)ca * hp + (col >> 1));
+                const float4 vb = __ldg(V4 + (int64_t)cb * hp + (col >> 1));
+                const int2 sa = __ldg(reinterpret_cast<const int2 *>(S + (int64_t)la * a.pitch + col));
+                const int2 sb = __ldg(reinterpret_cast<const int2 *>(S + (int64_t)lb * a.pitch + col));
+                float2 p0 = cmul(make_float2(va.x, va.y), make_float2(vb.x, vb.y));
+                float2 p1 = cmul(make_float2(va.z, va.w), make_float2(vb.z, vb.w));
+                p0 = cscale(p0, pow2f(sa.x + sb.x - sL.x));
+                p1 = cscale(p1, pow2f(sa.y + sb.y - sL.y));
+                r = make_float4(p0.x, p0.y, p1.x, p1.y);
+            } else {
+                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (uint32_t e = e0; e < e1; ++e) {
+                    const uint32_t c = ac.child[e];
+                    const int lc = ac.node_level[c];
+                    const float4 v = __ldg(V4 + (int64_t)c * hp + (col >> 1));
+                    const int2 sc = __ldg(reinterpret_cast<const int2 *>(S + (int64_t)lc * a.pitch + col));
+                    const float f0 = pow2f(sc.x - sL.x), f1 = pow2f(sc.y - sL.y);
+                    acc.x += v.x * f0; acc.y += v.y * f0;
+                    acc.z += v.z * f1; acc.w += v.w * f1;
+                }
+                r = acc;
+            }
+            V4[(int64_t)n * hp + (col >> 1)] = r;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(TPB) up_list_f64(DevAC ac, LevelArgs a, const uint32_t *nodes, int64_t count,
+                                                    const PassDesc *pd, double2 *__restrict__ V) {
+    const int64_t ncols = desc_cols(*pd);
+    if (ncols <= 0 || count <= 0) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nchunks = (ncols + 31) >> 5;
+    const int64_t items = ((count + NB - 1) / NB) * nchunks;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t it = wid; it < items; it += nw) {
+        const int64_t chunk = it % nchunks;
+        const int64_t blk = it / nchunks;
+        const int64_t col = chunk * 32 + lane;
+        if (col >= ncols) continue;
+        const int64_t k1 = min(count, (blk + 1) * NB);
+        for (int64_t kk = blk * NB; kk < k1; ++kk) {
+            const uint32_t n = nodes[kk];
+            const uint8_t o = ac.op[n];
+            const uint32_t e0 = ac.child_off[n], e1 = ac.child_off[n + 1];
+            double2 r;
+            if (o == OP_MUL) {
+                const double2 va = __ldg(V + (int64_t)ac.child[e0] * a.pitch + col);
+                const double2 vb = __ldg(V + (int64_t)ac.child[e0 + 1] * a.pitch + col);
+                r = cmul(va, vb);
+            } else {
+                r = make_double2(0.0, 0.0);
+                for (uint32_t e = e0; e < e1; ++e) {
+                    const double2 v = __ldg(V + (int64_t)ac.child[e] * a.pitch + col);
+                    r.x += v.x; r.y += v.y;
+                }
+            }
+            V[(int64_t)n * a.pitch + col] = r;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ downward pass, split by fan-out
 // Per level, nodes whose parent lists hold at most HEAVY entries are "light": a warp owns NB
 // of them x one column chunk and walks each parent list four entries at a time (independent
@@ -1277,6 +1386,18 @@ struct qkc_ac {
     std::vector<uint32_t> var_card;               // cardinality of every indicator variable
     std::vector<uint32_t> h_child_off, h_child;  // host copy of the structure (density ACs)
     std::vector<uint8_t> h_op;  // node ops (host copy, memoised-pass metadata)
+    std::vector<int32_t> h_param_angle;  // angle slot of every parameter leaf
+    // incremental re-evaluation: the dirty cone of every angle slot (built on first use), and
+    // whether the tile still holds the last qkc_evaluate's values (one tile, its columns)
+    struct DirtyCone {
+        uint32_t *d_nodes = nullptr, *d_leaves = nullptr;
+        std::vector<int64_t> lvl;  // [D + 1] offsets of each level's nodes in d_nodes
+        int nleaves = 0;
+    };
+    std::vector<DirtyCone *> cones;
+    bool eval_ok = false;
+    int64_t eval_cols = 0;
+    const int32_t *eval_colvec = nullptr;
     uint64_t *d_sigma = nullptr;
     MemoDesc *d_mdesc = nullptr;
     struct GraphSlot { cudaGraphExec_t exec = nullptr; const void *V = nullptr, *A = nullptr; int64_t pitch = 0; };
@@ -1288,7 +1409,7 @@ struct qkc_ac {
         std::vector<std::vector<uint8_t>> floor0;               // per step, [D]
         std::vector<int64_t> a_base, b_base, offu_base, g_base;  // per step
         std::vector<double> a_bytes_slot, b_bytes_col;           // per step: algorithmic bytes per slot unit / column
-        uint32_t *d_a_nodes = nullptr, *d_b_nodes = nullptr;
+        uint32_t *d_a_nodes = nullptr;
         MemoAGroup *d_a_grp = nullptr;  // tier-A key-width groups, per step and level
         int64_t *d_offu = nullptr;
         uint32_t *d_emask = nullptr;    // [step][edge]: a child's key bits inside its tier-A parent's key
@@ -1389,11 +1510,13 @@ extern "C" void qkc_free_ac(qkc_ac *a) {
     cudaFree(a->d_desc);
     cudaFree(a->d_status);
     cudaFree(a->d_sigma);
+    for (auto *c : a->cones)
+        if (c) { cudaFree(c->d_nodes); cudaFree(c->d_leaves); delete c; }
     cudaFree(a->d_mdesc);
     cudaFree(a->d_VA);
     for (auto *m : a->memo) {
         if (!m) continue;
-        cudaFree(m->d_a_nodes); cudaFree(m->d_b_nodes); cudaFree(m->d_a_grp); cudaFree(m->d_offu);
+        cudaFree(m->d_a_nodes); cudaFree(m->d_a_grp); cudaFree(m->d_offu);
         cudaFree(m->d_emask); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
         for (auto &g : m->gA) if (g.exec) cudaGraphExecDestroy(g.exec);
         for (auto &g : m->gB) if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -1599,14 +1722,15 @@ extern "C" qkc_status qkc_load_ac(qkc_ctx *ctx, const uint8_t *bytes, uint64_t l
         qkc_free_ac(a);
         return st;
     }
+    a->h_child_off = coff;  // host copy of the structure (memoised passes, dirty cones)
+    a->h_child = child;
+    a->h_op = op;
+    a->h_param_angle = p_angle;
     if (kind == QKC_AC_DENSITY || kind == QKC_AC_DENSITY_STEPS) {  // indicator supports (memoised sampling)
         a->sigma.assign(N, 0ull);
         for (uint32_t i = 0; i < nind; ++i) a->sigma[i] = 1ull << (uint32_t)ind_var[i];
         for (uint32_t i = nl; i < N; ++i)
             for (uint32_t e = coff[i]; e < coff[i + 1]; ++e) a->sigma[i] |= a->sigma[child[e]];
-        a->h_child_off = coff;
-        a->h_child = child;
-        a->h_op = op;
         if ((st = upload(&a->d_sigma, a->sigma.data(), N, b))) {
             qkc_free_ac(a);
             return st;
@@ -1666,6 +1790,7 @@ static qkc_status ensure_tile(qkc_ac *a, int64_t cols, uint32_t rows = 0) {
     want = std::min(want, cap);
     if (want <= a->tile && rows <= a->vrows) return QKC_OK;
     QKC_CUDA(cudaDeviceSynchronize());
+    a->eval_ok = false;
     cudaFree(a->d_V); cudaFree(a->d_A); cudaFree(a->d_S); cudaFree(a->d_obs); cudaFree(a->d_keys);
     a->d_V = a->d_A = nullptr; a->d_S = a->d_obs = nullptr; a->d_keys = nullptr; a->tile = 0; a->adj_ok = false;
     cudaError_t e1 = cudaMalloc(&a->d_V, (size_t)rows * want * a->elem());
@@ -1945,6 +2070,7 @@ extern "C" qkc_status qkc_evaluate(qkc_ac *a, const int32_t *col_vec, const int8
                                    double *out, void *stream) {
     qkc_status st = check_query(a, col_vec, ev, n_cols, "qkc_evaluate");
     if (st) return st;
+    a->eval_ok = false;
     if (n_cols == 0) return QKC_OK;
     if (!out) return fail(QKC_ERR_ARG, "qkc_evaluate: out is null");
     QKC_CUDA(cudaSetDevice(a->ctx->device));
@@ -1957,6 +2083,97 @@ extern "C" qkc_status qkc_evaluate(qkc_ac *a, const int32_t *col_vec, const int8
         if ((st = run_roots(a, c0, nc, nullptr, s))) return st;
     }
     QKC_CUDA(cudaMemcpyAsync(out, a->d_root, sizeof(double2) * n_cols, cudaMemcpyDeviceToDevice, s));
+    a->eval_ok = n_cols <= a->tile;  // one tile: its node values stay for qkc_reevaluate
+    a->eval_cols = n_cols;
+    a->eval_colvec = col_vec;
+    return QKC_OK;
+}
+
+// The dirty cone of angle slot k: its parameter leaves and every node above one of them, by level.
+static qkc_status dirty_cone(qkc_ac *a, int k, qkc_ac::DirtyCone **out) {
+    if (a->cones.empty()) a->cones.assign(a->n_angles, nullptr);
+    if (a->cones[k]) {
+        *out = a->cones[k];
+        return QKC_OK;
+    }
+    const uint32_t N = a->N, D = a->D;
+    std::vector<char> dirty(N, 0);
+    std::vector<uint32_t> leaves, nodes;
+    for (uint32_t i = 0; i < a->n_param; ++i)
+        if (a->h_param_angle[i] == k) {
+            dirty[a->n_ind + i] = 1;
+            leaves.push_back(a->n_ind + i);
+        }
+    auto *c = new qkc_ac::DirtyCone;
+    c->lvl.assign(D + 1, 0);
+    for (uint32_t L = 1; L < D; ++L) {  // children sit on lower levels, so one sweep by level suffices
+        for (uint32_t n = a->level_off[L]; n < a->level_off[L + 1]; ++n) {
+            for (uint32_t e = a->h_child_off[n]; e < a->h_child_off[n + 1] && !dirty[n]; ++e)
+                if (dirty[a->h_child[e]]) dirty[n] = 1;
+            if (dirty[n]) nodes.push_back(n);
+        }
+        c->lvl[L + 1] = (int64_t)nodes.size();
+    }
+    c->nleaves = (int)leaves.size();
+    int64_t b = 0;
+    qkc_status st;
+    if ((st = upload(&c->d_nodes, nodes.data(), nodes.size(), b)) ||
+        (st = upload(&c->d_leaves, leaves.data(), leaves.size(), b))) {
+        cudaFree(c->d_nodes);
+        cudaFree(c->d_leaves);
+        delete c;
+        return st;
+    }
+    a->cones[k] = c;
+    *out = c;
+    return QKC_OK;
+}
+
+extern "C" qkc_status qkc_reevaluate(qkc_ac *a, int32_t angle_slot, const int32_t *col_vec, int64_t n_cols,
+                                     double *out, void *stream) {
+    if (!a || n_cols < 0 || (n_cols > 0 && !out) || angle_slot < 0 || angle_slot >= (int32_t)a->n_angles)
+        return fail(QKC_ERR_ARG, "qkc_reevaluate: bad argument");
+    if (n_cols == 0) return QKC_OK;
+    if (!a->eval_ok || a->eval_cols != n_cols || a->eval_colvec != col_vec)
+        return fail(QKC_ERR_ARG, "qkc_reevaluate: must follow qkc_evaluate (or qkc_reevaluate) on this AC with the "
+                                 "same col_vec and n_cols, within one tile, and no other pass in between");
+    QKC_CUDA(cudaSetDevice(a->ctx->device));
+    qkc_ac::DirtyCone *cone = nullptr;
+    qkc_status st = dirty_cone(a, angle_slot, &cone);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    EvSrc es{nullptr, nullptr, 0, 0, col_vec, nullptr, std::max<int64_t>(1, a->n_vec)};
+    set_desc<<<1, 1, 0, s>>>(a->d_desc, PassDesc{es, a->d_pv, a->vec_cap, 0, n_cols});
+    ++a->launches;
+    const DevAC d = a->dev();
+    const int64_t pitch = a->tile;
+    if (cone->nleaves > 0) {
+        const unsigned g = grid_for((int64_t)cone->nleaves * n_cols);
+        if (a->prec == 32)
+            rebind_param_leaves<float2><<<g, TPB, 0, s>>>(cone->d_leaves, cone->nleaves, a->d_desc, pitch,
+                                                          (float2 *)a->d_V, (int)a->n_ind);
+        else
+            rebind_param_leaves<double2><<<g, TPB, 0, s>>>(cone->d_leaves, cone->nleaves, a->d_desc, pitch,
+                                                           (double2 *)a->d_V, (int)a->n_ind);
+        ++a->launches;
+    }
+    const int sms = a->ctx->sm_count;
+    for (uint32_t L = 1; L < a->D; ++L) {
+        const int64_t i0 = cone->lvl[L], i1 = cone->lvl[L + 1];
+        if (i1 == i0) continue;
+        const int64_t cw = a->prec == 32 ? 64 : 32;
+        const int64_t items = ((i1 - i0 + NB - 1) / NB) * ((n_cols + cw - 1) / cw);
+        const unsigned g = grid_for(items * 32, TPB, (int64_t)sms * 8);
+        LevelArgs la{0, 0, (int)L, pitch};
+        if (a->prec == 32)
+            up_list_f32<<<g, TPB, 0, s>>>(d, la, cone->d_nodes + i0, i1 - i0, a->d_desc, (float2 *)a->d_V, a->d_S);
+        else
+            up_list_f64<<<g, TPB, 0, s>>>(d, la, cone->d_nodes + i0, i1 - i0, a->d_desc, (double2 *)a->d_V);
+        ++a->launches;
+    }
+    QKC_LAUNCH_CHECK();
+    if ((st = run_roots(a, 0, n_cols, nullptr, s))) return st;
+    QKC_CUDA(cudaMemcpyAsync(out, a->d_root, sizeof(double2) * n_cols, cudaMemcpyDeviceToDevice, s));
     return QKC_OK;
 }
 
@@ -1964,6 +2181,7 @@ extern "C" qkc_status qkc_marginals(qkc_ac *a, const int32_t *col_vec, const int
                                     double *root_out, double *marg_out, void *stream) {
     qkc_status st = check_query(a, col_vec, ev, n_cols, "qkc_marginals");
     if (st) return st;
+    a->eval_ok = false;
     if (a->kind == QKC_AC_DENSITY_STEPS)  // the downward pass needs the root alone on the top level
         return fail(QKC_ERR_UNSUPPORTED, "qkc_marginals: not on a DENSITY_STEPS AC (use its DENSITY AC)");
     if (n_cols == 0) return QKC_OK;
@@ -1996,6 +2214,7 @@ extern "C" qkc_status qkc_gradient(qkc_ac *a, const int32_t *col_vec, const int8
                                    int64_t n_cols, int64_t n_vectors, double *value, double *grad, void *stream) {
     qkc_status st = check_query(a, col_vec, ev, n_cols, "qkc_gradient");
     if (st) return st;
+    a->eval_ok = false;
     if (a->kind == QKC_AC_DENSITY_STEPS)
         return fail(QKC_ERR_UNSUPPORTED, "qkc_gradient: not on a DENSITY_STEPS AC (use its DENSITY AC)");
     if (!col_vec || !weight || !value || !grad || n_vectors <= 0 || n_vectors > a->n_vec)
@@ -2249,7 +2468,6 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
     int64_t dummy = 0;
     if ((*st = upload(&m->d_a_nodes, an.data(), an.size(), dummy)) ||
         (*st = upload(&m->d_a_grp, grp.data(), grp.size(), dummy)) ||
-        (*st = upload(&m->d_b_nodes, bn.data(), bn.size(), dummy)) ||
         (*st = upload(&m->d_offu, offu.data(), offu.size(), dummy)) ||
         (*st = upload(&m->d_emask, emask.data(), emask.size(), dummy)) ||
         (*st = upload(&m->d_bdesc, bdesc.data(), bdesc.size(), dummy)) ||
@@ -2257,7 +2475,7 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
         (*st = upload(&m->d_kplan, kplan.data(), kplan.size(), dummy)) ||
         (*st = upload(&m->d_aplan, aplan.data(), aplan.size(), dummy)) ||
         (*st = upload(&m->d_bplan, bplan.data(), bplan.size(), dummy))) {
-        cudaFree(m->d_a_nodes); cudaFree(m->d_a_grp); cudaFree(m->d_b_nodes); cudaFree(m->d_offu);
+        cudaFree(m->d_a_nodes); cudaFree(m->d_a_grp); cudaFree(m->d_offu);
         cudaFree(m->d_emask); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
         delete m;
         return nullptr;
@@ -2418,6 +2636,7 @@ extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t
     if (a->kind != QKC_AC_DENSITY && a->kind != QKC_AC_DENSITY_STEPS)
         return fail(QKC_ERR_UNSUPPORTED, "qkc_sample: needs a DENSITY or DENSITY_STEPS AC");
     if (n_vec > a->n_vec && a->n_param > 0) return fail(QKC_ERR_ARG, "qkc_sample: more vectors than bound");
+    a->eval_ok = false;
     if (max_shots == 0) return QKC_OK;
     if (n_vec * max_shots > (int64_t)INT32_MAX / 2) return fail(QKC_ERR_ARG, "qkc_sample: too many samples");
     QKC_CUDA(cudaSetDevice(a->ctx->device));
@@ -2553,6 +2772,7 @@ extern "C" qkc_status qkc_gibbs(qkc_ac *a, const int32_t *col_vec, const uint64_
                                 void *stream) {
     qkc_status st = check_query(a, col_vec, state, n_chains, "qkc_gibbs");
     if (st) return st;
+    a->eval_ok = false;
     if (a->kind != QKC_AC_AMPLITUDE) return fail(QKC_ERR_UNSUPPORTED, "qkc_gibbs: needs an AMPLITUDE AC");
     if (!seeds || n_sweeps < 0 || sweep_offset < 0) return fail(QKC_ERR_ARG, "qkc_gibbs: bad argument");
     if (n_chains == 0 || n_sweeps == 0) return QKC_OK;

@@ -70,6 +70,7 @@ def lib():
         "qkc_set_tile_limit": [P, I64],
         "qkc_set_params": [P, P, I64, P],
         "qkc_evaluate": [P, P, P, I64, P, P],
+        "qkc_reevaluate": [P, I32, P, I64, P, P],
         "qkc_marginals": [P, P, P, I64, P, P, P],
         "qkc_gradient": [P, P, P, P, I64, I64, P, P, P],
         "qkc_sample": [P, P, P, I64, I64, I64, P, P],
@@ -254,6 +255,16 @@ def evaluate(ac: AC, col_vec, evidence, out=None, stream=None):
     if out is None:
         out = torch.empty((n, 2), dtype=torch.float64, device=evidence.device)
     _check(lib().qkc_evaluate(ac._h, _ptr(col_vec), _ptr(evidence), n, _ptr(out), _stream(stream)))
+    return out
+
+
+def reevaluate(ac: AC, angle_slot: int, col_vec, n_cols: int, out=None, stream=None):
+    """qkc_reevaluate: after set_params changed one angle slot, recompute only the nodes that depend
+    on it, for the columns of the preceding evaluate (same col_vec tensor); float64 [n_cols][2]."""
+    import torch
+    if out is None:
+        out = torch.empty((n_cols, 2), dtype=torch.float64, device=col_vec.device)
+    _check(lib().qkc_reevaluate(ac._h, int(angle_slot), _ptr(col_vec), int(n_cols), _ptr(out), _stream(stream)))
     return out
 
 

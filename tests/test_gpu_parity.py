@@ -566,3 +566,57 @@ def test_light_cone_step_ac_evaluate_and_unsupported_calls(cuda_ctx, prec):
             with pytest.raises(Exception):
                 N().gradient(ac, t(cv), t(ev), t(np.ones(32)), V)
     assert np.abs(vals[0] - vals[1]).max() < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_reevaluate_after_one_angle_update(cuda_ctx, prec):
+    """qkc_reevaluate recomputes only the dirty cone of the changed angle slot: after each of a chain
+    of one-slot updates its values equal a fresh qkc_evaluate at the same angles (FP64 exactly,
+    FP32 within the FP32 tolerance) and the density-matrix oracle's."""
+    c = I.hardware_efficient_ansatz(4, 2, I.NOISE_CFG3)
+    n, V = c.n_qubits, 3
+    angs = I.uniform_angles(V, c.n_angles, seed=31).copy()
+    ac = N().load_ac(cuda_ctx, N().compile(c, 1), precision=prec)
+    fresh = N().load_ac(cuda_ctx, N().compile(c, 1), precision=prec)
+    ev = np.array([[(x >> (n - 1 - j)) & 1 for j in range(n)] for x in range(2 ** n)] * V, dtype=np.int8)
+    cv_h = np.repeat(np.arange(V, dtype=np.int32), 2 ** n)
+    cv, ev_d = t(cv_h), t(ev)
+    N().set_params(ac, t(angs))
+    N().evaluate(ac, cv, ev_d)
+    rng = I.SplitMix(77)
+    for step in range(8):
+        k = rng.randint(c.n_angles)
+        angs[:, k] = angs[:, k] + 0.3 + 0.1 * step
+        N().set_params(ac, t(angs))
+        got = N().reevaluate(ac, k, cv, len(cv_h)).cpu().numpy()
+        N().set_params(fresh, t(angs))
+        ref = N().evaluate(fresh, cv, ev_d).cpu().numpy()
+        if prec == 64:
+            assert np.array_equal(got, ref), (step, k)
+        else:
+            assert np.abs(got - ref).max() < TOL[32]
+        for v in range(V):
+            P = Q.probabilities(c, angs[v])
+            assert np.abs(got[v * 2 ** n:(v + 1) * 2 ** n, 0] - P).max() < TOL[prec]
+
+
+def test_reevaluate_preconditions(cuda_ctx):
+    """qkc_reevaluate refuses to run without a preceding evaluation of the same columns, after any
+    other pass, and for an angle slot out of range."""
+    c = I.hardware_efficient_ansatz(3, 1, None)
+    ac = N().load_ac(cuda_ctx, N().compile(c, 1), precision=64)
+    angs = I.uniform_angles(2, c.n_angles, seed=5)
+    N().set_params(ac, t(angs))
+    cv = t(np.array([0, 1, 1], dtype=np.int32))
+    ev = t(np.full((3, 3), -1, dtype=np.int8))
+    with pytest.raises(Exception):
+        N().reevaluate(ac, 0, cv, 3)
+    N().evaluate(ac, cv, ev)
+    N().reevaluate(ac, 0, cv, 3)
+    with pytest.raises(Exception):
+        N().reevaluate(ac, c.n_angles, cv, 3)
+    with pytest.raises(Exception):
+        N().reevaluate(ac, 0, cv, 2)
+    N().marginals(ac, cv, ev)
+    with pytest.raises(Exception):
+        N().reevaluate(ac, 0, cv, 3)
