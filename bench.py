@@ -624,9 +624,13 @@ def run_serve(args):
             circs[f"qaoa{n}_g{g}"] = I.qaoa_maxcut(n, I.random_regular_graph(n, 3, seed=40 + n + 100 * g), 1,
                                                   I.NOISE_CFG2, name=f"qaoa{n}_g{g}")
     acs = {k: N.compile(c, N.QKC_AC_DENSITY) for k, c in circs.items()}
+    # ours samples from the light-cone step ACs (--sampler lightcone, the default) or the density ACs
+    ours = ({k: N.compile(c, N.QKC_AC_DENSITY_STEPS) for k, c in circs.items()} if args.sampler == "lightcone"
+            else acs)
     reqs = poisson_requests(list(acs), {k: c.n_angles for k, c in circs.items()}, args.rate, args.duration, seed=4)
     ctx = N.Context(0)
-    srv = Server(ctx, acs, precision=32, lanes=2, max_batch=32, max_shots=10000, tile_columns=8192)
+    srv = Server(ctx, ours, precision=32, lanes=2, max_batch=32, max_shots=10000, tile_columns=8192,
+                 memoised=args.sampler != "plain")
     res, st = srv.run(reqs, time_limit=args.duration * 4)
     del srv
     torch.cuda.empty_cache()
@@ -635,7 +639,7 @@ def run_serve(args):
     res_b, st_b = base.run(reqs, time_limit=args.duration * 4)
     print(json.dumps({"metric": "serving samples/s and p50/p99 latency", "workload": "serve_qaoa_8acs",
                       "rate_per_s": args.rate, "duration_s": args.duration, "requests": len(reqs),
-                      "ours_fp32_continuous": st, "baseline_fp64_one_at_a_time": st_b,
+                      "sampler": args.sampler, "ours_fp32_continuous": st, "baseline_fp64_one_at_a_time": st_b,
                       "ac_nodes": {k: N.header(b)["n_nodes"] for k, b in acs.items()}}), flush=True)
 
 
