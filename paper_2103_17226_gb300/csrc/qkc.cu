@@ -757,7 +757,8 @@ constexpr int MEMO_QUAD_K = 7;
 // One level of tier A: a thread per slot, or per four slots of one node, of the level's tier-A
 // blocks (vector, node, key).
 template <typename C>
-__global__ void __launch_bounds__(TPB) memoA_level(DevAC ac, const MemoDesc *mdp, const uint32_t *nodes,
+__global__ void __launch_bounds__(TPB, sizeof(C) == 8 ? 8 : 1) memoA_level(DevAC ac, const MemoDesc *mdp,
+                                                                          const uint32_t *nodes,
                                                     const MemoAGroup *grp, int ng, int64_t u0, uint32_t T) {
     if (T == 0 || ng <= 0) return;
     const MemoDesc md = *mdp;
@@ -863,7 +864,7 @@ __global__ void memo_keys(const PassDesc *pd, const MemoDesc *mdp) {
 }
 
 // One level of tier B (FP32): as up_level_f32 over a node list, tier-A children read by key.
-__global__ void __launch_bounds__(TPB, 4) memoB_level_f32(LevelArgs a, const uint2 *bdesc, int64_t count,
+__global__ void __launch_bounds__(TPB, 5) memoB_level_f32(LevelArgs a, const uint2 *bdesc, int64_t count,
                                                         const PassDesc *pd, const MemoDesc *mdp,
                                                         float2 *__restrict__ V, const int *__restrict__ S,
                                                         int *__restrict__ obs) {
@@ -875,18 +876,19 @@ __global__ void __launch_bounds__(TPB, 4) memoB_level_f32(LevelArgs a, const uin
     const EvSrc es = pd->es;
     const int64_t col0 = pd->col0;
     const int lane = threadIdx.x & 31;
-    const int64_t nchunks = (ncols + 63) >> 6;
-    const int64_t items = ((count + NB - 1) / NB) * nchunks;
-    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // work items (node block, column chunk) in 32 bits: blocks < 2^28, chunks < 2^26
+    const uint32_t nchunks = (uint32_t)((ncols + 63) >> 6);
+    const uint32_t nblk = (uint32_t)((count + NB - 1) / NB);
+    const uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     const int64_t hp = a.pitch >> 1;
     float4 *V4 = reinterpret_cast<float4 *>(V);
-    // item it = node block it / nchunks, column chunk it % nchunks, stepped without division
-    int64_t blk = wid / nchunks, chunk = wid % nchunks;
-    const int64_t dq = nw / nchunks, dr = nw % nchunks;
-    for (int64_t it = wid; it < items; it += nw) {
-        const int64_t col = chunk * 64 + lane * 2;
-        const int64_t blk_i = blk;
+    // item = node block * nchunks + column chunk, stepped by the warp count without division
+    uint32_t blk = wid / nchunks, chunk = wid % nchunks;
+    const uint32_t dq = nw / nchunks, dr = nw % nchunks;
+    while (blk < nblk) {
+        const int64_t col = (int64_t)chunk * 64 + lane * 2;
+        const uint32_t blk_i = blk;
         chunk += dr;
         blk += dq;
         if (chunk >= nchunks) {
@@ -895,14 +897,11 @@ __global__ void __launch_bounds__(TPB, 4) memoB_level_f32(LevelArgs a, const uin
         }
         if (col >= ncols) continue;
         const bool two = col + 1 < ncols;
-        const int64_t g0 = col0 + col, g1 = two ? g0 + 1 : g0;
-        const int64_t vec0 = vec_of(es, g0), vec1 = vec_of(es, g1);
-        // prefixes in qubit order (bit q = x_q) so a child's key is extract_bits(prefix, its support)
-        const uint64_t pre0 = md.j ? __brevll(es.prefix[g0] << (64 - md.j)) : 0ull;
-        const uint64_t pre1 = md.j ? __brevll(es.prefix[g1] << (64 - md.j)) : 0ull;
+        const int64_t g0 = col0 + col;
+        const uint32_t vec0 = (uint32_t)vec_of(es, g0), vec1 = (uint32_t)vec_of(es, two ? g0 + 1 : g0);
         const int2 sL = *reinterpret_cast<const int2 *>(S + (int64_t)a.L * a.pitch + col);
         int m0 = -127, m1 = -127;
-        const int64_t k1 = min(count, (blk_i + 1) * NB);
+        const int64_t k1 = min(count, ((int64_t)blk_i + 1) * NB);
         // one child's two column values and scale exponents (tier A: unscaled, exponent 0); the
         // edge record holds the child's tile row or key plan, and its level
         auto child_vals = [&](uint32_t r, float2 &v0, float2 &v1, int &s0, int &s1) {
@@ -925,16 +924,18 @@ __global__ void __launch_bounds__(TPB, 4) memoB_level_f32(LevelArgs a, const uin
                     const uint2 kk = *reinterpret_cast<const uint2 *>(md.keys + (int64_t)mid * md.kpitch + col);
                     key0 = kk.x;
                     key1 = two ? kk.y : kk.x;  // the table holds no key past the last column
-                } else {
+                } else {  // the group prefixes in qubit order (bit q = x_q), compressed to the child's support
+                    const uint64_t pre0 = md.j ? __brevll(es.prefix[g0] << (64 - md.j)) : 0ull;
+                    const uint64_t pre1 = md.j ? __brevll(es.prefix[two ? g0 + 1 : g0] << (64 - md.j)) : 0ull;
                     key0 = plan_key(kp, pre0, narrow);
                     key1 = plan_key(kp, pre1, narrow);
                 }
-                v0 = VA[base + ((vec0 << kc) | (int64_t)key0)];
-                v1 = VA[base + ((vec1 << kc) | (int64_t)key1)];
+                v0 = VA[base + (int64_t)((((uint64_t)vec0) << kc) | key0)];
+                v1 = VA[base + (int64_t)((((uint64_t)vec1) << kc) | key1)];
                 s0 = s1 = 0;
             }
         };
-        for (int64_t kk = blk_i * NB; kk < k1; ++kk) {
+        for (int64_t kk = (int64_t)blk_i * NB; kk < k1; ++kk) {
             const uint2 dsc = __ldg(bdesc + kk);  // (first edge record, degree | op << 24)
             const uint32_t r0 = dsc.x, deg = dsc.y & 0xffffffu, o = dsc.y >> 24;
             float2 q0, q1;
