@@ -67,6 +67,7 @@ namespace {
 
 enum : uint8_t { OP_IND = 0, OP_PARAM = 1, OP_CONST = 2, OP_ADD = 3, OP_MUL = 4 };
 constexpr int NB = 8;          // nodes per warp item
+constexpr int NBB = 16;        // tier-B nodes per warp item (memoised passes)
 constexpr int TPB = 256;       // threads per block
 constexpr int OBS_EMPTY = -1000;
 constexpr int MEMO_BKEYS = 32;  // per step, the distinct tier-A child supports whose group keys are tabled
@@ -878,7 +879,7 @@ __global__ void __launch_bounds__(TPB, 5) memoB_level_f32(LevelArgs a, const uin
     const int lane = threadIdx.x & 31;
     // work items (node block, column chunk) in 32 bits: blocks < 2^28, chunks < 2^26
     const uint32_t nchunks = (uint32_t)((ncols + 63) >> 6);
-    const uint32_t nblk = (uint32_t)((count + NB - 1) / NB);
+    const uint32_t nblk = (uint32_t)((count + NBB - 1) / NBB);
     const uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     const int64_t hp = a.pitch >> 1;
@@ -901,7 +902,7 @@ __global__ void __launch_bounds__(TPB, 5) memoB_level_f32(LevelArgs a, const uin
         const uint32_t vec0 = (uint32_t)vec_of(es, g0), vec1 = (uint32_t)vec_of(es, two ? g0 + 1 : g0);
         const int2 sL = *reinterpret_cast<const int2 *>(S + (int64_t)a.L * a.pitch + col);
         int m0 = -127, m1 = -127;
-        const int64_t k1 = min(count, ((int64_t)blk_i + 1) * NB);
+        const int64_t k1 = min(count, ((int64_t)blk_i + 1) * NBB);
         // one child's two column values and scale exponents (tier A: unscaled, exponent 0); the
         // edge record holds the child's tile row or key plan, and its level
         auto child_vals = [&](uint32_t r, float2 &v0, float2 &v1, int &s0, int &s1) {
@@ -935,7 +936,7 @@ __global__ void __launch_bounds__(TPB, 5) memoB_level_f32(LevelArgs a, const uin
                 s0 = s1 = 0;
             }
         };
-        for (int64_t kk = (int64_t)blk_i * NB; kk < k1; ++kk) {
+        for (int64_t kk = (int64_t)blk_i * NBB; kk < k1; ++kk) {
             const uint2 dsc = __ldg(bdesc + kk);  // (first edge record, degree | op << 24)
             const uint32_t r0 = dsc.x, deg = dsc.y & 0xffffffu, o = dsc.y >> 24;
             float2 q0, q1;
@@ -980,7 +981,7 @@ __global__ void __launch_bounds__(TPB) memoB_level_f64(LevelArgs a, const uint2 
     const int64_t col0 = pd->col0;
     const int lane = threadIdx.x & 31;
     const int64_t nchunks = (ncols + 31) >> 5;
-    const int64_t items = ((count + NB - 1) / NB) * nchunks;
+    const int64_t items = ((count + NBB - 1) / NBB) * nchunks;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int64_t blk = wid / nchunks, chunk = wid % nchunks;
@@ -998,8 +999,8 @@ __global__ void __launch_bounds__(TPB) memoB_level_f64(LevelArgs a, const uint2 
         const int64_t g = col0 + col;
         const int64_t vec = vec_of(es, g);
         const uint64_t pre = md.j ? __brevll(es.prefix[g] << (64 - md.j)) : 0ull;  // qubit order
-        const int64_t k1 = min(count, (blk_i + 1) * NB);
-        for (int64_t kk = blk_i * NB; kk < k1; ++kk) {
+        const int64_t k1 = min(count, (blk_i + 1) * NBB);
+        for (int64_t kk = blk_i * NBB; kk < k1; ++kk) {
             const uint2 dsc = __ldg(bdesc + kk);
             const uint32_t r0 = dsc.x, deg = dsc.y & 0xffffffu, o = dsc.y >> 24;
             double2 r = make_double2(o == OP_MUL ? 1.0 : 0.0, 0.0);
@@ -2527,7 +2528,7 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
                 level_scale_kernel<<<gs, TPB, 0, s>>>(d, (int)L, pitch, m->floor0[j][L], a->d_S, a->d_obs);
             LevelArgs la{(uint32_t)b0, 0, (int)L, pitch};  // lo: the level's first tier-B row
             const int64_t cw = a->prec == 32 ? 64 : 32;
-            const int64_t items = ((b1 - b0 + NB - 1) / NB) * ((pitch + cw - 1) / cw);
+            const int64_t items = ((b1 - b0 + NBB - 1) / NBB) * ((pitch + cw - 1) / cw);
             const unsigned g = grid_for(items * 32, TPB, (int64_t)sms * 8);
             const uint2 *bd = m->d_bdesc + m->b_base[j] + b0;
             if (a->prec == 32)
