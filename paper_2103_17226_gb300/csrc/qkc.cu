@@ -865,7 +865,7 @@ __global__ void memo_keys(const PassDesc *pd, const MemoDesc *mdp) {
 }
 
 // One level of tier B (FP32): as up_level_f32 over a node list, tier-A children read by key.
-__global__ void __launch_bounds__(TPB, 5) memoB_level_f32(LevelArgs a, const uint2 *bdesc, int64_t count,
+__global__ void __launch_bounds__(TPB, 4) memoB_level_f32(LevelArgs a, const uint2 *bdesc, int64_t count,
                                                         const PassDesc *pd, const MemoDesc *mdp,
                                                         float2 *__restrict__ V, const int *__restrict__ S,
                                                         int *__restrict__ obs) {
@@ -905,8 +905,7 @@ __global__ void __launch_bounds__(TPB, 5) memoB_level_f32(LevelArgs a, const uin
         const int64_t k1 = min(count, ((int64_t)blk_i + 1) * NBB);
         // one child's two column values and scale exponents (tier A: unscaled, exponent 0); the
         // edge record holds the child's tile row or key plan, and its level
-        auto child_vals = [&](uint32_t r, float2 &v0, float2 &v1, int &s0, int &s1) {
-            const uint2 rec = __ldg(md.brec + r);
+        auto child_vals = [&](const uint2 rec, float2 &v0, float2 &v1, int &s0, int &s1) {
             const uint32_t eo = rec.x;
             if (eo & 0x80000000u) {  // tier B: the child's row of the tile
                 const float4 v = __ldg(V4 + (int64_t)(eo & 0x7fffffffu) * hp + (col >> 1));
@@ -936,15 +935,26 @@ __global__ void __launch_bounds__(TPB, 5) memoB_level_f32(LevelArgs a, const uin
                 s0 = s1 = 0;
             }
         };
-        for (int64_t kk = (int64_t)blk_i * NBB; kk < k1; ++kk) {
-            const uint2 dsc = __ldg(bdesc + kk);  // (first edge record, degree | op << 24)
+        // the next node's descriptor and first two edge records are loaded one node ahead, so the
+        // descriptor -> record -> value chain of one node overlaps the work of the previous one
+        int64_t kk = (int64_t)blk_i * NBB;
+        uint2 dsc = __ldg(bdesc + kk);  // (first edge record, degree | op << 24)
+        uint2 ra = __ldg(md.brec + dsc.x);
+        uint2 rb = (dsc.y & 0xffffffu) >= 2u ? __ldg(md.brec + dsc.x + 1) : ra;  // a node's own records only
+        for (; kk < k1; ++kk) {
             const uint32_t r0 = dsc.x, deg = dsc.y & 0xffffffu, o = dsc.y >> 24;
+            const uint2 ca = ra, cb = rb;
+            if (kk + 1 < k1) {
+                dsc = __ldg(bdesc + kk + 1);
+                ra = __ldg(md.brec + dsc.x);
+                rb = (dsc.y & 0xffffffu) >= 2u ? __ldg(md.brec + dsc.x + 1) : ra;
+            }
             float2 q0, q1;
             if (o == OP_MUL) {
                 float2 a0, a1, b0, b1;
                 int sa0, sa1, sb0, sb1;
-                child_vals(r0, a0, a1, sa0, sa1);
-                child_vals(r0 + 1, b0, b1, sb0, sb1);
+                child_vals(ca, a0, a1, sa0, sa1);
+                child_vals(cb, b0, b1, sb0, sb1);
                 q0 = cscale(cmul(a0, b0), pow2f(sa0 + sb0 - sL.x));
                 q1 = cscale(cmul(a1, b1), pow2f(sa1 + sb1 - sL.y));
             } else {
@@ -953,7 +963,7 @@ __global__ void __launch_bounds__(TPB, 5) memoB_level_f32(LevelArgs a, const uin
                 for (uint32_t e = 0; e < deg; ++e) {
                     float2 v0, v1;
                     int s0, s1;
-                    child_vals(r0 + e, v0, v1, s0, s1);
+                    child_vals(e == 0 ? ca : e == 1 ? cb : __ldg(md.brec + r0 + e), v0, v1, s0, s1);
                     const float f0 = pow2f(s0 - sL.x), f1 = pow2f(s1 - sL.y);
                     q0.x += v0.x * f0; q0.y += v0.y * f0;
                     q1.x += v1.x * f1; q1.y += v1.y * f1;
