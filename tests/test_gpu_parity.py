@@ -620,3 +620,29 @@ def test_reevaluate_preconditions(cuda_ctx):
     N().marginals(ac, cv, ev)
     with pytest.raises(Exception):
         N().reevaluate(ac, 0, cv, 3)
+
+
+def test_light_cone_step_ac_malformed_bytes(cuda_ctx):
+    """The loader checks a step AC's roots table: a root out of range, a last root that is not the
+    header's root, or a root count that does not match the qubits are format errors."""
+    c = I.workload("qaoa4_ring_p1")
+    b = bytearray(N().compile(c, N().QKC_AC_DENSITY_STEPS))
+    h = np.frombuffer(bytes(b[:64]), dtype="<u4")
+    nv, Nn, E, D, nl, nq = int(h[5]), int(h[6]), int(h[7]), int(h[8]), int(h[9]), int(h[3])
+    off = 64
+    for nbytes in (4 * nv, 4 * nv, 4 * (D + 1), Nn, 4 * (Nn + 1), 4 * E, 4 * nl, 4 * nl, 16 * nl):
+        off = (off + nbytes + 7) & ~7
+    N().load_ac(cuda_ctx, bytes(b), precision=64).close()  # well formed
+    bad = bytearray(b)
+    bad[off:off + 4] = np.array([Nn + 5], dtype="<u4").tobytes()  # root of step 0 out of range
+    with pytest.raises(Exception):
+        N().load_ac(cuda_ctx, bytes(bad), precision=64)
+    bad = bytearray(b)
+    r0 = bytes(b[off:off + 4])
+    bad[off + 4 * (nq - 1):off + 4 * nq] = r0 if r0 != bytes(b[40:44]) else np.array([0], dtype="<u4").tobytes()
+    with pytest.raises(Exception):  # last step root is not the header's root
+        N().load_ac(cuda_ctx, bytes(bad), precision=64)
+    bad = bytearray(b)
+    bad[48:52] = np.array([nq - 1], dtype="<u4").tobytes()  # root count
+    with pytest.raises(Exception):
+        N().load_ac(cuda_ctx, bytes(bad), precision=64)
