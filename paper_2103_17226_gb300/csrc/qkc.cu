@@ -70,6 +70,9 @@ constexpr int NB = 8;          // nodes per warp item
 constexpr int NBB = 16;        // tier-B nodes per warp item (memoised passes)
 constexpr int TPB = 256;       // threads per block
 constexpr int OBS_EMPTY = -1000;
+constexpr int64_t MEMO_RUN_T = 1024;           // tier-A levels with at most this many threads per vector
+                                               // are walked in runs by one launch
+constexpr int64_t MEMO_INLINE_SCALE_B = 4096;  // tier-B sets up to this size form level scales inline
 constexpr int MEMO_BKEYS = 32;  // per step, the distinct tier-A child supports whose group keys are tabled
 constexpr int MEMO_APLANS = 7;  // log2 of the compress plans per step for scattered tier-A key masks
 constexpr int MEMO_MARGIN = 2;  // early steps: memoise a node when its key space is >= 4x smaller than V 2^j
@@ -755,6 +758,79 @@ struct MemoAGroup {
 // of bits is OR-linear, a child key is ck(key0) | ck(32 r), two per-child constants.
 constexpr int MEMO_QUAD_K = 7;
 
+// One thread's tier-A work at level-local thread index t for vector vec: one slot, or four slots of
+// one node (keys key0 + 32 r) from key width MEMO_QUAD_K.
+template <typename C>
+__device__ __forceinline__ void memoA_slot(const DevAC &ac, const MemoDesc &md, C *VA, const uint32_t *nodes,
+                                           const MemoAGroup *grp, int ng, int64_t u0, int64_t vec, uint32_t t) {
+    int gi = 0;
+    while (gi + 1 < ng && __ldg(&grp[gi + 1].t0) <= t) ++gi;
+    const uint32_t t0 = __ldg(&grp[gi].t0), nb = __ldg(&grp[gi].nb), ug = __ldg(&grp[gi].u0);
+    const int k = (int)__ldg(&grp[gi].k);
+    const uint32_t q = t - t0;
+    const bool quad = k >= MEMO_QUAD_K;
+    const uint32_t rel = quad ? (((q >> 5) << 7) | (q & 31u)) : q;  // first unit within the group
+    const uint32_t nl = rel >> k;
+    const uint32_t key0 = rel & ((1u << k) - 1u);
+    const uint32_t n = nodes[nb + nl];
+    C r[4];
+    const uint8_t o = ac.op[n];
+    if (o <= OP_CONST) {  // leaves have at most one key bit: one slot
+        r[0] = memo_leaf<C>(ac, md, n, vec, key0);
+    } else {
+        const uint32_t e0 = ac.child_off[n], e1 = ac.child_off[n + 1];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            r[i].x = (o == OP_MUL) ? 1 : 0;
+            r[i].y = 0;
+        }
+        const uint32_t full = (1u << k) - 1u;
+        for (uint32_t e = e0; e < e1; ++e) {
+            const uint32_t c = ac.child[e];
+            const uint32_t me = md.emask[e];  // the child's key bits inside this node's key
+            int kc;
+            uint32_t ck0, m;
+            if (me == full) {  // same key space: same key
+                kc = k;
+                ck0 = key0;
+                m = full;
+            } else if (me & 0x80000000u) {
+                const KeyPlan *kp = md.aplan + (me & 0x7fffffffu);
+                kc = (int)__ldg(&kp->k);
+                m = (uint32_t)__ldg(&kp->m);
+                ck0 = plan_key(kp, key0, true);
+            } else {
+                kc = __popc(me);
+                m = me;
+                ck0 = extract_bits(key0, me);
+            }
+            const uint32_t d1 = ((m >> 5) & 1u) ? 1u << __popc(m & 31u) : 0u;  // ck(32)
+            const uint32_t d2 = ((m >> 6) & 1u) ? 1u << __popc(m & 63u) : 0u;  // ck(64)
+            const C *src = VA + md.V * md.offu[c] + (vec << kc);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (i > 0 && !quad) break;
+                const C v = src[ck0 | ((i & 1) ? d1 : 0u) | ((i & 2) ? d2 : 0u)];
+                if (o == OP_MUL) {
+                    C mm;
+                    mm.x = r[i].x * v.x - r[i].y * v.y;
+                    mm.y = r[i].x * v.y + r[i].y * v.x;
+                    r[i] = mm;
+                } else {
+                    r[i].x += v.x;
+                    r[i].y += v.y;
+                }
+            }
+        }
+    }
+    C *dst = VA + md.V * (u0 + ug + ((int64_t)nl << k)) + (vec << k) + key0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (i > 0 && !quad) break;
+        dst[32 * i] = r[i];
+    }
+}
+
 // One level of tier A: a thread per slot, or per four slots of one node, of the level's tier-A
 // blocks (vector, node, key).
 template <typename C>
@@ -773,79 +849,34 @@ __global__ void __launch_bounds__(TPB, sizeof(C) == 8 ? 8 : 1) memoA_level(DevAC
     const uint32_t dq = gridDim.x / nblk, dr = gridDim.x % nblk;
     for (int64_t b = blockIdx.x; b < items; b += gridDim.x) {
         const uint32_t t = rb * TPB + threadIdx.x;
-        if (t < T) {
-            int gi = 0;
-            while (gi + 1 < ng && __ldg(&grp[gi + 1].t0) <= t) ++gi;
-            const uint32_t t0 = __ldg(&grp[gi].t0), nb = __ldg(&grp[gi].nb), ug = __ldg(&grp[gi].u0);
-            const int k = (int)__ldg(&grp[gi].k);
-            const uint32_t q = t - t0;
-            const bool quad = k >= MEMO_QUAD_K;
-            const uint32_t rel = quad ? (((q >> 5) << 7) | (q & 31u)) : q;  // first unit within the group
-            const uint32_t nl = rel >> k;
-            const uint32_t key0 = rel & ((1u << k) - 1u);
-            const uint32_t n = nodes[nb + nl];
-            C r[4];
-            const uint8_t o = ac.op[n];
-            if (o <= OP_CONST) {  // leaves have at most one key bit: one slot
-                r[0] = memo_leaf<C>(ac, md, n, vec, key0);
-            } else {
-                const uint32_t e0 = ac.child_off[n], e1 = ac.child_off[n + 1];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    r[i].x = (o == OP_MUL) ? 1 : 0;
-                    r[i].y = 0;
-                }
-                const uint32_t full = (1u << k) - 1u;
-                for (uint32_t e = e0; e < e1; ++e) {
-                    const uint32_t c = ac.child[e];
-                    const uint32_t me = md.emask[e];  // the child's key bits inside this node's key
-                    int kc;
-                    uint32_t ck0, m;
-                    if (me == full) {  // same key space: same key
-                        kc = k;
-                        ck0 = key0;
-                        m = full;
-                    } else if (me & 0x80000000u) {
-                        const KeyPlan *kp = md.aplan + (me & 0x7fffffffu);
-                        kc = (int)__ldg(&kp->k);
-                        m = (uint32_t)__ldg(&kp->m);
-                        ck0 = plan_key(kp, key0, true);
-                    } else {
-                        kc = __popc(me);
-                        m = me;
-                        ck0 = extract_bits(key0, me);
-                    }
-                    const uint32_t d1 = ((m >> 5) & 1u) ? 1u << __popc(m & 31u) : 0u;  // ck(32)
-                    const uint32_t d2 = ((m >> 6) & 1u) ? 1u << __popc(m & 63u) : 0u;  // ck(64)
-                    const C *src = VA + md.V * md.offu[c] + (vec << kc);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        if (i > 0 && !quad) break;
-                        const C v = src[ck0 | ((i & 1) ? d1 : 0u) | ((i & 2) ? d2 : 0u)];
-                        if (o == OP_MUL) {
-                            C mm;
-                            mm.x = r[i].x * v.x - r[i].y * v.y;
-                            mm.y = r[i].x * v.y + r[i].y * v.x;
-                            r[i] = mm;
-                        } else {
-                            r[i].x += v.x;
-                            r[i].y += v.y;
-                        }
-                    }
-                }
-            }
-            C *dst = VA + md.V * (u0 + ug + ((int64_t)nl << k)) + (vec << k) + key0;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                if (i > 0 && !quad) break;
-                dst[32 * i] = r[i];
-            }
-        }
+        if (t < T) memoA_slot<C>(ac, md, VA, nodes, grp, ng, u0, vec, t);
         rb += dr;
         vec += dq;
         if (rb >= nblk) {
             rb -= nblk;
             ++vec;
+        }
+    }
+}
+
+// A run of consecutive small tier-A levels in one launch: a block per vector walks the levels in
+// order, its threads covering each level's slots, with a block barrier between levels (a slot reads
+// only slots of its own vector on lower levels).
+struct MemoARunLevel {
+    uint32_t i0, g0, ng, T;  // first node and first group (within the step), groups, threads per vector
+    int64_t u0;              // first unit of the level
+};
+template <typename C>
+__global__ void __launch_bounds__(TPB) memoA_run(DevAC ac, const MemoDesc *mdp, const uint32_t *nodes,
+                                                  const MemoAGroup *grp, const MemoARunLevel *lv, int nlv) {
+    const MemoDesc md = *mdp;
+    C *VA = static_cast<C *>(md.VA);
+    for (int64_t vec = blockIdx.x; vec < md.V; vec += gridDim.x) {
+        for (int l = 0; l < nlv; ++l) {
+            const MemoARunLevel L = lv[l];
+            for (uint32_t t = threadIdx.x; t < L.T; t += blockDim.x)
+                memoA_slot<C>(ac, md, VA, nodes + L.i0, grp + L.g0, (int)L.ng, L.u0, vec, t);
+            __syncthreads();
         }
     }
 }
@@ -865,9 +896,28 @@ __global__ void memo_keys(const PassDesc *pd, const MemoDesc *mdp) {
 }
 
 // One level of tier B (FP32): as up_level_f32 over a node list, tier-A children read by key.
-__global__ void __launch_bounds__(TPB, 4) memoB_level_f32(LevelArgs a, const uint2 *bdesc, int64_t count,
+// The level's scale exponent in one column, from its child levels' scales and observed exponents
+// (the rule of level_scale_kernel: child levels with no value in the column are skipped).
+__device__ __forceinline__ int level_scale_col(const DevAC &ac, int L, int64_t pitch, int floor_zero, const int *S,
+                                               const int *obs, int64_t c) {
+    int s = INT_MIN;
+    for (uint32_t k = ac.cl_off[L]; k < ac.cl_off[L + 1]; ++k) {
+        const int Lp = ac.cl[k];
+        const int o = obs[(int64_t)Lp * pitch + c];
+        if (o == OBS_EMPTY) continue;
+        s = max(s, S[(int64_t)Lp * pitch + c] + o);
+    }
+    if (s == INT_MIN) s = 0;
+    if (floor_zero && s < 0) s = 0;
+    return s;
+}
+
+// a.hi bit 0: the level reads unscaled tier-A values (its scale is at least 0); bit 1: this kernel
+// forms the level's scale itself (every item of a column chunk computes and writes the same value;
+// used for small tier-B sets, where a separate scale launch per level costs more than it saves).
+__global__ void __launch_bounds__(TPB, 4) memoB_level_f32(DevAC ac, LevelArgs a, const uint2 *bdesc, int64_t count,
                                                         const PassDesc *pd, const MemoDesc *mdp,
-                                                        float2 *__restrict__ V, const int *__restrict__ S,
+                                                        float2 *__restrict__ V, int *__restrict__ S,
                                                         int *__restrict__ obs) {
     const int64_t ncols = desc_cols(*pd);
     if (ncols <= 0 || count <= 0) return;
@@ -900,7 +950,15 @@ __global__ void __launch_bounds__(TPB, 4) memoB_level_f32(LevelArgs a, const uin
         const bool two = col + 1 < ncols;
         const int64_t g0 = col0 + col;
         const uint32_t vec0 = (uint32_t)vec_of(es, g0), vec1 = (uint32_t)vec_of(es, two ? g0 + 1 : g0);
-        const int2 sL = *reinterpret_cast<const int2 *>(S + (int64_t)a.L * a.pitch + col);
+        int2 sL;
+        if (a.hi & 2u) {
+            sL.x = level_scale_col(ac, a.L, a.pitch, (int)(a.hi & 1u), S, obs, col);
+            sL.y = two ? level_scale_col(ac, a.L, a.pitch, (int)(a.hi & 1u), S, obs, col + 1) : sL.x;
+            S[(int64_t)a.L * a.pitch + col] = sL.x;
+            if (two) S[(int64_t)a.L * a.pitch + col + 1] = sL.y;
+        } else {
+            sL = *reinterpret_cast<const int2 *>(S + (int64_t)a.L * a.pitch + col);
+        }
         int m0 = -127, m1 = -127;
         const int64_t k1 = min(count, ((int64_t)blk_i + 1) * NBB);
         // one child's two column values and scale exponents (tier A: unscaled, exponent 0); the
@@ -1412,12 +1470,24 @@ struct qkc_ac {
     const int32_t *eval_colvec = nullptr;
     uint64_t *d_sigma = nullptr;
     MemoDesc *d_mdesc = nullptr;
-    struct GraphSlot { cudaGraphExec_t exec = nullptr; const void *V = nullptr, *A = nullptr; int64_t pitch = 0; };
+    // a captured launch sequence and the buffers it was captured with: the scratch generation changes
+    // with every reallocation of a buffer a sequence names (values, scales, adjoints, roots), so a
+    // graph is captured again whenever any of them moved, not only the value tile
+    struct GraphSlot {
+        cudaGraphExec_t exec = nullptr;
+        const void *V = nullptr, *A = nullptr;
+        int64_t pitch = 0;
+        uint64_t gen = 0;
+    };
+    uint64_t scratch_gen = 1;
     struct MemoMeta {
         int cap = 0;
         int64_t max_units = 0;
         std::vector<std::vector<int64_t>> a_lvl, u_lvl, b_lvl, g_lvl;  // per step, [D + 1]
         std::vector<std::vector<int64_t>> t_lvl;                        // per step and level: tier-A threads
+        struct AItem { int L; int64_t off; int cnt; };  // one tier-A launch: level L, or a run of cnt levels
+        std::vector<std::vector<AItem>> a_items;        // per step, in level order
+        MemoARunLevel *d_runlv = nullptr;               // the runs' levels, all steps
         std::vector<std::vector<uint8_t>> floor0;               // per step, [D]
         std::vector<int64_t> a_base, b_base, offu_base, g_base;  // per step
         std::vector<double> a_bytes_slot, b_bytes_col;           // per step: algorithmic bytes per slot unit / column
@@ -1488,6 +1558,7 @@ extern "C" qkc_status qkc_ctx_create(int device, qkc_ctx **out) {
 extern "C" void qkc_ctx_destroy(qkc_ctx *ctx) { delete ctx; }
 
 static void free_scratch(qkc_ac *a) {
+    ++a->scratch_gen;
     cudaFree(a->d_pv); a->d_pv = nullptr;
     cudaFree(a->d_V); a->d_V = nullptr;
     cudaFree(a->d_A); a->d_A = nullptr; a->adj_ok = false;
@@ -1529,7 +1600,7 @@ extern "C" void qkc_free_ac(qkc_ac *a) {
     for (auto *m : a->memo) {
         if (!m) continue;
         cudaFree(m->d_a_nodes); cudaFree(m->d_a_grp); cudaFree(m->d_offu);
-        cudaFree(m->d_emask); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
+        cudaFree(m->d_emask); cudaFree(m->d_runlv); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
         for (auto &g : m->gA) if (g.exec) cudaGraphExecDestroy(g.exec);
         for (auto &g : m->gB) if (g.exec) cudaGraphExecDestroy(g.exec);
         delete m;
@@ -1803,6 +1874,7 @@ static qkc_status ensure_tile(qkc_ac *a, int64_t cols, uint32_t rows = 0) {
     if (want <= a->tile && rows <= a->vrows) return QKC_OK;
     QKC_CUDA(cudaDeviceSynchronize());
     a->eval_ok = false;
+    ++a->scratch_gen;
     cudaFree(a->d_V); cudaFree(a->d_A); cudaFree(a->d_S); cudaFree(a->d_obs); cudaFree(a->d_keys);
     a->d_V = a->d_A = nullptr; a->d_S = a->d_obs = nullptr; a->d_keys = nullptr; a->tile = 0; a->adj_ok = false;
     cudaError_t e1 = cudaMalloc(&a->d_V, (size_t)rows * want * a->elem());
@@ -1823,6 +1895,7 @@ static qkc_status ensure_tile(qkc_ac *a, int64_t cols, uint32_t rows = 0) {
 static qkc_status ensure_adj(qkc_ac *a) {
     if (a->adj_ok) return QKC_OK;
     QKC_CUDA(cudaDeviceSynchronize());
+    ++a->scratch_gen;
     cudaFree(a->d_A);
     a->d_A = nullptr;
     cudaError_t e = cudaMalloc(&a->d_A, (size_t)a->N * a->tile * a->elem());
@@ -1837,6 +1910,7 @@ static qkc_status ensure_adj(qkc_ac *a) {
 static qkc_status ensure_roots(qkc_ac *a, int64_t n) {
     if (n <= a->root_cap) return QKC_OK;
     QKC_CUDA(cudaDeviceSynchronize());
+    ++a->scratch_gen;
     cudaFree(a->d_root);
     a->d_root = nullptr;
     a->root_cap = 0;
@@ -1986,7 +2060,7 @@ static int64_t down_sequence_launches(const qkc_ac *a) {
 // Capture (or reuse) the graph of one pass kind; rebuilt when the tile buffers move.
 static qkc_status pass_graph(qkc_ac *a, bool down, cudaGraphExec_t *out) {
     qkc_ac::GraphSlot &g = down ? a->g_down : a->g_up;
-    if (g.exec && g.V == a->d_V && g.A == a->d_A && g.pitch == a->tile) {
+    if (g.exec && g.V == a->d_V && g.A == a->d_A && g.pitch == a->tile && g.gen == a->scratch_gen) {
         *out = g.exec;
         return QKC_OK;
     }
@@ -2016,6 +2090,7 @@ static qkc_status pass_graph(qkc_ac *a, bool down, cudaGraphExec_t *out) {
     g.V = a->d_V;
     g.A = a->d_A;
     g.pitch = a->tile;
+    g.gen = a->scratch_gen;
     *out = g.exec;
     return QKC_OK;
 }
@@ -2323,6 +2398,8 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
     std::vector<int64_t> offu;
     std::vector<MemoAGroup> grp;
     std::vector<KeyPlan> kplan, aplan, bplan;
+    std::vector<MemoARunLevel> runlv;
+    m->a_items.assign(nq, {});
     std::vector<int32_t> plan_of;  // per node: its key plan in this step, -1 if none yet
     std::vector<int64_t> row_of;   // per node: its tier-B row in this step
     std::vector<char> reach;       // per node: reachable from this step's root
@@ -2466,6 +2543,31 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
             m->t_lvl[j][L] = th;
         }
         m->bp_cnt.push_back((int64_t)bplan.size() - m->bp_base[j]);
+        {  // tier-A launches: consecutive small levels form one run (a block per vector walks them)
+            std::vector<uint32_t> pend;
+            auto flush = [&]() {
+                if (pend.size() >= 2) {
+                    m->a_items[j].push_back({-1, (int64_t)runlv.size(), (int)pend.size()});
+                    for (uint32_t L : pend)
+                        runlv.push_back(MemoARunLevel{(uint32_t)m->a_lvl[j][L], (uint32_t)m->g_lvl[j][L],
+                                                      (uint32_t)(m->g_lvl[j][L + 1] - m->g_lvl[j][L]),
+                                                      (uint32_t)m->t_lvl[j][L], m->u_lvl[j][L]});
+                } else if (pend.size() == 1) {
+                    m->a_items[j].push_back({(int)pend[0], 0, 0});
+                }
+                pend.clear();
+            };
+            for (uint32_t L = 0; L < D; ++L) {
+                if (m->a_lvl[j][L + 1] == m->a_lvl[j][L]) continue;
+                if (m->t_lvl[j][L] <= MEMO_RUN_T) {
+                    pend.push_back(L);
+                } else {
+                    flush();
+                    m->a_items[j].push_back({(int)L, 0, 0});
+                }
+            }
+            flush();
+        }
         m->root_row.push_back(row_of[a->roots[j]]);
         m->max_rows = std::max<int64_t>(m->max_rows, (int64_t)bn.size() - m->b_base[j]);
         m->a_bytes_slot.push_back(abytes * (double)a->elem());
@@ -2482,13 +2584,14 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
         (*st = upload(&m->d_a_grp, grp.data(), grp.size(), dummy)) ||
         (*st = upload(&m->d_offu, offu.data(), offu.size(), dummy)) ||
         (*st = upload(&m->d_emask, emask.data(), emask.size(), dummy)) ||
+        (*st = upload(&m->d_runlv, runlv.data(), runlv.size(), dummy)) ||
         (*st = upload(&m->d_bdesc, bdesc.data(), bdesc.size(), dummy)) ||
         (*st = upload(&m->d_brec, brec.data(), brec.size(), dummy)) ||
         (*st = upload(&m->d_kplan, kplan.data(), kplan.size(), dummy)) ||
         (*st = upload(&m->d_aplan, aplan.data(), aplan.size(), dummy)) ||
         (*st = upload(&m->d_bplan, bplan.data(), bplan.size(), dummy))) {
         cudaFree(m->d_a_nodes); cudaFree(m->d_a_grp); cudaFree(m->d_offu);
-        cudaFree(m->d_emask); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
+        cudaFree(m->d_emask); cudaFree(m->d_runlv); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
         delete m;
         return nullptr;
     }
@@ -2502,22 +2605,31 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
 static void launch_memoA_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, cudaStream_t s) {
     const DevAC d = a->dev();
     const unsigned g = (unsigned)(a->ctx->sm_count * 16);
-    for (uint32_t L = 0; L < a->D; ++L) {
-        const int64_t i0 = m->a_lvl[j][L], i1 = m->a_lvl[j][L + 1];
-        if (i1 == i0) continue;
+    const unsigned gr = (unsigned)(a->ctx->sm_count * 4);  // run kernels: a block per vector, grid-stride
+    const uint32_t *nodes_j = m->d_a_nodes + m->a_base[j];
+    const MemoAGroup *grp_j = m->d_a_grp + m->g_base[j];
+    for (const auto &it : m->a_items[j]) {
+        if (it.cnt > 0) {
+            if (a->prec == 32)
+                memoA_run<float2><<<gr, TPB, 0, s>>>(d, a->d_mdesc, nodes_j, grp_j, m->d_runlv + it.off, it.cnt);
+            else
+                memoA_run<double2><<<gr, TPB, 0, s>>>(d, a->d_mdesc, nodes_j, grp_j, m->d_runlv + it.off, it.cnt);
+            continue;
+        }
+        const uint32_t L = (uint32_t)it.L;
+        const int64_t i0 = m->a_lvl[j][L];
         const int64_t u0 = m->u_lvl[j][L];
         const uint32_t T = (uint32_t)m->t_lvl[j][L];
-        const uint32_t *nodes = m->d_a_nodes + m->a_base[j] + i0;
-        const MemoAGroup *gp = m->d_a_grp + m->g_base[j] + m->g_lvl[j][L];
+        const uint32_t *nodes = nodes_j + i0;
+        const MemoAGroup *gp = grp_j + m->g_lvl[j][L];
         const int ng = (int)(m->g_lvl[j][L + 1] - m->g_lvl[j][L]);
         if (a->prec == 32) memoA_level<float2><<<g, TPB, 0, s>>>(d, a->d_mdesc, nodes, gp, ng, u0, T);
         else memoA_level<double2><<<g, TPB, 0, s>>>(d, a->d_mdesc, nodes, gp, ng, u0, T);
     }
 }
 static int64_t memoA_launches(const qkc_ac *a, const qkc_ac::MemoMeta *m, int j) {
-    int64_t n = 0;
-    for (uint32_t L = 0; L < a->D; ++L) n += m->a_lvl[j][L + 1] > m->a_lvl[j][L];
-    return n;
+    (void)a;
+    return (int64_t)m->a_items[j].size();
 }
 static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, cudaStream_t s) {
     const DevAC d = a->dev();
@@ -2531,18 +2643,20 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
         // exponent starts empty and the scale kernel runs for those levels alone
         if (a->prec == 32)
             obs_reset<<<(unsigned)(((int64_t)D * pitch + TPB - 1) / TPB), TPB, 0, s>>>(a->d_obs, (int64_t)D * pitch);
+        const bool inline_scale = m->b_lvl[j][D] <= MEMO_INLINE_SCALE_B;
         for (uint32_t L = 1; L < D; ++L) {
             const int64_t b0 = m->b_lvl[j][L], b1 = m->b_lvl[j][L + 1];
             if (b1 == b0) continue;
-            if (a->prec == 32)
+            if (a->prec == 32 && !inline_scale)
                 level_scale_kernel<<<gs, TPB, 0, s>>>(d, (int)L, pitch, m->floor0[j][L], a->d_S, a->d_obs);
-            LevelArgs la{(uint32_t)b0, 0, (int)L, pitch};  // lo: the level's first tier-B row
+            // lo: the level's first tier-B row; hi: bit 0 reads tier-A values, bit 1 scale formed inline
+            LevelArgs la{(uint32_t)b0, (uint32_t)m->floor0[j][L] | (inline_scale ? 2u : 0u), (int)L, pitch};
             const int64_t cw = a->prec == 32 ? 64 : 32;
             const int64_t items = ((b1 - b0 + NBB - 1) / NBB) * ((pitch + cw - 1) / cw);
             const unsigned g = grid_for(items * 32, TPB, (int64_t)sms * 8);
             const uint2 *bd = m->d_bdesc + m->b_base[j] + b0;
             if (a->prec == 32)
-                memoB_level_f32<<<g, TPB, 0, s>>>(la, bd, b1 - b0, a->d_desc, a->d_mdesc, (float2 *)a->d_V, a->d_S,
+                memoB_level_f32<<<g, TPB, 0, s>>>(d, la, bd, b1 - b0, a->d_desc, a->d_mdesc, (float2 *)a->d_V, a->d_S,
                                                    a->d_obs);
             else
                 memoB_level_f64<<<g, TPB, 0, s>>>(la, bd, b1 - b0, a->d_desc, a->d_mdesc, (double2 *)a->d_V);
@@ -2557,7 +2671,8 @@ static int64_t memoB_launches(const qkc_ac *a, const qkc_ac::MemoMeta *m, int j)
     if (m->b_lvl[j][a->D] > 0) {
         n += a->prec == 32 ? 1 : 0;
         n += m->bp_cnt[j] > 0;
-        for (uint32_t L = 1; L < a->D; ++L) n += (m->b_lvl[j][L + 1] > m->b_lvl[j][L]) * (a->prec == 32 ? 2 : 1);
+        const int per = (a->prec == 32 && m->b_lvl[j][a->D] > MEMO_INLINE_SCALE_B) ? 2 : 1;
+        for (uint32_t L = 1; L < a->D; ++L) n += (m->b_lvl[j][L + 1] > m->b_lvl[j][L]) * per;
     }
     return n;
 }
@@ -2566,7 +2681,8 @@ static qkc_status memo_graph(qkc_ac *a, qkc_ac::MemoMeta *m, int j, bool partB, 
     auto &slot = partB ? m->gB : m->gA;
     if ((int)slot.size() <= j) slot.resize(a->n_qubits);
     auto &g = slot[j];
-    if (g.exec && (!partB || (g.V == a->d_V && g.A == (const void *)a->d_root && g.pitch == a->tile))) {
+    if (g.exec && (!partB || (g.V == a->d_V && g.A == (const void *)a->d_root && g.pitch == a->tile &&
+                              g.gen == a->scratch_gen))) {
         *out = g.exec;
         return QKC_OK;
     }
@@ -2592,6 +2708,7 @@ static qkc_status memo_graph(qkc_ac *a, qkc_ac::MemoMeta *m, int j, bool partB, 
     g.V = a->d_V;
     g.A = a->d_root;
     g.pitch = a->tile;
+    g.gen = a->scratch_gen;
     *out = g.exec;
     return QKC_OK;
 }
