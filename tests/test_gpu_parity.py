@@ -646,3 +646,29 @@ def test_light_cone_step_ac_malformed_bytes(cuda_ctx):
     bad[48:52] = np.array([nq - 1], dtype="<u4").tobytes()  # root count
     with pytest.raises(Exception):
         N().load_ac(cuda_ctx, bytes(bad), precision=64)
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_sampling_after_scratch_reallocations_equals_fresh(cuda_ctx, kind):
+    """One AC sampled again and again while its scratch is reallocated between calls (the memoised
+    key cap, hence the tile rows, follows the shot count; the per-group sampler needs a row per node)
+    gives, call by call, the samples of a fresh AC: captured launch sequences follow the buffers."""
+    c = I.random_circuit(6, 24, seed=905, noise_prob=0.4)
+    b = N().compile(c, kind)
+    V = 3
+    angs = t(I.uniform_angles(V, c.n_angles, seed=41))
+    seeds = t(I.vector_seeds(V, 41).astype(np.int64))
+    ac = N().load_ac(cuda_ctx, b, precision=32)
+    N().set_tile_limit(ac, 256)
+    for mode, S in ((2, 40), (2, 3000), (0, 500), (2, 40), (1, 1500), (0, 40), (2, 3000)):
+        shots = t(np.full(V, S, dtype=np.int32))
+        N().set_sampler(ac, mode)
+        N().set_params(ac, angs)
+        got = N().sample(ac, seeds, shots, S).cpu().numpy()
+        fresh = N().load_ac(cuda_ctx, b, precision=32)
+        N().set_tile_limit(fresh, 256)
+        N().set_sampler(fresh, mode)
+        N().set_params(fresh, angs)
+        ref = N().sample(fresh, seeds, shots, S).cpu().numpy()
+        fresh.close()
+        assert np.array_equal(got, ref), (mode, S)
