@@ -182,7 +182,7 @@ qkc_status qkc_reserve(qkc_ac *ac, int64_t max_vectors, int64_t max_columns);
 
 /*
  * qkc_set_tile_limit -- cap the column tile of this AC (0 = default: values and
- * adjoints each within 25% of the device memory; otherwise >= 64, rounded down
+ * adjoints each within 30% of the device memory; otherwise >= 64, rounded down
  * to a multiple of 64).  Calls with more columns than the tile process them in
  * tiles.  Lets many resident ACs share one device (serving).  Takes effect on
  * the next scratch growth; set it before the first query.

@@ -1862,7 +1862,7 @@ static qkc_status ensure_tile(qkc_ac *a, int64_t cols, uint32_t rows = 0) {
     int64_t want = (cols + 63) / 64 * 64;
     if (want < 64) want = 64;
     const int64_t per_col = (int64_t)rows * (int64_t)a->elem() + 8LL * a->D + 4LL * MEMO_BKEYS;
-    int64_t cap = (int64_t)((double)a->ctx->total_mem * 0.25) / std::max<int64_t>(1, per_col);
+    int64_t cap = (int64_t)((double)a->ctx->total_mem * 0.30) / std::max<int64_t>(1, per_col);
     if (const char *env = std::getenv("QKC_MAX_TILE_COLUMNS")) {  // smaller tiles (tests of the tiled path)
         const long long lim = std::atoll(env);
         if (lim > 0) cap = std::min<int64_t>(cap, lim);
