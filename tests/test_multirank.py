@@ -51,3 +51,17 @@ def test_reference_arm_prints_on_rank_zero_only():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                         "--warmup", "0"], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_all_cores_oracle_baseline_uses_every_core():
+    """The CPU baseline's all-cores leg runs the oracle unchanged in one spawn-started process per host
+    core and returns their joint chain-rule sample rate (here on the 4-qubit ring for half a second)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2103_17226_gb300 import inputs as I, native as N
+    W = bench.make_workload("qaoa32", 100)
+    c = I.workload("qaoa4_ring_p1")
+    W = dict(W, circuit=c, angles=I.uniform_angles(1, c.n_angles, seed=1), seeds=I.vector_seeds(1, 1))
+    rate, cores = bench.oracle_all_cores(W, N.compile(c, N.QKC_AC_DENSITY), seconds=0.5)
+    assert cores == (os.cpu_count() or 1)
+    assert rate > 0
