@@ -181,6 +181,21 @@ def _oracle_sampler(job):
     return n, time.perf_counter() - t0
 
 
+def host_cpu():
+    """The host's CPU as far as the OS tells: architecture and a model string from /proc/cpuinfo."""
+    import platform
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu part", "hardware") and not model:
+                    model = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return f"{platform.machine()} {model}".strip()
+
+
 def oracle_all_cores(W, ac_bytes, seconds=6.0):
     """The oracle as it stands, one process per host core (a spawn-started pool: no process is
     forked from one that holds a CUDA context); aggregate chain-rule samples per second."""
@@ -227,7 +242,7 @@ def oracle_rate(W, ac_bytes, budget_s=12.0, all_cores=True):
                 sample=(f"1 vector: {T} gradient columns ({t_grad:.2f} s on one core, counted / {cores}) + "
                         f"chain-rule samples on {cores} spawned processes ({agg:.1f} samples/s together) on "
                         f"acref.c, FP64; one core alone: {one_core:.2f} samples/s "
-                        f"({t_s * 1e3:.1f} ms per sample)"))
+                        f"({t_s * 1e3:.1f} ms per sample); host CPU: {host_cpu()}"))
 
 
 def run_reference(args):
