@@ -672,3 +672,42 @@ def test_sampling_after_scratch_reallocations_equals_fresh(cuda_ctx, kind):
         ref = N().sample(fresh, seeds, shots, S).cpu().numpy()
         fresh.close()
         assert np.array_equal(got, ref), (mode, S)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_qaoa40_sampling_wide_prefixes(cuda_ctx, prec):
+    """40 qubits: from step 33 on, group prefixes and key plans need 64-bit words (the 32-bit compress
+    covers steps <= 32 only). Memoised and per-group samples agree bit for bit on the density AC, and
+    the first samples of two vectors are the FP64 AC oracle's chain rule (the light-cone step AC runs
+    the same memoised kernels; at 40 qubits its per-step metadata is several GB, so it is left out)."""
+    n = 40
+    c = I.qaoa_maxcut(n, I.random_regular_graph(n, 3, seed=7), 1, None)
+    b = N().compile(c, 1)
+    V, S = 2, 150
+    angs = I.uniform_angles(V, c.n_angles, seed=43)
+    seeds_h = I.vector_seeds(V, 43)
+    seeds = t(seeds_h.astype(np.int64))
+    shots = t(np.full(V, S, dtype=np.int32))
+    outs = {}
+    for key, bb, mode in (("plain", b, 0), ("memo", b, 2)):
+        ac = N().load_ac(cuda_ctx, bb, precision=prec)
+        N().set_sampler(ac, mode)
+        N().set_params(ac, t(angs))
+        outs[key] = N().sample(ac, seeds, shots, S).cpu().numpy()
+        N().check_status(ac)
+        ac.close()
+    assert np.array_equal(outs["plain"], outs["memo"])
+    ref = R.ACRef(b)
+    for v in range(V):
+        k = 2
+        want = ref.sample(angs[v], int(seeds_h[v]), k)
+
+        def pref(prefix, v=v):
+            ev = list(prefix) + [-1] * (n - len(prefix))
+            P = ref.up(angs[v], ev).real
+            ev[len(prefix)] = 0
+            return P, ref.up(angs[v], ev).real
+
+        margins = mismatch_margins(pref, int(seeds_h[v]), outs["memo"][v, :k].astype(np.uint64), want, n)
+        assert all(m <= TIE[prec] for m in margins), margins
+        assert len(margins) <= (0 if prec == 64 else 1)
