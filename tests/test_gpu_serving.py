@@ -10,19 +10,21 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def _acs():
+def _acs(kind=1):
     from paper_2103_17226_gb300 import native as N
     circs = {
         "qaoa6": I.qaoa_maxcut(6, I.random_regular_graph(6, 3, 61), 1, I.NOISE_CFG2, name="qaoa6"),
         "qaoa8": I.qaoa_maxcut(8, I.random_regular_graph(8, 3, 81), 1, I.NOISE_CFG2, name="qaoa8"),
         "hea4": I.hardware_efficient_ansatz(4, 2, I.NOISE_CFG3, name="hea4"),
     }
-    return circs, {k: N.compile(c, N.QKC_AC_DENSITY) for k, c in circs.items()}
+    return circs, {k: N.compile(c, kind) for k, c in circs.items()}
 
 
-def test_alone_equals_mix_and_fp64_matches_oracle(cuda_ctx):
+@pytest.mark.parametrize("kind", [1, 2])
+def test_alone_equals_mix_and_fp64_matches_oracle(cuda_ctx, kind):
+    """kind 1: density ACs; kind 2: light-cone step ACs (what the serving bench keeps resident)."""
     from paper_2103_17226_gb300.serve import Request, Server, poisson_requests
-    circs, acs = _acs()
+    circs, acs = _acs(kind)
     n_angles = {k: c.n_angles for k, c in circs.items()}
     reqs = poisson_requests(list(acs), n_angles, rate_per_s=20000.0, duration_s=0.004, seed=7, shots_lo=50,
                             shots_hi=1500)
