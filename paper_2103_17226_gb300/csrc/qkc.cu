@@ -67,7 +67,7 @@ namespace {
 
 enum : uint8_t { OP_IND = 0, OP_PARAM = 1, OP_CONST = 2, OP_ADD = 3, OP_MUL = 4 };
 constexpr int NB = 8;          // nodes per warp item
-constexpr int NBB = 16;        // tier-B nodes per warp item (memoised passes)
+constexpr int NBB = 32;        // tier-B nodes per warp item (memoised passes)
 constexpr int TPB = 256;       // threads per block
 constexpr int OBS_EMPTY = -1000;
 constexpr int64_t MEMO_RUN_T = 1024;           // tier-A levels with at most this many threads per vector
