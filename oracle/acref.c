@@ -17,8 +17,11 @@
  *                sum over leaves of angle k of adjoint * d leaf / d angle_k.
  *  sampling      the chain rule P(x) = prod_j P(x_j | x_<j), each factor from
  *                two upward passes (evidence x_<j, and x_<j with X_j = 0).
- * Parity unpinned: none (pinned against the density-matrix and brute-force
- * oracles and hand-built ACs in tests/test_oracle_pins.py).
+ * Parity unpinned: none.  The passes and the gradient are pinned against the
+ * density-matrix and brute-force oracles and hand-built ACs
+ * (tests/test_oracle_pins.py, tests/test_acref_and_compiler.py); the sampler is
+ * pinned index for index against the density-matrix chain rule on noisy
+ * circuits of up to 10 qubits (tests/test_oracle_sampler_pins.py).
  */
 #include <complex.h>
 #include <math.h>

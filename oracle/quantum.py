@@ -9,7 +9,8 @@ Every function here is the textbook definition written out with numpy:
   * outcome probabilities are the diagonal of rho, P(x) = <x|rho|x>;
   * qubit 0 is the most significant bit of an outcome index (axis 0 of the
     state tensor).
-Parity unpinned: none -- every function is pinned in tests/test_oracle_pins.py.
+Parity unpinned: none -- every function is pinned in tests/test_oracle_pins.py
+(the chain-rule sampler also by planted mistakes in tests/test_oracle_sampler_pins.py).
 """
 from __future__ import annotations
 
