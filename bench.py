@@ -208,41 +208,92 @@ def oracle_all_cores(W, ac_bytes, seconds=6.0):
     return sum(n for n, _ in res) / max(t for _, t in res), cores
 
 
-def oracle_rate(W, ac_bytes, budget_s=12.0, all_cores=True):
+def oracle_errors(W, ref, value, grad, first_samples, gpu):
+    """The GPU's results for vector 0 against the oracle's (computed in the CPU-baseline leg from
+    the same calls it times): |<H>| and gradient errors, p0/P on random prefixes, and sample indices
+    (a mismatch is tolerated only where |u P - p0| <= 1e-5 P, the FP32 tie margin)."""
+    from oracle import quantum as Q
+    n = W["circuit"].n_qubits
+    a = W["angles"][0]
+    out = {"vs": "FP64 AC oracle (oracle/acref.c) on vector 0 of the workload",
+           "value_abs_err": abs(gpu["value0"] - value), "grad_max_abs_err": float(np.abs(gpu["grad0"] - grad).max()),
+           "value_scale": float(np.abs(W["coef"]).sum())}
+    if gpu.get("prefix_ev") is not None:
+        rel = []
+        for ev, (gP, gp0) in zip(gpu["prefix_ev"], gpu["prefix_vals"]):
+            P = ref.up(a, ev).real
+            ev0 = list(ev)
+            ev0[ev0.index(-1)] = 0
+            p0 = ref.up(a, ev0).real
+            rel.append(abs(gp0 / gP - p0 / P) / (p0 / P))
+        out["p0_over_P_max_rel_err"] = max(rel)
+        out["prefixes_checked"] = len(rel)
+    if first_samples is not None:
+        got = gpu["bits0"][:len(first_samples)].astype(np.uint64)
+        seed = int(W["seeds"][0])
+        mis, beyond = 0, 0
+        for s in np.nonzero(got != first_samples)[0]:
+            mis += 1
+            g, r = int(got[s]), int(first_samples[s])
+            j = next(k for k in range(n) if ((g ^ r) >> (n - 1 - k)) & 1)
+            pre = [(r >> (n - 1 - k)) & 1 for k in range(j)]
+            ev = pre + [-1] * (n - j)
+            P = ref.up(a, ev).real
+            ev[j] = 0
+            p0 = ref.up(a, ev).real
+            beyond += abs(Q.sample_uniform(seed, int(s), j, n) * P - p0) > 1e-5 * P
+        out.update(samples_checked=len(first_samples), sample_mismatches=mis, mismatches_beyond_tie_margin=beyond)
+    return out
+
+
+def oracle_rate(W, ac_bytes, budget_s=12.0, all_cores=True, gpu=None):
     """Time the oracle as it stands (acref.c, FP64, one host core) on a bounded sample of
-    the workload: the per-vector gradient columns, then samples until the budget."""
+    the workload: the per-vector gradient columns, then samples until the budget.  With the
+    GPU's results for vector 0 (`gpu`), the same oracle outputs also give the error report."""
     from oracle import acref as R
     ref = R.ACRef(ac_bytes)
     a = W["angles"][0]
     t0 = time.perf_counter()
+    value, grad = 0.0, np.zeros(W["circuit"].n_angles)
     for t, (s, cf) in enumerate(zip(W["sup"], W["coef"])):
-        ref.gradient(a, [-2 if b else -1 for b in s], cf)
+        v_, g_ = ref.gradient(a, [-2 if b else -1 for b in s], cf)
+        value += v_
+        grad += g_
     t_grad = time.perf_counter() - t0
     T = len(W["coef"])
     if W["shots"] == 0:
-        return dict(value=T / t_grad, unit=W["unit"], cores=1, kind="oracle",
-                    sample=f"1 vector x {T} Z-string columns (up + down pass each) on acref.c, FP64, one core")
-    n_s = 0
+        res = dict(value=T / t_grad, unit=W["unit"], cores=1, kind="oracle",
+                   sample=f"1 vector x {T} Z-string columns (up + down pass each) on acref.c, FP64, one core")
+        if gpu is not None:
+            res["errors"] = oracle_errors(W, ref, value, grad, None, gpu)
+        return res
     t1 = time.perf_counter()
-    while time.perf_counter() - t1 < max(1.0, budget_s - t_grad) or n_s == 0:
+    first = ref.sample(a, int(W["seeds"][0]), 64)  # the GPU's first 64 samples of vector 0
+    n_s = 64
+    while time.perf_counter() - t1 < max(1.0, budget_s - t_grad):
         ref.sample(a, int(W["seeds"][0]) + n_s, 4)
         n_s += 4
     t_s = (time.perf_counter() - t1) / n_s
+    errors = oracle_errors(W, ref, value, grad, first, gpu) if gpu is not None else None
     per_vec = t_grad + W["shots"] * t_s
     one_core = W["shots"] / per_vec
     if not all_cores:
-        return dict(value=one_core, unit=W["unit"], cores=1, kind="oracle",
-                    sample=(f"1 vector: {T} gradient columns ({t_grad:.2f} s) + {n_s} chain-rule samples "
-                            f"({t_s * 1e3:.1f} ms each) on acref.c, FP64, one core; rate = {W['shots']} samples / "
-                            f"(gradient + {W['shots']} x per-sample time)"))
-    agg, cores = oracle_all_cores(W, ac_bytes)
-    # all cores: samples at the aggregate rate, the gradient columns split over the cores
-    per_vec_all = t_grad / cores + W["shots"] / agg
-    return dict(value=W["shots"] / per_vec_all, unit=W["unit"], cores=cores, kind="oracle",
-                sample=(f"1 vector: {T} gradient columns ({t_grad:.2f} s on one core, counted / {cores}) + "
-                        f"chain-rule samples on {cores} spawned processes ({agg:.1f} samples/s together) on "
-                        f"acref.c, FP64; one core alone: {one_core:.2f} samples/s "
-                        f"({t_s * 1e3:.1f} ms per sample); host CPU: {host_cpu()}"))
+        res = dict(value=one_core, unit=W["unit"], cores=1, kind="oracle",
+                   sample=(f"1 vector: {T} gradient columns ({t_grad:.2f} s) + {n_s} chain-rule samples "
+                           f"({t_s * 1e3:.1f} ms each) on acref.c, FP64, one core; rate = {W['shots']} samples / "
+                           f"(gradient + {W['shots']} x per-sample time)"))
+    else:
+        agg, cores = oracle_all_cores(W, ac_bytes)
+        # all cores: samples at the aggregate rate, the gradient columns split over the cores
+        per_vec_all = t_grad / cores + W["shots"] / agg
+        res = dict(value=W["shots"] / per_vec_all, unit=W["unit"], cores=cores, kind="oracle",
+                   sample=(f"1 vector: {T} gradient columns ({t_grad:.2f} s on one core, counted / {cores}) + "
+                           f"chain-rule samples on {cores} spawned processes ({agg:.1f} samples/s together) on "
+                           f"acref.c, FP64; one core alone: {one_core:.2f} samples/s "
+                           f"({t_s * 1e3:.1f} ms per sample); host CPU: {host_cpu()}"))
+    if errors is not None:
+        res["errors"] = errors
+    return res
 
 
 def run_reference(args):
@@ -268,6 +319,30 @@ def run_reference(args):
                              "sample": rates[-1]["sample"]},
             "e2e": {"value": val, "unit": W["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def gpu_results(W, ac, step, dev):
+    """Vector 0's GPU results at the workload's base angles, for the error report: one more step
+    (outside the timed regions), and p0 and P of 16 random prefixes by the FP32 upward pass."""
+    import torch
+    from paper_2103_17226_gb300 import inputs as I, native as N
+    val, grad, bits = step(0)
+    out = {"value0": float(val[0]), "grad0": grad[0].cpu().numpy(),
+           "bits0": bits[0, :64].cpu().numpy() if bits is not None else None}
+    if W["shots"]:
+        n = W["circuit"].n_qubits
+        rng = I.SplitMix(99)
+        evs = []
+        for _ in range(16):
+            L = 1 + rng.randint(n - 1)
+            pre = [rng.randint(2) for _ in range(L)]
+            evs.append(pre + [-1] * (n - L))
+        cols = [e for ev in evs for e in (ev, [x if i != ev.index(-1) else 0 for i, x in enumerate(ev)])]
+        r = N.evaluate(ac, torch.zeros(len(cols), dtype=torch.int32, device=dev),
+                       torch.tensor(np.array(cols, dtype=np.int8), device=dev)).cpu().numpy()
+        out["prefix_ev"] = evs
+        out["prefix_vals"] = [(r[2 * k, 0], r[2 * k + 1, 0]) for k in range(len(evs))]
+    return out
 
 
 # ---------------------------------------------------------------- multi-rank aggregation
@@ -440,8 +515,9 @@ def run_ours(args):
         ach = kinds[dom][0] / (kinds[dom][1] * 1e6) if kinds[dom][1] > 0 else None
         per_launch_bytes = kinds[dom][0] / max(1, kinds[dom][2])
         up_gbs, dn_gbs, memo_gbs = gbs("up"), gbs("down"), gbs("memo")
-        # edge evaluations the per-column method would do for the same queries
-        edge_evals = info["n_edges"] * (stats["up_columns"] + stats["down_columns"] + stats["memo_columns"])
+        # child references the level kernels actually evaluated (tier-A slots, tier-B group columns,
+        # upward and downward passes of the gradient columns)
+        edge_evals = stats["up_edges"] + stats["down_edges"] + stats["memo_edges"]
         line = {
             "metric": W["metric"], "value": value, "unit": W["unit"], "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -472,7 +548,9 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": W["unit"], "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         }
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = oracle_rate(W, ac_bytes)
+            cb = oracle_rate(W, ac_bytes, gpu=gpu_results(W, ac, step, dev))
+            line["errors"] = cb.pop("errors", None)
+            line["cpu_baseline"] = cb
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -370,6 +370,9 @@ typedef struct {
     int64_t memo_passes, memo_columns;  /* memoised sampling passes (qkc_set_sampler mode 1) */
     double memo_ms, memo_bytes;         /* both tiers */
     double memo_a_ms, memo_a_bytes;     /* tier A alone (the per-slot part of memo_ms / memo_bytes) */
+    double up_edges, down_edges, memo_edges;  /* child references actually evaluated (one per child of a
+                                                 computed node per column or slot; downward: one per
+                                                 parent entry visited) */
 } qkc_stats;
 qkc_status qkc_stats_enable(qkc_ac *ac, int32_t enable, int64_t max_records);
 qkc_status qkc_get_stats(qkc_ac *ac, qkc_stats *out);

@@ -114,3 +114,37 @@ class ACRef:
         if st != 0:
             raise MemoryError("oac_sample")
         return bits[:shots]
+
+
+# ---------------------------------------------------------------- many columns on the host cores
+_worker_ac = {}
+
+
+def _worker(job):
+    """One job of a spawned pool: ("sample", angles, seed, shots) or ("up", angles, evidence)."""
+    key, ac_bytes, task = job
+    if key not in _worker_ac:
+        _worker_ac.clear()
+        _worker_ac[key] = ACRef(ac_bytes)
+    ref = _worker_ac[key]
+    if task[0] == "sample":
+        return ref.sample(task[1], task[2], task[3])
+    return ref.up(task[1], task[2])
+
+
+def run_many(ac_bytes: bytes, tasks, processes: int = 0):
+    """Run oracle tasks -- ("sample", angles, seed, shots) or ("up", angles, evidence) -- on one
+    spawn-started process per host core (a process forked from one holding a CUDA context can
+    hang; spawn starts clean ones).  Results in task order.  The evaluator itself is unchanged:
+    each task is one plain call of ACRef.sample or ACRef.up."""
+    import multiprocessing as mp
+    import os
+    from concurrent.futures import ProcessPoolExecutor
+    procs = processes or min(len(tasks), os.cpu_count() or 1)
+    key = hash(ac_bytes)
+    jobs = [(key, ac_bytes, t) for t in tasks]
+    if procs <= 1:
+        return [_worker(j) for j in jobs]
+    # an executor (unlike multiprocessing.Pool) raises when a worker dies instead of waiting forever
+    with ProcessPoolExecutor(procs, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_worker, jobs, chunksize=1))

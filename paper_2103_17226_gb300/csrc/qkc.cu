@@ -1491,6 +1491,7 @@ struct qkc_ac {
         std::vector<std::vector<uint8_t>> floor0;               // per step, [D]
         std::vector<int64_t> a_base, b_base, offu_base, g_base;  // per step
         std::vector<double> a_bytes_slot, b_bytes_col;           // per step: algorithmic bytes per slot unit / column
+        std::vector<double> a_edges_slot, b_edges_col;           // per step: child references per vector / column
         uint32_t *d_a_nodes = nullptr;
         MemoAGroup *d_a_grp = nullptr;  // tier-A key-width groups, per step and level
         int64_t *d_offu = nullptr;
@@ -1520,7 +1521,11 @@ struct qkc_ac {
     // every chain of level kernels with the number of columns it processed
     int64_t launches = 0;
     bool timing = false;
-    struct Rec { cudaEvent_t e0, e1; int kind; double fixed_bytes, col_bytes; };  // 0 up, 1 down, 2/3 memo tier B/A
+    struct Rec {  // kind 0 up, 1 down, 2/3 memo tier B/A
+        cudaEvent_t e0, e1;
+        int kind;
+        double fixed_bytes, col_bytes, fixed_edges, col_edges;
+    };
     std::vector<Rec> recs;
     int64_t *d_statcols = nullptr;
     int64_t statcap = 0;
@@ -1972,6 +1977,8 @@ static qkc_status rec_begin(qkc_ac *a, int kind, const int32_t *n_active, int64_
     r.kind = kind;
     r.fixed_bytes = 0.0;
     r.col_bytes = 0.0;
+    r.fixed_edges = 0.0;
+    r.col_edges = 0.0;
     QKC_CUDA(cudaEventCreate(&r.e0));
     QKC_CUDA(cudaEventCreate(&r.e1));
     stat_record<<<1, 1, 0, s>>>(n_active, col0, ncols, a->d_statcols + a->recs.size());
@@ -2445,7 +2452,7 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
         const size_t ob = offu.size();
         offu.resize(ob + N, -1);
         int64_t units = 0;
-        double abytes = 0.0, bbytes = 0.0;
+        double abytes = 0.0, bbytes = 0.0, aedges = 0.0, bedges = 0.0;
         for (uint32_t L = 0; L < D; ++L) {
             // leaves are always memoised (at most one key bit, V * 2 slots): the memoised pass
             // binds no leaf per group, so every leaf a per-group node reads must be here
@@ -2472,6 +2479,7 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
                 units += 1ll << k;
                 const double deg = (double)(child_off[n + 1] - child_off[n]);
                 abytes += (double)(1ll << k) * (deg + 1.0);
+                aedges += (double)(1ll << k) * deg;
                 const uint64_t rn = a->sigma[n] & jmask;
                 for (uint32_t e = child_off[n]; e < child_off[n + 1]; ++e) {
                     const uint64_t rc = a->sigma[child[e]] & jmask;
@@ -2509,6 +2517,7 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
                 bdesc.push_back(make_uint2((uint32_t)((int64_t)brec.size() - m->br_base[j]),
                                            deg | ((uint32_t)a->h_op[n] << 24)));
                 bbytes += (double)(child_off[n + 1] - child_off[n]) + 1.0;
+                bedges += (double)(child_off[n + 1] - child_off[n]);
                 for (uint32_t e = child_off[n]; e < child_off[n + 1]; ++e) {
                     const uint32_t c = child[e];
                     const int64_t oc = offu[ob + c];
@@ -2572,6 +2581,8 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
         m->max_rows = std::max<int64_t>(m->max_rows, (int64_t)bn.size() - m->b_base[j]);
         m->a_bytes_slot.push_back(abytes * (double)a->elem());
         m->b_bytes_col.push_back(bbytes * (double)a->elem());
+        m->a_edges_slot.push_back(aedges);
+        m->b_edges_col.push_back(bedges);
         m->max_units = std::max(m->max_units, units);
     }
     if (m->max_units >= 0xffffffffll) {  // block offsets are stored in 32 bits per edge
@@ -2728,13 +2739,19 @@ static qkc_status memo_pass(qkc_ac *a, qkc_ac::MemoMeta *m, int j, int clamp, in
     ++a->launches;
     const size_t ra = a->recs.size();
     if ((st = rec_begin(a, 3, nullptr, 0, 0, s))) return st;
-    if (ra < a->recs.size()) a->recs[ra].fixed_bytes = (double)n_vec * m->a_bytes_slot[j];
+    if (ra < a->recs.size()) {
+        a->recs[ra].fixed_bytes = (double)n_vec * m->a_bytes_slot[j];
+        a->recs[ra].fixed_edges = (double)n_vec * m->a_edges_slot[j];
+    }
     QKC_CUDA(cudaGraphLaunch(gA, s));  // tier A: once per step
     a->launches += memoA_launches(a, m, j);
     if ((st = rec_end(a, ra, s))) return st;
     const size_t ri = a->recs.size();
     if ((st = rec_begin(a, 2, n_active, 0, bound, s))) return st;
-    if (ri < a->recs.size()) a->recs[ri].col_bytes = m->b_bytes_col[j];
+    if (ri < a->recs.size()) {
+        a->recs[ri].col_bytes = m->b_bytes_col[j];
+        a->recs[ri].col_edges = m->b_edges_col[j];
+    }
     const int64_t pitch = a->tile;
     for (int64_t c0 = 0; c0 < bound; c0 += pitch) {  // tier B and the roots, per tile of groups
         const int64_t nc = std::min<int64_t>(pitch, bound - c0);
@@ -2992,9 +3009,11 @@ extern "C" qkc_status qkc_get_stats(qkc_ac *a, qkc_stats *o) {
                 o->memo_columns += cols[i];
                 o->memo_ms += ms;
                 o->memo_bytes += a->recs[i].col_bytes * (double)cols[i];
+                o->memo_edges += a->recs[i].col_edges * (double)cols[i];
             } else if (a->recs[i].kind == 3) {  // memoised sampling pass, tier A: per slot
                 o->memo_ms += ms;
                 o->memo_bytes += a->recs[i].fixed_bytes;
+                o->memo_edges += a->recs[i].fixed_edges;
                 o->memo_a_ms += ms;
                 o->memo_a_bytes += a->recs[i].fixed_bytes;
             } else if (a->recs[i].kind == 0) {
@@ -3004,6 +3023,7 @@ extern "C" qkc_status qkc_get_stats(qkc_ac *a, qkc_stats *o) {
                 o->up_launches += (int64_t)(a->D - 1);
                 // child reads + node writes of the internal nodes (the algorithmic bytes of the level kernels)
                 o->up_bytes += elem * ((double)a->E + (double)(a->N - a->n_leaves)) * (double)cols[i];
+                o->up_edges += (double)a->E * (double)cols[i];
             } else {
                 o->down_passes += 1;
                 o->down_columns += cols[i];
@@ -3015,6 +3035,7 @@ extern "C" qkc_status qkc_get_stats(qkc_ac *a, qkc_stats *o) {
                 const double reads = (double)a->down_edges + (double)a->down_sib;
                 const double writes = (double)(a->light_off[a->D] + a->heavy_off[a->D]);
                 o->down_bytes += elem * (reads + writes) * (double)cols[i];
+                o->down_edges += (double)a->down_edges * (double)cols[i];
             }
         }
     }

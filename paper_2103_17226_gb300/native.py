@@ -47,7 +47,8 @@ class Stats(ctypes.Structure):
                 ("down_ms", ctypes.c_double), ("down_bytes", ctypes.c_double),
                 ("memo_passes", ctypes.c_int64), ("memo_columns", ctypes.c_int64),
                 ("memo_ms", ctypes.c_double), ("memo_bytes", ctypes.c_double),
-                ("memo_a_ms", ctypes.c_double), ("memo_a_bytes", ctypes.c_double)]
+                ("memo_a_ms", ctypes.c_double), ("memo_a_bytes", ctypes.c_double),
+                ("up_edges", ctypes.c_double), ("down_edges", ctypes.c_double), ("memo_edges", ctypes.c_double)]
 
 
 def lib():
