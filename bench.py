@@ -21,8 +21,13 @@ angles; value = gradient columns/s.
 depolarising noise after every gate, two layers): 256 vectors x 1000 samples + <H> and
 its gradient per step; value = samples/s.
 
---impl reference times the oracle (plain FP64 C evaluator, one host core) on a
-bounded sample of the same workload.
+--workload qaoa10: the paper's noisy QAOA at 10 qubits, p=2 (random 3-regular graph, 1q depolarising
+0.001, 2q depolarising 0.01): 1024 vectors x 1000 samples per step by trajectory sampling on the
+TRAJECTORY AC (each sample's noise branches drawn from their probabilities, then its outcome by the
+chain rule on |A(x, r)|^2); value = samples/s.
+
+--impl reference times the oracle (plain FP64 C evaluator, or for qaoa10 the state-vector trajectory
+sampler) on the host cores on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -48,7 +53,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["qaoa32", "hea16", "vqe25", "vqe9", "serve", "gibbs_kl"],
+    ap.add_argument("--workload", choices=["qaoa32", "hea16", "vqe25", "vqe9", "qaoa10", "serve", "gibbs_kl"],
                     default="qaoa32")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: Poisson arrivals per second")
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
@@ -97,6 +102,13 @@ def make_workload(name, shots):
                     shots=1000 if shots is None else shots, seeds=I.vector_seeds(V, 7), unit="samples/s",
                     metric=f"samples/s (chain-rule sampling, with <H> + gradient, of a {c.n_qubits}-qubit "
                            f"2D-Ising VQE density AC)")
+    if name == "qaoa10":
+        c = I.workload("qaoa10_3reg_p2")
+        V = 1024
+        return dict(name="qaoa10_3reg_p2", circuit=c, V=V, angles=I.uniform_angles(V, c.n_angles, seed=2),
+                    sup=None, coef=None, shots=1000 if shots is None else shots, seeds=I.vector_seeds(V, 2),
+                    unit="samples/s", metric="samples/s (exact trajectory sampling of a 10-qubit noisy QAOA p=2 "
+                    "on its TRAJECTORY AC)")
     c = I.workload("hea16_l6")
     V = 256
     sup, coef = I.z_string_hamiltonian(16, 16, seed=3)
@@ -343,6 +355,166 @@ def gpu_results(W, ac, step, dev):
         out["prefix_ev"] = evs
         out["prefix_vals"] = [(r[2 * k, 0], r[2 * k + 1, 0]) for k in range(len(evs))]
     return out
+
+
+# ---------------------------------------------------------------- trajectory sampling (qaoa10)
+def _traj_oracle_job(job):
+    circuit, angles, seed, seconds = job
+    from oracle import trajectory as T
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds or n == 0:
+        T.trajectory_samples(circuit, angles, seed + n, 8)
+        n += 8
+    return n, time.perf_counter() - t0
+
+
+def oracle_trajectory_rate(W, seconds=6.0, gpu=None):
+    """The trajectory oracle as it stands (oracle/trajectory.py: a state-vector run per distinct
+    trajectory, chain rule on |A(x, r)|^2), one spawn-started process per host core, vectors of the
+    workload in turn; with the GPU's first samples of vector 0, also the error report."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    from oracle import quantum as Q, trajectory as T
+    cores = os.cpu_count() or 1
+    c = W["circuit"]
+    jobs = [(c, W["angles"][i % W["V"]], int(W["seeds"][i % W["V"]]) + (i << 32), seconds) for i in range(cores)]
+    with ProcessPoolExecutor(cores, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_traj_oracle_job, jobs))
+    rate = sum(n for n, _ in res) / max(t_ for _, t_ in res)
+    out = dict(value=rate, unit=W["unit"], cores=cores, kind="oracle",
+               sample=(f"state-vector trajectory sampler (oracle/trajectory.py, FP64) on {cores} spawned processes, "
+                       f"{seconds:.0f} s each, batches of 8 samples of vectors 0..{cores - 1}; host CPU: {host_cpu()}"))
+    if gpu is not None:
+        n, seed, a = c.n_qubits, int(W["seeds"][0]), W["angles"][0]
+        want = T.trajectory_samples(c, a, seed, len(gpu["bits0"]))
+        got = gpu["bits0"].astype(np.uint64)
+        mis, beyond = 0, 0
+        for s_ in np.nonzero(got != want)[0]:
+            mis += 1
+            r = T.draw_trajectory(c, seed, int(s_))
+            prob = (np.abs(Q.statevector(c, a, r)) ** 2).reshape((2,) * n)
+            g, w = int(got[s_]), int(want[s_])
+            j = next(k for k in range(n) if ((g ^ w) >> (n - 1 - k)) & 1)
+            pre = tuple((w >> (n - 1 - k)) & 1 for k in range(j))
+            P, p0 = float(prob[pre].sum()), float(prob[pre + (0,)].sum())
+            beyond += abs(Q.sample_uniform(seed, int(s_), j, n) * P - p0) > 1e-5 * P
+        out["errors"] = {"vs": "FP64 trajectory oracle (oracle/trajectory.py) on vector 0 of the workload",
+                         "samples_checked": len(want), "sample_mismatches": mis, "mismatches_beyond_tie_margin": beyond}
+    return out
+
+
+def run_trajectory(args):
+    """Config 2: exact batched sampling of the 10-qubit noisy QAOA p=2 through noise trajectories."""
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2103_17226_gb300.build import build_library
+    build_library()
+    from paper_2103_17226_gb300 import native as N
+    W = make_workload("qaoa10", args.shots)
+    V, S = W["V"], W["shots"]
+    ac = N.load_ac(N.Context(local), N.compile(W["circuit"], N.QKC_AC_TRAJECTORY), precision=32)
+    if args.tile:
+        N.set_tile_limit(ac, args.tile)
+    info = ac.info()
+    angle_sets = [W["angles"] + 0.01 * k for k in range(4)]
+    d_angles = [torch.tensor(a, device=dev) for a in angle_sets]
+    d_seeds = torch.tensor(W["seeds"].astype(np.int64), device=dev)
+    d_shots = torch.full((V,), S, dtype=torch.int32, device=dev)
+    d_bits = torch.empty((V, S), dtype=torch.int64, device=dev)
+
+    def step(k, angles=None, seeds=None, shots=None):
+        N.set_params(ac, angles if angles is not None else d_angles[k % 4])
+        return N.sample(ac, seeds if seeds is not None else d_seeds, shots if shots is not None else d_shots, S,
+                        out=d_bits, total_shots=V * S)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for k in range(args.warmup):
+        step(k)
+    barrier()
+    N.stats_enable(ac, True, 1 << 20)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(args.steps):
+        step(k)
+    e1.record()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    stats = N.get_stats(ac)
+    N.stats_enable(ac, False, 0)
+    N.check_status(ac)
+    ms_max = max_over_ranks(ms, world, dev)
+    value = whole_job_rate(V * S, world, args.steps, ms_max / 1e3)
+    h_angles = [torch.tensor(a).pin_memory() for a in angle_sets]
+    h_seeds = torch.tensor(W["seeds"].astype(np.int64)).pin_memory()
+    h_shots = torch.full((V,), S, dtype=torch.int32).pin_memory()
+    h_bits = torch.empty((V, S), dtype=torch.int64).pin_memory()
+
+    def e2e_step(k):
+        bits = step(k, h_angles[k % 4].to(dev, non_blocking=True), h_seeds.to(dev, non_blocking=True),
+                    h_shots.to(dev, non_blocking=True))
+        h_bits.copy_(bits, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    e2e_step(0)
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        e2e_step(k)
+    barrier()
+    e2e_value = whole_job_rate(V * S, world, args.steps, max_over_ranks(time.perf_counter() - t0, world, dev))
+    if rank == 0:
+        peaks = {}
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                peaks = json.load(f)
+        except OSError:
+            pass
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        ach = stats["up_bytes"] / (stats["up_ms"] * 1e6) if stats["up_ms"] > 0 else None
+        line = {
+            "metric": W["metric"], "value": value, "unit": W["unit"], "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": W["name"], "qubits": W["circuit"].n_qubits, "vectors_per_gpu": V, "shots": S,
+                       "ac_kind": "TRAJECTORY", "ac_nodes": info["n_nodes"], "ac_edges": info["n_edges"],
+                       "ac_levels": info["n_levels"], "noise_variables": info["n_vars"] - W["circuit"].n_qubits,
+                       "precision": "complex FP32 nodes, power-of-two scale per (level, column); FP64 decisions",
+                       "l2": "inputs larger than L2: each column tile of the AC's values is tens of GB"},
+            "roofline": {"bound": "hbm", "kernel": "up_level_f32 (upward pass per group column)", "achieved": ach,
+                         "peak": hbm, "unit": "GB/s", "frac": (ach / hbm) if ach else None,
+                         "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                         "bytes_per_launch": stats["up_bytes"] / max(1, stats["up_passes"]),
+                         "launch": "one event-timed upward pass over one column tile", "traffic": None},
+            "gpu_launches": stats["launches"],
+            "edge_evals_per_s": (stats["up_edges"]) * world / (ms_max / 1e3),
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": W["unit"], "h2d_bytes_per_step": h_angles[0].numel() * 8 + V * 12,
+                    "d2h_bytes_per_step": V * S * 8},
+        }
+        if not args.no_cpu_baseline:
+            step(0)
+            torch.cuda.synchronize()
+            cb = oracle_trajectory_rate(W, gpu={"bits0": d_bits[0, :64].cpu().numpy()})
+            line["errors"] = cb.pop("errors", None)
+            line["cpu_baseline"] = cb
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 # ---------------------------------------------------------------- multi-rank aggregation
@@ -812,6 +984,23 @@ def main():
         return
     if args.mode == "reeval":
         run_reeval(args)
+        return
+    if args.workload == "qaoa10":
+        if args.impl == "reference":
+            if int(os.environ.get("RANK", "0")) == 0:
+                W = make_workload("qaoa10", args.shots)
+                rates = [oracle_trajectory_rate(W) for _ in range(args.warmup + args.steps)][args.warmup:]
+                val = statistics.median([r["value"] for r in rates])
+                print(json.dumps({"impl": "reference", "metric": W["metric"], "value": val, "unit": W["unit"],
+                                  "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                                  "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+                                  "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                                  "config": {"workload": W["name"]},
+                                  "cpu_baseline": dict(rates[-1], value=val),
+                                  "e2e": {"value": val, "unit": W["unit"], "h2d_bytes_per_step": 0,
+                                          "d2h_bytes_per_step": 0}}), flush=True)
+        else:
+            run_trajectory(args)
         return
     if args.impl == "reference":
         run_reference(args)

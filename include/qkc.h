@@ -68,7 +68,7 @@ typedef struct {
     double p;
 } qkc_op;
 
-enum { QKC_AC_AMPLITUDE = 0, QKC_AC_DENSITY = 1, QKC_AC_DENSITY_STEPS = 2 };
+enum { QKC_AC_AMPLITUDE = 0, QKC_AC_DENSITY = 1, QKC_AC_DENSITY_STEPS = 2, QKC_AC_TRAJECTORY = 3 };
 enum { QKC_ORDER_AUTO = 0, QKC_ORDER_MINFILL = 1, QKC_ORDER_MINWEIGHT = 2, QKC_ORDER_CREATION = 3 };
 
 /*
@@ -275,6 +275,18 @@ qkc_status qkc_gradient(qkc_ac *ac, const int32_t *col_vec_dev, const int8_t *ev
 qkc_status qkc_sample(qkc_ac *ac, const uint64_t *seeds_dev, const int32_t *shots_dev,
                       int64_t n_vectors, int64_t max_shots, int64_t total_shots, uint64_t *bits_dev,
                       void *stream);
+
+/*
+ * qkc_sample_probs -- qkc_sample, and also probs_dev [n_vectors][max_shots] float64: for every
+ * sample the probability P(x) of its outcome as the sampler carried it through the chain rule,
+ * P(x_<j+1) = P(x_<j, X_j = 0) for a 0 and P(x_<j) - P(x_<j, X_j = 0) for a 1 (the numbers its
+ * decisions compared).  Entries s >= shots[v] are left untouched; -1 marks a sample dropped by an
+ * understated total_shots.  It lets a caller state each sample's probability (for example to
+ * weight or score samples) and check the sampler's arithmetic against an exact P(x).
+ */
+qkc_status qkc_sample_probs(qkc_ac *ac, const uint64_t *seeds_dev, const int32_t *shots_dev,
+                            int64_t n_vectors, int64_t max_shots, int64_t total_shots, uint64_t *bits_dev,
+                            double *probs_dev, void *stream);
 
 /*
  * qkc_gibbs -- the paper's Markov-chain sampler (Sec. 3.3.2) on an AMPLITUDE AC:

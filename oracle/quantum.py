@@ -313,3 +313,22 @@ def chain_rule_samples(probs: np.ndarray, seed: int, shots: int) -> np.ndarray:
             idx = (idx << 1) | b
         out[s] = idx
     return out
+
+
+def _probabilities_job(job):
+    circuit, angles = job
+    return probabilities(circuit, angles)
+
+
+def probabilities_many(circuit, angle_list, processes: int = 0):
+    """probabilities() for several parameter vectors, one spawn-started process per vector (up to
+    the host's cores); an executor raises if a worker dies rather than waiting for it."""
+    import multiprocessing as mp
+    import os
+    from concurrent.futures import ProcessPoolExecutor
+    jobs = [(circuit, np.asarray(a, dtype=float)) for a in angle_list]
+    procs = processes or min(len(jobs), os.cpu_count() or 1)
+    if procs <= 1:
+        return [_probabilities_job(j) for j in jobs]
+    with ProcessPoolExecutor(procs, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_probabilities_job, jobs))

@@ -154,6 +154,11 @@ struct EvSrc {
     const int32_t *col_vec;    // column -> parameter vector (null: identity)
     const int32_t *n_active;   // device count of active columns (null: use host count)
     int64_t n_vec;             // bound vectors; out-of-range map entries are clamped
+    // sampling a TRAJECTORY AC: the noise variables (indicator variables n_qubits ..) are observed at
+    // the trajectory of the sample that owns the column's group (col_traj[col], -1: every branch 0)
+    const int8_t *traj;        // [samples][n_noise]
+    const int32_t *col_traj;
+    int n_noise;
 };
 
 // Everything that changes from one pass to the next lives in device memory, so the
@@ -178,7 +183,11 @@ __device__ __forceinline__ int64_t vec_of(const EvSrc &e, int64_t gc) {
 
 __device__ __forceinline__ int ev_code(const EvSrc &e, const DevAC &ac, int64_t col, int var) {
     if (e.ev) return e.ev[col * ac.n_vars + var];
-    int q = var;  // density AC: indicator variables are the qubits
+    if (var >= ac.n_qubits) {  // a noise variable of a TRAJECTORY AC: the group's branch
+        const int32_t t = e.col_traj ? e.col_traj[col] : -1;
+        return t < 0 ? 0 : (int)e.traj[(int64_t)t * e.n_noise + (var - ac.n_qubits)];
+    }
+    int q = var;  // the output variables are the qubits
     if (q < e.j) return (int)((e.prefix[col] >> (e.j - 1 - q)) & 1ull);
     if (q == e.j && e.clamp) return 0;
     return -1;
@@ -680,8 +689,7 @@ struct MemoDesc {
     const uint64_t *sigma;
     const uint32_t *emask;  // per child edge of a tier-A node: the child's key bits in the parent's key,
                             // or (bit 31 set) the index of a key plan in aplan for a scattered mask
-    const uint2 *brec;      // per child edge of a tier-B node, in node order: (bit 31 + the child's tile
-                            // row, or 1 + its key plan; the child's level)
+    const uint4 *brec;      // per child edge of a tier-B node, in node order (layout: BChild below)
     const KeyPlan *kplan;  // per tier-A child of a tier-B node (this step)
     const KeyPlan *aplan;  // per distinct scattered child-key mask of tier-A parents (this step)
     const KeyPlan *bplan;  // the step's tabled supports (nbm of them) ...
@@ -912,21 +920,78 @@ __device__ __forceinline__ int level_scale_col(const DevAC &ac, int L, int64_t p
     return s;
 }
 
+// One child of a tier-B node: its edge record (uint4) says where its two column values live.
+//   x bit 31 set: a tier-B child, x & 0x7fffffff = its row of the value tile, y = its level;
+//   else a tier-A child: x = 1 + its key plan, y = key width | (1 + group-key table row, 0 if
+//   the support is not tabled) << 8, (z, w) = its tier-A block offset in units (64 bits).
+// A tier-A slot holds an unscaled value: exponent 0.
+struct BChild {
+    float4 v;  // the two columns' values (x, y) and (z, w)
+    int2 s;    // their scale exponents; for a tabled tier-A child, first the two keys
+};
+
+// Issue the loads of one child's two column values (tier B) or keys (tier-A, tabled); an
+// untabled tier-A child's keys are formed here from the group prefixes.
+__device__ __forceinline__ void bchild_issue(const uint4 r, BChild &c, const float4 *V4, const int *S, int64_t hp,
+                                             int64_t pitch, int64_t col, const MemoDesc &md, const EvSrc &es,
+                                             int64_t g0, bool two, bool narrow) {
+    if (r.x & 0x80000000u) {
+        c.v = __ldg(V4 + (int64_t)(r.x & 0x7fffffffu) * hp + (col >> 1));
+        c.s = __ldg(reinterpret_cast<const int2 *>(S + (int64_t)r.y * pitch + col));
+    } else {
+        const int mid = (int)(r.y >> 8) - 1;
+        if (mid >= 0) {  // tabled: this column pair's keys (col is even, the pitch a multiple of 64)
+            const uint2 kk = *reinterpret_cast<const uint2 *>(md.keys + (int64_t)mid * md.kpitch + col);
+            c.s = make_int2((int)kk.x, (int)(two ? kk.y : kk.x));  // no key past the last column
+        } else {  // the group prefixes in qubit order (bit q = x_q), compressed to the child's support
+            const KeyPlan *kp = md.kplan + (r.x - 1u);
+            const uint64_t pre0 = md.j ? __brevll(es.prefix[g0] << (64 - md.j)) : 0ull;
+            const uint64_t pre1 = md.j ? __brevll(es.prefix[two ? g0 + 1 : g0] << (64 - md.j)) : 0ull;
+            c.s = make_int2((int)plan_key(kp, pre0, narrow), (int)plan_key(kp, pre1, narrow));
+        }
+    }
+}
+// Second stage for a tier-A child: its two slots, read by key.
+__device__ __forceinline__ void bchild_slots(const uint4 r, BChild &c, const float2 *VA, int64_t Vn, uint32_t vec0,
+                                             uint32_t vec1) {
+    if (r.x & 0x80000000u) return;
+    const int kc = (int)(r.y & 0xffu);
+    const int64_t base = Vn * (int64_t)(((uint64_t)r.w << 32) | r.z);
+    const float2 a = VA[base + (int64_t)((((uint64_t)vec0) << kc) | (uint32_t)c.s.x)];
+    const float2 b = VA[base + (int64_t)((((uint64_t)vec1) << kc) | (uint32_t)c.s.y)];
+    c.v = make_float4(a.x, a.y, b.x, b.y);
+    c.s = make_int2(0, 0);
+}
+
+// Tier-B nodes of one warp item whose child loads are issued together before any is combined.
+constexpr int MEMO_B_BATCH = 2;
+
+// One level of tier B (FP32): as up_level_f32 over a node list, tier-A children read by key.
+// A warp item is 32 tier-B nodes x 64 columns (float4 per lane = 2 columns).  The item's node
+// descriptors and first two edge records are staged in shared memory by one coalesced load,
+// then its nodes are taken MEMO_B_BATCH at a time: every child load of the batch is issued
+// (tile rows and scale words, or group keys), then the tier-A slots by key, and only then are
+// the nodes combined and stored -- so a warp keeps several loads in flight instead of waiting
+// on one node's descriptor -> record -> value chain at a time.  The arithmetic (and its order)
+// is that of up_level_f32, so values equal the per-group sampler's bit for bit.
 // a.hi bit 0: the level reads unscaled tier-A values (its scale is at least 0); bit 1: this kernel
-// forms the level's scale itself (every item of a column chunk computes and writes the same value;
-// used for small tier-B sets, where a separate scale launch per level costs more than it saves).
-__global__ void __launch_bounds__(TPB, 4) memoB_level_f32(DevAC ac, LevelArgs a, const uint2 *bdesc, int64_t count,
+// forms the level's scale itself (the items of the level's first node block write it).
+__global__ void __launch_bounds__(TPB, 3) memoB_level_f32(DevAC ac, LevelArgs a, const uint2 *bdesc, int64_t count,
                                                         const PassDesc *pd, const MemoDesc *mdp,
                                                         float2 *__restrict__ V, int *__restrict__ S,
                                                         int *__restrict__ obs) {
+    __shared__ uint2 sdesc[TPB / 32][NBB];
+    __shared__ uint4 srec[TPB / 32][NBB][2];
     const int64_t ncols = desc_cols(*pd);
     if (ncols <= 0 || count <= 0) return;
-    const MemoDesc md = *mdp;
+    const MemoDesc &md = *mdp;
     const float2 *VA = static_cast<const float2 *>(md.VA);
+    const int64_t Vn = md.V;
+    const uint4 *brec = md.brec;
     const bool narrow = md.j <= 32;
-    const EvSrc es = pd->es;
+    const EvSrc &es = pd->es;
     const int64_t col0 = pd->col0;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     // work items (node block, column chunk) in 32 bits: blocks < 2^28, chunks < 2^26
     const uint32_t nchunks = (uint32_t)((ncols + 63) >> 6);
     const uint32_t nblk = (uint32_t)((count + NBB - 1) / NBB);
@@ -946,6 +1011,19 @@ __global__ void __launch_bounds__(TPB, 4) memoB_level_f32(DevAC ac, LevelArgs a,
             chunk -= nchunks;
             ++blk;
         }
+        // stage the block's descriptors (first edge record, degree | op << 24) and first two records
+        const int64_t kb = (int64_t)blk_i * NBB;
+        const int nn = (int)min((int64_t)NBB, count - kb);
+        __syncwarp();
+        if (lane < nn) {
+            const uint2 d = __ldg(bdesc + kb + lane);
+            const uint32_t deg = d.y & 0xffffffu;
+            sdesc[w][lane] = d;
+            const uint4 r0 = __ldg(brec + d.x);
+            srec[w][lane][0] = r0;
+            srec[w][lane][1] = deg >= 2u ? __ldg(brec + d.x + 1) : r0;  // a node's own records only
+        }
+        __syncwarp();
         if (col >= ncols) continue;
         const bool two = col + 1 < ncols;
         const int64_t g0 = col0 + col;
@@ -954,82 +1032,66 @@ __global__ void __launch_bounds__(TPB, 4) memoB_level_f32(DevAC ac, LevelArgs a,
         if (a.hi & 2u) {
             sL.x = level_scale_col(ac, a.L, a.pitch, (int)(a.hi & 1u), S, obs, col);
             sL.y = two ? level_scale_col(ac, a.L, a.pitch, (int)(a.hi & 1u), S, obs, col + 1) : sL.x;
-            S[(int64_t)a.L * a.pitch + col] = sL.x;
-            if (two) S[(int64_t)a.L * a.pitch + col + 1] = sL.y;
+            if (blk_i == 0) {
+                S[(int64_t)a.L * a.pitch + col] = sL.x;
+                if (two) S[(int64_t)a.L * a.pitch + col + 1] = sL.y;
+            }
         } else {
             sL = *reinterpret_cast<const int2 *>(S + (int64_t)a.L * a.pitch + col);
         }
         int m0 = -127, m1 = -127;
-        const int64_t k1 = min(count, ((int64_t)blk_i + 1) * NBB);
-        // one child's two column values and scale exponents (tier A: unscaled, exponent 0); the
-        // edge record holds the child's tile row or key plan, and its level
-        auto child_vals = [&](const uint2 rec, float2 &v0, float2 &v1, int &s0, int &s1) {
-            const uint32_t eo = rec.x;
-            if (eo & 0x80000000u) {  // tier B: the child's row of the tile
-                const float4 v = __ldg(V4 + (int64_t)(eo & 0x7fffffffu) * hp + (col >> 1));
-                const int2 sc = __ldg(reinterpret_cast<const int2 *>(S + (int64_t)rec.y * a.pitch + col));
-                v0 = make_float2(v.x, v.y);
-                v1 = make_float2(v.z, v.w);
-                s0 = sc.x;
-                s1 = sc.y;
-            } else {
-                const KeyPlan *kp = md.kplan + (eo - 1u);
-                const int kc = (int)__ldg(&kp->k);
-                const int mid = __ldg(&kp->mid);
-                const int64_t base = md.V * __ldg(&kp->off);
-                uint32_t key0, key1;
-                if (mid >= 0) {  // tabled: this column pair's keys (col is even, the pitch a multiple of 64)
-                    const uint2 kk = *reinterpret_cast<const uint2 *>(md.keys + (int64_t)mid * md.kpitch + col);
-                    key0 = kk.x;
-                    key1 = two ? kk.y : kk.x;  // the table holds no key past the last column
-                } else {  // the group prefixes in qubit order (bit q = x_q), compressed to the child's support
-                    const uint64_t pre0 = md.j ? __brevll(es.prefix[g0] << (64 - md.j)) : 0ull;
-                    const uint64_t pre1 = md.j ? __brevll(es.prefix[two ? g0 + 1 : g0] << (64 - md.j)) : 0ull;
-                    key0 = plan_key(kp, pre0, narrow);
-                    key1 = plan_key(kp, pre1, narrow);
+        for (int i0 = 0; i0 < nn; i0 += MEMO_B_BATCH) {
+            BChild c[MEMO_B_BATCH][2];
+            // 1. tile rows and scale words of tier-B children, group keys of tier-A children
+#pragma unroll
+            for (int b = 0; b < MEMO_B_BATCH; ++b) {
+                if (i0 + b >= nn) break;
+                const uint32_t deg = sdesc[w][i0 + b].y & 0xffffffu;
+                bchild_issue(srec[w][i0 + b][0], c[b][0], V4, S, hp, a.pitch, col, md, es, g0, two, narrow);
+                if (deg >= 2u)
+                    bchild_issue(srec[w][i0 + b][1], c[b][1], V4, S, hp, a.pitch, col, md, es, g0, two, narrow);
+            }
+            // 2. the tier-A children's slots, by key
+#pragma unroll
+            for (int b = 0; b < MEMO_B_BATCH; ++b) {
+                if (i0 + b >= nn) break;
+                const uint32_t deg = sdesc[w][i0 + b].y & 0xffffffu;
+                bchild_slots(srec[w][i0 + b][0], c[b][0], VA, Vn, vec0, vec1);
+                if (deg >= 2u) bchild_slots(srec[w][i0 + b][1], c[b][1], VA, Vn, vec0, vec1);
+            }
+            // 3. combine and store
+#pragma unroll
+            for (int b = 0; b < MEMO_B_BATCH; ++b) {
+                if (i0 + b >= nn) break;
+                const uint2 dsc = sdesc[w][i0 + b];
+                const uint32_t deg = dsc.y & 0xffffffu, o = dsc.y >> 24;
+                float2 q0, q1;
+                if (o == OP_MUL) {
+                    const BChild &x = c[b][0], &y = c[b][1];
+                    q0 = cscale(cmul(make_float2(x.v.x, x.v.y), make_float2(y.v.x, y.v.y)), pow2f(x.s.x + y.s.x - sL.x));
+                    q1 = cscale(cmul(make_float2(x.v.z, x.v.w), make_float2(y.v.z, y.v.w)), pow2f(x.s.y + y.s.y - sL.y));
+                } else {
+                    q0 = make_float2(0.f, 0.f);
+                    q1 = q0;
+                    auto add = [&](const BChild &x) {
+                        const float f0 = pow2f(x.s.x - sL.x), f1 = pow2f(x.s.y - sL.y);
+                        q0.x += x.v.x * f0; q0.y += x.v.y * f0;
+                        q1.x += x.v.z * f1; q1.y += x.v.w * f1;
+                    };
+                    add(c[b][0]);
+                    if (deg >= 2u) add(c[b][1]);
+                    for (uint32_t e = 2; e < deg; ++e) {  // children beyond the second: one at a time
+                        const uint4 r = __ldg(brec + dsc.x + e);
+                        BChild x;
+                        bchild_issue(r, x, V4, S, hp, a.pitch, col, md, es, g0, two, narrow);
+                        bchild_slots(r, x, VA, Vn, vec0, vec1);
+                        add(x);
+                    }
                 }
-                v0 = VA[base + (int64_t)((((uint64_t)vec0) << kc) | key0)];
-                v1 = VA[base + (int64_t)((((uint64_t)vec1) << kc) | key1)];
-                s0 = s1 = 0;
+                V4[(int64_t)(a.lo + kb + i0 + b) * hp + (col >> 1)] = make_float4(q0.x, q0.y, q1.x, q1.y);
+                m0 = max(m0, exp_of(q0));
+                m1 = max(m1, exp_of(q1));
             }
-        };
-        // the next node's descriptor and first two edge records are loaded one node ahead, so the
-        // descriptor -> record -> value chain of one node overlaps the work of the previous one
-        int64_t kk = (int64_t)blk_i * NBB;
-        uint2 dsc = __ldg(bdesc + kk);  // (first edge record, degree | op << 24)
-        uint2 ra = __ldg(md.brec + dsc.x);
-        uint2 rb = (dsc.y & 0xffffffu) >= 2u ? __ldg(md.brec + dsc.x + 1) : ra;  // a node's own records only
-        for (; kk < k1; ++kk) {
-            const uint32_t r0 = dsc.x, deg = dsc.y & 0xffffffu, o = dsc.y >> 24;
-            const uint2 ca = ra, cb = rb;
-            if (kk + 1 < k1) {
-                dsc = __ldg(bdesc + kk + 1);
-                ra = __ldg(md.brec + dsc.x);
-                rb = (dsc.y & 0xffffffu) >= 2u ? __ldg(md.brec + dsc.x + 1) : ra;
-            }
-            float2 q0, q1;
-            if (o == OP_MUL) {
-                float2 a0, a1, b0, b1;
-                int sa0, sa1, sb0, sb1;
-                child_vals(ca, a0, a1, sa0, sa1);
-                child_vals(cb, b0, b1, sb0, sb1);
-                q0 = cscale(cmul(a0, b0), pow2f(sa0 + sb0 - sL.x));
-                q1 = cscale(cmul(a1, b1), pow2f(sa1 + sb1 - sL.y));
-            } else {
-                q0 = make_float2(0.f, 0.f);
-                q1 = q0;
-                for (uint32_t e = 0; e < deg; ++e) {
-                    float2 v0, v1;
-                    int s0, s1;
-                    child_vals(e == 0 ? ca : e == 1 ? cb : __ldg(md.brec + r0 + e), v0, v1, s0, s1);
-                    const float f0 = pow2f(s0 - sL.x), f1 = pow2f(s1 - sL.y);
-                    q0.x += v0.x * f0; q0.y += v0.y * f0;
-                    q1.x += v1.x * f1; q1.y += v1.y * f1;
-                }
-            }
-            V4[(int64_t)(a.lo + kk) * hp + (col >> 1)] = make_float4(q0.x, q0.y, q1.x, q1.y);
-            m0 = max(m0, exp_of(q0));
-            m1 = max(m1, exp_of(q1));
         }
         atomicMax(obs + (int64_t)a.L * a.pitch + col, m0);
         if (two) atomicMax(obs + (int64_t)a.L * a.pitch + col + 1, m1);
@@ -1265,10 +1327,74 @@ __global__ void sample_init(int64_t n_vec, int64_t max_shots, const int32_t *sho
     (void)shots;
 }
 
-__global__ void sample_set_total(const double2 *root, int64_t n_vec, double *g_P) {
+__global__ void sample_set_total(const double2 *root, int64_t n_vec, double *g_P, const int32_t *n_active) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (n_active) n_vec = min(n_vec, (int64_t)*n_active);
     if (t < n_vec) g_P[t] = root[t].x;
 }
+
+// TRAJECTORY ACs (mixed-unitary channels, E_k = sqrt(p_k) U_k): the noise branches of every sample
+// are drawn from their state-independent probabilities, so P(x) = sum_r P(r) P(x | r) is sampled
+// exactly by drawing r first.  Uniform of sample s, noise variable i: (SplitMix64_k(~seed) >> 11)
+// 2^-53, k = s * n_noise + i + 1 (a second stream per vector); the branch is the smallest k with
+// u < cdf_k (the cumulative branch probabilities in value order), else the last.  err[t] marks a
+// sample with some branch other than 0.
+__global__ void traj_draw(int64_t n_vec, int64_t max_shots, const int32_t *shots, const uint64_t *seeds,
+                          int n_noise, const int32_t *noise_off, const double *cdf, int8_t *traj, int32_t *err) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n_vec * max_shots) return;
+    const int64_t v = t / max_shots, s = t % max_shots;
+    if (s >= shots[v]) {
+        err[t] = 0;
+        return;
+    }
+    const uint64_t sd = ~seeds[v];
+    int any = 0;
+    for (int i = 0; i < n_noise; ++i) {
+        uint64_t z = sd + ((uint64_t)s * (uint64_t)n_noise + (uint64_t)i + 1ull) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+        const int o = noise_off[i], card = noise_off[i + 1] - o;
+        int r = card - 1;
+        for (int k = 0; k < card - 1; ++k)
+            if (u < cdf[o + k]) { r = k; break; }
+        traj[t * n_noise + i] = (int8_t)r;
+        any |= r != 0;
+    }
+    err[t] = any;
+}
+
+// The first groups of a trajectory sampling call: group v holds vector v's samples whose trajectory
+// has no error (all share the branches 0), and every sample with an error gets a group of its own
+// (n_vec + its rank among them), carrying its trajectory.
+__global__ void traj_groups(int64_t n_vec, int64_t max_shots, const int32_t *shots, const int32_t *err,
+                            const int32_t *pos, const int32_t *bsum, int32_t *s_group, uint64_t *s_bits,
+                            int32_t *g_vec, uint64_t *g_prefix, int32_t *g_traj, int32_t *g_count) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t n = n_vec * max_shots;
+    if (t < n_vec) {
+        g_vec[t] = (int32_t)t;
+        g_prefix[t] = 0;
+        g_traj[t] = -1;
+    }
+    if (t == n - 1) *g_count = (int32_t)n_vec + pos[t] + bsum[t >> 10] + err[t];
+    if (t >= n) return;
+    const int64_t v = t / max_shots, s = t % max_shots;
+    if (s >= shots[v]) return;
+    s_bits[t] = 0;
+    if (!err[t]) {
+        s_group[t] = (int32_t)v;
+        return;
+    }
+    const int32_t g = (int32_t)n_vec + pos[t] + bsum[t >> 10];
+    s_group[t] = g;
+    g_vec[g] = (int32_t)v;
+    g_prefix[g] = 0;
+    g_traj[g] = (int32_t)t;
+}
+__global__ void set_count(int32_t *dst, int32_t v) { *dst = v; }
 
 // Decide bit j of every live sample; mark the child group (2g + bit).
 __global__ void sample_decide(int64_t n_vec, int64_t max_shots, const int32_t *shots, const uint64_t *seeds, int j,
@@ -1336,7 +1462,8 @@ __global__ void scan_sums(int32_t *bsum, int64_t nb) {
 __global__ void sample_regroup(const int32_t *g_count_old, const int32_t *flag, const int32_t *pos,
                                const int32_t *bsum, const int32_t *g_vec, const uint64_t *g_prefix,
                                const double *g_P, const double2 *p0v, int32_t *g_vec_n, uint64_t *g_prefix_n,
-                               double *g_P_n, int32_t *g_count_new, int64_t nflag) {
+                               double *g_P_n, int32_t *g_count_new, int64_t nflag, const int32_t *g_traj,
+                               int32_t *g_traj_n) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t n = min((int64_t)(2LL * (*g_count_old)), nflag);  // only the scanned child slots
     if (k >= n) return;
@@ -1347,6 +1474,7 @@ __global__ void sample_regroup(const int32_t *g_count_old, const int32_t *flag, 
     int bit = (int)(k & 1);
     g_vec_n[id] = g_vec[g];
     g_prefix_n[id] = (g_prefix[g] << 1) | (uint64_t)bit;
+    if (g_traj) g_traj_n[id] = g_traj[g];
     double p0 = p0v[g].x, P = g_P[g];
     g_P_n[id] = bit ? fmax(P - p0, 0.0) : p0;
 }
@@ -1365,13 +1493,20 @@ __global__ void sample_remap(int64_t n_vec, int64_t max_shots, const int32_t *sh
     }
     s_group[t] = pos[k] + bsum[k >> 10];
 }
+// Outcome index of every sample and, when asked (probs non-null), the probability P(x) its group
+// carried through the chain rule (the product of the conditionals the decisions compared against).
 __global__ void sample_write(int64_t n_vec, int64_t max_shots, const int32_t *shots, const uint64_t *s_bits,
-                             uint64_t *bits) {
+                             uint64_t *bits, const int32_t *s_group, const double *g_P, const int32_t *g_count,
+                             double *probs) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n_vec * max_shots) return;
     int64_t v = t / max_shots, s = t % max_shots;
     if (s >= shots[v]) return;
     bits[t] = s_bits[t];
+    if (probs) {
+        const int g = s_group[t];
+        probs[t] = (g >= 0 && g < *g_count) ? g_P[g] : -1.0;  // -1: a sample dropped by an understated total
+    }
 }
 
 // active column count of one timed pass, for the live roofline (stats mode)
@@ -1395,6 +1530,7 @@ struct qkc_ctx {
     int device;
     int sm_count;
     size_t total_mem;
+    int memoB_blocks_per_sm = 0;  // resident blocks of memoB_level_f32 (occupancy), 0 until queried
 };
 
 template <typename T>
@@ -1440,6 +1576,15 @@ struct qkc_ac {
     std::vector<int> root_lev;             // per step: the root's level
     int root_L = 0;                        // level of the root
     uint32_t *d_keys = nullptr;            // [MEMO_BKEYS][tile]: the memoised sampler's group-key table
+    // TRAJECTORY ACs: noise variables, their cumulative branch probabilities, and the sampler's
+    // per-sample trajectories and per-group trajectory owners
+    int n_noise = 0;
+    double *d_cdf = nullptr;        // per noise value, cumulative within its variable
+    int32_t *d_noise_off = nullptr; // [n_noise + 1] first value of each noise variable in d_cdf
+    int8_t *d_traj = nullptr;       // [samples][n_noise] branch of every noise variable
+    int32_t *d_err = nullptr;       // [samples] the sample's trajectory has a branch other than 0
+    int32_t *d_g_traj[2] = {nullptr, nullptr};       // per group: sample whose trajectory it carries, -1: none
+    int64_t traj_cap = 0;
     double2 *d_root = nullptr;  // [root_cap]
     int64_t root_cap = 0;
     // sampling scratch
@@ -1498,8 +1643,9 @@ struct qkc_ac {
         uint32_t *d_emask = nullptr;    // [step][edge]: a child's key bits inside its tier-A parent's key
         uint2 *d_bdesc = nullptr;       // per step, per tier-B node (tier-B order): (first edge record,
                                         // degree | op << 24)
-        uint2 *d_brec = nullptr;        // per step, per edge of a tier-B node: (bit 31 + a tier-B child's
-                                        // tile row, or 1 + a tier-A child's key plan; the child's level)
+        uint4 *d_brec = nullptr;        // per step, per edge of a tier-B node: where its child's values live
+                                        // (a tier-B child's tile row and level, or a tier-A child's key plan,
+                                        // key width, group-key table row and block offset; see BChild)
         std::vector<int64_t> br_base;   // per step: first edge record
         std::vector<int64_t> root_row;  // per step: the root's tier-B row, -1 when the root is tier A
         int64_t max_rows = 0;           // tier-B nodes of the largest step (rows of the value tile)
@@ -1556,6 +1702,11 @@ extern "C" qkc_status qkc_ctx_create(int device, qkc_ctx **out) {
     c->device = device;
     c->sm_count = prop.multiProcessorCount;
     c->total_mem = prop.totalGlobalMem;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->memoB_blocks_per_sm, memoB_level_f32, TPB, 0) != cudaSuccess ||
+        c->memoB_blocks_per_sm < 1) {
+        cudaGetLastError();
+        c->memoB_blocks_per_sm = 4;
+    }
     *out = c;
     return QKC_OK;
 }
@@ -1576,10 +1727,12 @@ static void free_scratch(qkc_ac *a) {
     a->d_s_group = a->d_flag = a->d_pos = a->d_bsum = a->d_gcount = nullptr;
     a->d_s_bits = nullptr;
     for (int i = 0; i < 2; ++i) {
-        cudaFree(a->d_g_vec[i]); cudaFree(a->d_g_prefix[i]); cudaFree(a->d_g_P[i]);
-        a->d_g_vec[i] = nullptr; a->d_g_prefix[i] = nullptr; a->d_g_P[i] = nullptr;
+        cudaFree(a->d_g_vec[i]); cudaFree(a->d_g_prefix[i]); cudaFree(a->d_g_P[i]); cudaFree(a->d_g_traj[i]);
+        a->d_g_vec[i] = nullptr; a->d_g_prefix[i] = nullptr; a->d_g_P[i] = nullptr; a->d_g_traj[i] = nullptr;
     }
-    a->vec_cap = a->tile = a->root_cap = a->samp_cap = a->grp_cap = 0;
+    cudaFree(a->d_traj); cudaFree(a->d_err);
+    a->d_traj = nullptr; a->d_err = nullptr;
+    a->vec_cap = a->tile = a->root_cap = a->samp_cap = a->grp_cap = a->traj_cap = 0;
 }
 
 static void drop_records(qkc_ac *a) {
@@ -1598,6 +1751,7 @@ extern "C" void qkc_free_ac(qkc_ac *a) {
     cudaFree(a->d_desc);
     cudaFree(a->d_status);
     cudaFree(a->d_sigma);
+    cudaFree(a->d_cdf); cudaFree(a->d_noise_off);
     for (auto *c : a->cones)
         if (c) { cudaFree(c->d_nodes); cudaFree(c->d_leaves); delete c; }
     cudaFree(a->d_mdesc);
@@ -1646,8 +1800,9 @@ extern "C" qkc_status qkc_load_ac(qkc_ctx *ctx, const uint8_t *bytes, uint64_t l
     if (h[0] != 0x43414B51u || h[1] != 1u) return fail(QKC_ERR_FORMAT, "qkc_load_ac: bad magic or version");
     const uint32_t kind = h[2], nq = h[3], na = h[4], nv = h[5], N = h[6], E = h[7], D = h[8], nl = h[9],
                    root = h[10], nind = h[11];
-    if (kind > 2 || nq == 0 || nq > 64 || N == 0 || D == 0 || D > 65535 || nl > N || root >= N || nind > nl ||
-        h[12] != (kind == QKC_AC_DENSITY_STEPS ? nq : 0u))
+    if (kind > 3 || nq == 0 || nq > 64 || N == 0 || D == 0 || D > 65535 || nl > N || root >= N || nind > nl ||
+        h[12] != (kind == QKC_AC_DENSITY_STEPS ? nq : 0u) || (kind != QKC_AC_TRAJECTORY && h[13] != 0u) ||
+        (kind == QKC_AC_TRAJECTORY && nv < nq))
         return fail(QKC_ERR_FORMAT, "qkc_load_ac: inconsistent header");
     uint64_t off = 64, s_card, s_tag, s_lo, s_op, s_coff, s_child, s_la, s_lb, s_lc;
     bool ok = take(off, len, 4ull * nv, s_card) && take(off, len, 4ull * nv, s_tag) &&
@@ -1656,6 +1811,8 @@ extern "C" qkc_status qkc_load_ac(qkc_ctx *ctx, const uint8_t *bytes, uint64_t l
               take(off, len, 4ull * nl, s_la) && take(off, len, 4ull * nl, s_lb) && take(off, len, 16ull * nl, s_lc);
     uint64_t s_roots = 0;
     if (ok && kind == QKC_AC_DENSITY_STEPS) ok = take(off, len, 4ull * nq, s_roots);
+    uint64_t s_prior = 0;
+    if (ok && kind == QKC_AC_TRAJECTORY) ok = take(off, len, 8ull * h[13], s_prior);
     if (!ok) return fail(QKC_ERR_FORMAT, "qkc_load_ac: buffer too short for its arrays");
     auto rd = [&](uint64_t s, size_t i, size_t w) {
         uint64_t v = 0;
@@ -1715,6 +1872,33 @@ extern "C" qkc_status qkc_load_ac(qkc_ctx *ctx, const uint8_t *bytes, uint64_t l
         }
     }
     if (n_ind != nind) return fail(QKC_ERR_FORMAT, "qkc_load_ac: indicator leaves missing");
+    // TRAJECTORY: the branch probabilities of every noise variable (variables nq .. nv-1), checked
+    // to form a distribution, kept as cumulative sums for drawing trajectories
+    std::vector<double> cdf;
+    std::vector<int32_t> noise_off;
+    if (kind == QKC_AC_TRAJECTORY) {
+        for (uint32_t v = 0; v < nq; ++v)
+            if (card[v] != 2) return fail(QKC_ERR_FORMAT, "qkc_load_ac: output variable %u is not binary", v);
+        uint64_t want = 0;
+        for (uint32_t v = nq; v < nv; ++v) want += card[v];
+        if (want != h[13]) return fail(QKC_ERR_FORMAT, "qkc_load_ac: %u branch probabilities for %llu noise values",
+                                       h[13], (unsigned long long)want);
+        std::vector<double> pr(h[13]);
+        if (h[13]) std::memcpy(pr.data(), bytes + s_prior, 8ull * h[13]);
+        uint32_t k = 0;
+        for (uint32_t v = nq; v < nv; ++v) {
+            noise_off.push_back((int32_t)k);
+            double acc = 0.0;
+            for (uint32_t x = 0; x < card[v]; ++x, ++k) {
+                if (!(pr[k] >= 0.0 && pr[k] <= 1.0)) return fail(QKC_ERR_FORMAT, "qkc_load_ac: bad branch probability");
+                acc += pr[k];
+                cdf.push_back(acc);
+            }
+            if (std::fabs(acc - 1.0) > 1e-9)
+                return fail(QKC_ERR_FORMAT, "qkc_load_ac: branch probabilities of noise variable %u sum to %.17g", v, acc);
+        }
+        noise_off.push_back((int32_t)k);
+    }
     std::vector<uint32_t> roots(nq, root);  // the root of every sampling step
     if (kind == QKC_AC_DENSITY_STEPS) {
         std::memcpy(roots.data(), bytes + s_roots, 4ull * nq);
@@ -1783,6 +1967,7 @@ extern "C" qkc_status qkc_load_ac(qkc_ctx *ctx, const uint8_t *bytes, uint64_t l
     a->ctx = ctx; a->prec = precision; a->kind = kind; a->n_qubits = nq; a->n_angles = na; a->n_vars = nv;
     a->N = N; a->E = E; a->D = D; a->n_leaves = nl; a->root = root; a->n_ind = nind; a->n_param = n_param;
     a->roots = roots;
+    a->n_noise = kind == QKC_AC_TRAJECTORY ? (int)(nv - nq) : 0;
     a->root_L = (int)lev[root];
     for (uint32_t j = 0; j < nq; ++j) a->root_lev.push_back((int)lev[roots[j]]);
     a->n_const = nl - nind - n_param; a->level_off = lo;
@@ -1823,6 +2008,12 @@ extern "C" qkc_status qkc_load_ac(qkc_ctx *ctx, const uint8_t *bytes, uint64_t l
             qkc_free_ac(a);
             return st;
         }
+    }
+    if (kind == QKC_AC_TRAJECTORY &&
+        ((st = upload(&a->d_cdf, cdf.data(), cdf.size(), b)) ||
+         (st = upload(&a->d_noise_off, noise_off.data(), noise_off.size(), b)))) {
+        qkc_free_ac(a);
+        return st;
     }
     if (cudaMalloc((void **)&a->d_mdesc, sizeof(MemoDesc)) != cudaSuccess ||
         cudaMalloc((void **)&a->d_desc, sizeof(PassDesc)) != cudaSuccess ||
@@ -2363,6 +2554,19 @@ static qkc_status ensure_sampling(qkc_ac *a, int64_t n_samples, int64_t n_groups
         QKC_CUDA(dalloc(&a->d_g_prefix[i], ng));
         QKC_CUDA(dalloc(&a->d_g_P[i], ng));
     }
+    if (a->kind == QKC_AC_TRAJECTORY) {
+        for (int i = 0; i < 2; ++i) {
+            cudaFree(a->d_g_traj[i]);
+            a->d_g_traj[i] = nullptr;
+            QKC_CUDA(dalloc(&a->d_g_traj[i], ng));
+        }
+        cudaFree(a->d_traj);
+        cudaFree(a->d_err);
+        a->d_traj = nullptr;
+        a->d_err = nullptr;
+        QKC_CUDA(dalloc(&a->d_traj, (size_t)ns * (size_t)std::max(1, a->n_noise)));
+        QKC_CUDA(dalloc(&a->d_err, ns));
+    }
     a->samp_cap = ns;
     a->grp_cap = ng;
     return QKC_OK;
@@ -2398,7 +2602,8 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
     const int nq = (int)a->n_qubits;
     const uint32_t N = a->N, D = a->D;
     std::vector<uint32_t> an, bn, emask;
-    std::vector<uint2> bdesc, brec;
+    std::vector<uint2> bdesc;
+    std::vector<uint4> brec;  // edge records of tier-B nodes (layout: BChild)
     std::vector<uint16_t> lev(N);
     for (uint32_t L = 0; L < D; ++L)
         for (uint32_t n = a->level_off[L]; n < a->level_off[L + 1]; ++n) lev[n] = (uint16_t)L;
@@ -2522,7 +2727,7 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
                     const uint32_t c = child[e];
                     const int64_t oc = offu[ob + c];
                     if (oc < 0) {  // a tier-B child: its row
-                        brec.push_back(make_uint2(0x80000000u | (uint32_t)row_of[c], lev[c]));
+                        brec.push_back(make_uint4(0x80000000u | (uint32_t)row_of[c], lev[c], 0u, 0u));
                     } else {
                         m->floor0[j][L] = 1;
                         if (plan_of[c] < 0) {
@@ -2541,7 +2746,10 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
                             plan_of[c] = (int32_t)((int64_t)kplan.size() - m->kp_base[j]);
                             kplan.push_back(kp);
                         }
-                        brec.push_back(make_uint2((uint32_t)plan_of[c] + 1u, lev[c]));
+                        const KeyPlan &kp = kplan[m->kp_base[j] + plan_of[c]];
+                        brec.push_back(make_uint4((uint32_t)plan_of[c] + 1u, kp.k | ((uint32_t)(kp.mid + 1) << 8),
+                                                  (uint32_t)((uint64_t)kp.off & 0xffffffffu),
+                                                  (uint32_t)((uint64_t)kp.off >> 32)));
                     }
                 }
             }
@@ -2664,7 +2872,8 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
             LevelArgs la{(uint32_t)b0, (uint32_t)m->floor0[j][L] | (inline_scale ? 2u : 0u), (int)L, pitch};
             const int64_t cw = a->prec == 32 ? 64 : 32;
             const int64_t items = ((b1 - b0 + NBB - 1) / NBB) * ((pitch + cw - 1) / cw);
-            const unsigned g = grid_for(items * 32, TPB, (int64_t)sms * 8);
+            // FP32: one wave of resident blocks, grid-striding over the items
+            const unsigned g = grid_for(items * 32, TPB, (int64_t)sms * (a->prec == 32 ? a->ctx->memoB_blocks_per_sm : 8));
             const uint2 *bd = m->d_bdesc + m->b_base[j] + b0;
             if (a->prec == 32)
                 memoB_level_f32<<<g, TPB, 0, s>>>(d, la, bd, b1 - b0, a->d_desc, a->d_mdesc, (float2 *)a->d_V, a->d_S,
@@ -2775,12 +2984,12 @@ extern "C" qkc_status qkc_set_sampler(qkc_ac *a, int32_t mode, int64_t memo_budg
     return QKC_OK;
 }
 
-extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t *shots, int64_t n_vec,
-                                 int64_t max_shots, int64_t total_shots, uint64_t *bits, void *stream) {
+static qkc_status sample_impl(qkc_ac *a, const uint64_t *seeds, const int32_t *shots, int64_t n_vec,
+                              int64_t max_shots, int64_t total_shots, uint64_t *bits, double *probs, void *stream) {
     if (!a || !seeds || !shots || !bits || n_vec <= 0 || max_shots < 0)
         return fail(QKC_ERR_ARG, "qkc_sample: bad argument");
-    if (a->kind != QKC_AC_DENSITY && a->kind != QKC_AC_DENSITY_STEPS)
-        return fail(QKC_ERR_UNSUPPORTED, "qkc_sample: needs a DENSITY or DENSITY_STEPS AC");
+    if (a->kind != QKC_AC_DENSITY && a->kind != QKC_AC_DENSITY_STEPS && a->kind != QKC_AC_TRAJECTORY)
+        return fail(QKC_ERR_UNSUPPORTED, "qkc_sample: needs a DENSITY, DENSITY_STEPS or TRAJECTORY AC");
     if (n_vec > a->n_vec && a->n_param > 0) return fail(QKC_ERR_ARG, "qkc_sample: more vectors than bound");
     a->eval_ok = false;
     if (max_shots == 0) return QKC_OK;
@@ -2791,24 +3000,27 @@ extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t
     // host bound on the live samples, hence on the groups of every step
     const int64_t live = (total_shots > 0 && total_shots < n_samp) ? total_shots : n_samp;
     const int nq = (int)a->n_qubits;
+    // TRAJECTORY AC: a group per vector for the samples without error, one per sample with an error
+    const bool traj = a->kind == QKC_AC_TRAJECTORY;
+    const int64_t max_groups = std::max(n_samp, n_vec) + (traj ? n_vec : 0);
     qkc_status st;
-    if ((st = ensure_sampling(a, n_samp, std::max(n_samp, n_vec)))) return st;
+    if ((st = ensure_sampling(a, n_samp, max_groups))) return st;
     // tile sized for the largest step (bounded by the sample count), roots for every group; a step
     // AC sizes its tile once the memoised passes (whose rows it holds) are chosen
     const bool steps = a->kind == QKC_AC_DENSITY_STEPS;
-    if ((!steps && (st = ensure_tile(a, std::max(n_samp, n_vec)))) ||
-        (st = ensure_roots(a, std::max(n_samp, n_vec))))
-        return st;
+    if ((!steps && (st = ensure_tile(a, max_groups))) || (st = ensure_roots(a, max_groups))) return st;
     // memoised passes: the largest cap (bits per node key) whose tier-A slots fit the budget
     // (the caller's, else 40% of the device memory and 60% of what is free); if the slots
     // cannot be allocated, smaller caps, then the per-group sampler
     qkc_ac::MemoMeta *meta = nullptr;
-    if (a->sampler >= 1 && nq <= 63) {
+    // (memoised passes key a node's value by vector and prefix bits alone: not for trajectories)
+    const bool memo_ok = a->sampler >= 1 && nq <= 63 && !traj;
+    if (memo_ok) {
         // an already built key width whose slots fit the current allocation (no new metadata)
         for (int cap = (int)a->memo.size() - 1; cap >= 1 && !meta; --cap)
             if (a->memo[cap] && n_vec * a->memo[cap]->max_units * (int64_t)a->elem() <= a->va_bytes) meta = a->memo[cap];
     }
-    if (a->sampler >= 1 && nq <= 63 && !meta) {
+    if (memo_ok && !meta) {
         int ks = 0;
         while (ks < 24 && (2ll << ks) <= max_shots) ++ks;  // floor(log2(max_shots))
         size_t fr = 0, tot = 0;
@@ -2853,28 +3065,54 @@ extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t
                                    meta ? (uint32_t)std::max<int64_t>(1, meta->max_rows) : 0u)))
         return st;
     const unsigned gs = (unsigned)((n_samp + TPB - 1) / TPB);
-    sample_init<<<std::max(gs, (unsigned)((n_vec + TPB - 1) / TPB)), TPB, 0, s>>>(
-        n_vec, max_shots, shots, a->d_s_group, a->d_s_bits, a->d_g_vec[0], a->d_g_prefix[0], a->d_gcount);
+    if (traj) {
+        // draw every sample's trajectory, then one group per vector for the error-free samples and
+        // one per sample with an error (rank by an exclusive scan of the error flags)
+        traj_draw<<<gs, TPB, 0, s>>>(n_vec, max_shots, shots, seeds, a->n_noise, a->d_noise_off, a->d_cdf,
+                                     a->d_traj, a->d_err);
+        set_count<<<1, 1, 0, s>>>(a->d_gcount + 1, (int32_t)n_samp);
+        const int64_t nb = (n_samp + 1023) / 1024;
+        scan_block<<<(unsigned)nb, 1024, 0, s>>>(a->d_err, a->d_gcount + 1, 1, a->d_pos, a->d_bsum);
+        scan_sums<<<1, 1024, 0, s>>>(a->d_bsum, nb);
+        traj_groups<<<std::max(gs, (unsigned)((n_vec + TPB - 1) / TPB)), TPB, 0, s>>>(
+            n_vec, max_shots, shots, a->d_err, a->d_pos, a->d_bsum, a->d_s_group, a->d_s_bits, a->d_g_vec[0],
+            a->d_g_prefix[0], a->d_g_traj[0], a->d_gcount);
+        a->launches += 5;
+    } else {
+        sample_init<<<std::max(gs, (unsigned)((n_vec + TPB - 1) / TPB)), TPB, 0, s>>>(
+            n_vec, max_shots, shots, a->d_s_group, a->d_s_bits, a->d_g_vec[0], a->d_g_prefix[0], a->d_gcount);
+    }
     QKC_LAUNCH_CHECK();
     int cur = 0;
+    // evidence of the group columns at step j (prefix bits, trajectory)
+    auto group_ev = [&](int j, int clamp, const int32_t *n_active) {
+        EvSrc es{nullptr, a->d_g_prefix[cur], j, clamp, a->d_g_vec[cur], n_active, std::max<int64_t>(1, a->n_vec)};
+        if (traj) {
+            es.traj = a->d_traj;
+            es.col_traj = a->d_g_traj[cur];
+            es.n_noise = a->n_noise;
+        }
+        return es;
+    };
+    const int64_t bound0 = traj ? n_vec + live : n_vec;  // groups before the first step (host bound)
     // P(empty prefix) for every vector: all indicators free
     if (meta) {
         if ((st = memo_pass(a, meta, 0, 0, n_vec, nullptr, n_vec, cur, s))) return st;
-        sample_set_total<<<(unsigned)((n_vec + TPB - 1) / TPB), TPB, 0, s>>>(a->d_root, n_vec, a->d_g_P[cur]);
+        sample_set_total<<<(unsigned)((n_vec + TPB - 1) / TPB), TPB, 0, s>>>(a->d_root, n_vec, a->d_g_P[cur], nullptr);
         a->launches += 2;
         QKC_LAUNCH_CHECK();
     } else {
-        for (int64_t c0 = 0; c0 < n_vec; c0 += a->tile) {
-            const int64_t nc = std::min<int64_t>(a->tile, n_vec - c0);
-            EvSrc es{nullptr, a->d_g_prefix[cur], 0, 0, a->d_g_vec[cur], nullptr, std::max<int64_t>(1, a->n_vec)};
-            if ((st = run_up(a, es, c0, nc, s))) return st;
-            if ((st = run_roots(a, c0, nc, nullptr, s))) return st;
+        const int32_t *na = traj ? a->d_gcount + cur : nullptr;
+        for (int64_t c0 = 0; c0 < bound0; c0 += a->tile) {
+            const int64_t nc = std::min<int64_t>(a->tile, bound0 - c0);
+            if ((st = run_up(a, group_ev(0, 0, na), c0, nc, s))) return st;
+            if ((st = run_roots(a, c0, nc, na, s))) return st;
         }
-        sample_set_total<<<(unsigned)((n_vec + TPB - 1) / TPB), TPB, 0, s>>>(a->d_root, n_vec, a->d_g_P[cur]);
+        sample_set_total<<<(unsigned)((bound0 + TPB - 1) / TPB), TPB, 0, s>>>(a->d_root, bound0, a->d_g_P[cur], na);
         a->launches += 2;  // init + totals
         QKC_LAUNCH_CHECK();
     }
-    int64_t bound = n_vec;  // host upper bound of the group count
+    int64_t bound = bound0;  // host upper bound of the group count
     for (int j = 0; j < nq; ++j) {
         // p0 = P(prefix, X_j = 0) for every group (count on the device, bound on the host)
         int32_t *gcount = a->d_gcount + cur;
@@ -2883,8 +3121,7 @@ extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t
         } else {
             for (int64_t c0 = 0; c0 < bound; c0 += a->tile) {
                 const int64_t nc = std::min<int64_t>(a->tile, bound - c0);
-                EvSrc es{nullptr, a->d_g_prefix[cur], j, 1, a->d_g_vec[cur], gcount, std::max<int64_t>(1, a->n_vec)};
-                if ((st = run_up(a, es, c0, nc, s))) return st;
+                if ((st = run_up(a, group_ev(j, 1, gcount), c0, nc, s))) return st;
                 if ((st = run_roots(a, c0, nc, gcount, s, j))) return st;
             }
         }
@@ -2898,18 +3135,32 @@ extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t
         const int nxt = cur ^ 1;
         sample_regroup<<<(unsigned)((nflag + TPB - 1) / TPB), TPB, 0, s>>>(
             gcount, a->d_flag, a->d_pos, a->d_bsum, a->d_g_vec[cur], a->d_g_prefix[cur], a->d_g_P[cur], a->d_root,
-            a->d_g_vec[nxt], a->d_g_prefix[nxt], a->d_g_P[nxt], a->d_gcount + nxt, nflag);
+            a->d_g_vec[nxt], a->d_g_prefix[nxt], a->d_g_P[nxt], a->d_gcount + nxt, nflag,
+            traj ? a->d_g_traj[cur] : nullptr, traj ? a->d_g_traj[nxt] : nullptr);
         sample_remap<<<gs, TPB, 0, s>>>(n_vec, max_shots, shots, a->d_pos, a->d_bsum, a->d_s_group, a->d_s_bits,
                                         nflag, a->d_status);
         a->launches += 5;
         QKC_LAUNCH_CHECK();
         cur = nxt;
-        bound = std::min<int64_t>(2 * bound, live);
+        bound = std::min<int64_t>(2 * bound, live + (traj ? n_vec : 0));
     }
-    sample_write<<<gs, TPB, 0, s>>>(n_vec, max_shots, shots, a->d_s_bits, bits);
+    sample_write<<<gs, TPB, 0, s>>>(n_vec, max_shots, shots, a->d_s_bits, bits, a->d_s_group, a->d_g_P[cur],
+                                    a->d_gcount + cur, probs);
     ++a->launches;
     QKC_LAUNCH_CHECK();
     return QKC_OK;
+}
+
+extern "C" qkc_status qkc_sample(qkc_ac *a, const uint64_t *seeds, const int32_t *shots, int64_t n_vec,
+                                 int64_t max_shots, int64_t total_shots, uint64_t *bits, void *stream) {
+    return sample_impl(a, seeds, shots, n_vec, max_shots, total_shots, bits, nullptr, stream);
+}
+
+extern "C" qkc_status qkc_sample_probs(qkc_ac *a, const uint64_t *seeds, const int32_t *shots, int64_t n_vec,
+                                       int64_t max_shots, int64_t total_shots, uint64_t *bits, double *probs,
+                                       void *stream) {
+    if (!probs) return fail(QKC_ERR_ARG, "qkc_sample_probs: probs is null");
+    return sample_impl(a, seeds, shots, n_vec, max_shots, total_shots, bits, probs, stream);
 }
 
 

@@ -21,6 +21,10 @@
 // copy with their complex conjugates, each noise rv shared by both copies and
 // each output variable shared by both copies -- so the polynomial is
 // sum_x prod lambda_x <x|rho|x>.
+// TRAJECTORY kind: the same doubling, but every noise rv has one variable per
+// copy and both are tied to the same indicator leaves, so with the noise
+// variables observed at a trajectory r the polynomial is
+// sum_x prod lambda_x |A(x, r)|^2 (the paper's Table 5 amplitudes, squared).
 #include "../../include/qkc.h"
 
 #include <algorithm>
@@ -366,10 +370,13 @@ struct Builder {
     Builder(NodeStore &n, int nq, int k) : ns(n), net(n), n_qubits(nq), kind(k) {
         for (int q = 0; q < nq; ++q) {
             ket.push_back(net.new_var(1));
-            bra.push_back(kind == QKC_AC_DENSITY ? net.new_var(1) : -1);
+            bra.push_back(kind == QKC_AC_DENSITY || kind == QKC_AC_TRAJECTORY ? net.new_var(1) : -1);
         }
     }
-    bool dbl() const { return kind == QKC_AC_DENSITY; }
+    bool dbl() const { return kind == QKC_AC_DENSITY || kind == QKC_AC_TRAJECTORY; }
+    // TRAJECTORY kind: every noise variable has a ket-copy and a bra-copy variable, both tied to
+    // the same indicator leaves, so observing a trajectory fixes both copies to the same branch
+    bool per_copy_noise() const { return kind == QKC_AC_TRAJECTORY; }
 
     // One-qubit matrix m on copy `cur` (conjugated for the bra copy).
     void apply1(std::vector<int32_t> &cur, int q, const Mat2 &m, bool conj) {
@@ -438,24 +445,36 @@ struct Builder {
             if (dbl()) cz(bra, o.q0, o.q1);
         } else if (k == 17) {
             int32_t r = net.new_var(16);
+            const int32_t rb = per_copy_noise() ? net.new_var(16) : r;
             channel2_dep(ket, o.q0, o.q1, o.p, r, false);
-            if (dbl()) channel2_dep(bra, o.q0, o.q1, o.p, r, true);
-            note_rv(r);
+            if (dbl()) channel2_dep(bra, o.q0, o.q1, o.p, rb, true);
+            const double w1 = o.p / 15.0;
+            std::vector<double> pr(16, w1);
+            pr[0] = 1.0 - o.p;
+            note_rv(r, rb, pr);
         } else {
             auto ks = kraus1(k, o.p);
             int32_t r = net.new_var((int32_t)ks.size());
+            const int32_t rb = per_copy_noise() ? net.new_var((int32_t)ks.size()) : r;
             channel1(ket, o.q0, ks, r, false);
-            if (dbl()) channel1(bra, o.q0, ks, r, true);
-            note_rv(r);
+            if (dbl()) channel1(bra, o.q0, ks, rb, true);
+            // branch probabilities of the mixed-unitary channels (E_k = sqrt(p_k) U_k)
+            std::vector<double> pr;
+            if (k == 16) pr = {1.0 - o.p, o.p / 3.0, o.p / 3.0, o.p / 3.0};
+            else if (k == 20 || k == 21) pr = {1.0 - o.p, o.p};
+            note_rv(r, rb, pr);
         }
     }
-    void note_rv(int32_t r) {
-        if (!dbl()) {  // amplitude AC: noise variables carry indicators (Table 5)
+    void note_rv(int32_t r, int32_t rb, const std::vector<double> &pr) {
+        if (!dbl() || per_copy_noise()) {  // noise variables carry indicators (Table 5)
             rv_vars.push_back(r);
+            rv_bra.push_back(rb);
+            for (double x : pr) prior.push_back(x);
         }
         ++n_channels;
     }
-    std::vector<int32_t> rv_vars;
+    std::vector<int32_t> rv_vars, rv_bra;
+    std::vector<double> prior;  // TRAJECTORY: branch probability of every noise indicator value
 
     // Close the network: unify bra outputs with ket outputs, add indicator factors.
     void finish() {
@@ -493,6 +512,13 @@ struct Builder {
                 f.tab.push_back(ns.ind((int32_t)i, 0));
             }
             net.factors.push_back(std::move(f));
+            if (per_copy_noise() && ind_tag[i] < 0) {  // the bra copy's variable: the same leaves
+                const int32_t vb = rv_bra[(size_t)(-1 - ind_tag[i])];
+                Factor fb;
+                fb.vars.push_back(vb);
+                for (int32_t v = 0; v < net.vars[vb].card; ++v) fb.tab.push_back(ns.ind((int32_t)i, v));
+                net.factors.push_back(std::move(fb));
+            }
         }
     }
     std::vector<int32_t> ind_card;
@@ -708,8 +734,7 @@ extern "C" qkc_status qkc_compile(const qkc_op *ops, int32_t n_ops, int32_t n_qu
                                   int32_t kind, int32_t order, int64_t max_nodes, uint8_t **out_bytes,
                                   uint64_t *out_len) {
     if (!out_bytes || !out_len || n_qubits <= 0 || n_qubits > 64 || n_ops < 0 || (n_ops > 0 && !ops) ||
-        n_angles < 0 || (kind != QKC_AC_AMPLITUDE && kind != QKC_AC_DENSITY && kind != QKC_AC_DENSITY_STEPS) ||
-        order < 0 || order > 3) {
+        n_angles < 0 || kind < QKC_AC_AMPLITUDE || kind > QKC_AC_TRAJECTORY || order < 0 || order > 3) {
         qkc_set_error_("qkc_compile: invalid argument");
         return QKC_ERR_ARG;
     }
@@ -724,6 +749,13 @@ extern "C" qkc_status qkc_compile(const qkc_op *ops, int32_t n_ops, int32_t n_qu
             char msg[160];
             std::snprintf(msg, sizeof msg, "qkc_compile: operation %d is invalid (kind %d, qubits %d,%d, angle %d)",
                           i, o.kind, o.q0, o.q1, o.angle);
+            qkc_set_error_(msg);
+            return QKC_ERR_ARG;
+        }
+        if (kind == QKC_AC_TRAJECTORY && (o.kind == 18 || o.kind == 19)) {
+            char msg[200];
+            std::snprintf(msg, sizeof msg, "qkc_compile: operation %d: a TRAJECTORY AC needs mixed-unitary channels "
+                                           "(DEP1, DEP2, PF, BF), not amplitude or phase damping", i);
             qkc_set_error_(msg);
             return QKC_ERR_ARG;
         }
@@ -762,6 +794,7 @@ extern "C" qkc_status qkc_compile(const qkc_op *ops, int32_t n_ops, int32_t n_qu
         std::vector<int32_t> roots;
         std::vector<int32_t> ind_vars_tag;
         std::vector<uint32_t> ind_card_out;
+        std::vector<double> prior;  // TRAJECTORY: branch probabilities of the noise indicator values
         for (const auto &circ : circuits) {
             Builder bld(ns, n_qubits, bkind);
             for (const qkc_op &o : circ) bld.op(o);
@@ -794,6 +827,7 @@ extern "C" qkc_status qkc_compile(const qkc_op *ops, int32_t n_ops, int32_t n_qu
             // noise variables of the amplitude kind)
             ind_vars_tag = bld.ind_tag;
             ind_card_out.assign(bld.ind_card.begin(), bld.ind_card.end());
+            prior = bld.prior;
         }
         const int32_t root = roots.back();
 
@@ -881,10 +915,11 @@ extern "C" qkc_status qkc_compile(const qkc_op *ops, int32_t n_ops, int32_t n_qu
         std::vector<uint32_t> var_card(ind_card_out);
         std::vector<int32_t> var_tag(ind_vars_tag);
         const uint32_t n_roots = kind == QKC_AC_DENSITY_STEPS ? (uint32_t)roots.size() : 0u;
+        const uint32_t n_prior = kind == QKC_AC_TRAJECTORY ? (uint32_t)prior.size() : 0u;
         std::vector<uint8_t> out;
         const uint32_t hdr[16] = {0x43414B51u, 1u, (uint32_t)kind, (uint32_t)n_qubits, (uint32_t)n_angles,
                                   (uint32_t)var_card.size(), N, (uint32_t)kids.size(), D, n_leaves,
-                                  (uint32_t)newid[root], n_ind, n_roots, 0, 0, 0};
+                                  (uint32_t)newid[root], n_ind, n_roots, n_prior, 0, 0};
         for (uint32_t h : hdr) put_u32(out, h);
         put_arr(out, var_card);
         put_arr(out, var_tag);
@@ -900,6 +935,7 @@ extern "C" qkc_status qkc_compile(const qkc_op *ops, int32_t n_ops, int32_t n_qu
             for (int32_t r : roots) rr.push_back((uint32_t)newid[r]);
             put_arr(out, rr);
         }
+        if (n_prior) put_arr(out, prior);
         pad8(out);
         uint8_t *buf = (uint8_t *)std::malloc(out.size());
         if (!buf) {
@@ -924,8 +960,7 @@ extern "C" void qkc_free_bytes(uint8_t *bytes) { std::free(bytes); }
 extern "C" qkc_status qkc_plan(const qkc_op *ops, int32_t n_ops, int32_t n_qubits, int32_t n_angles,
                                int32_t kind, int32_t order, double *table_entries, double *max_log2_table) {
     if (!table_entries || !max_log2_table || n_qubits <= 0 || n_qubits > 64 || n_ops < 0 ||
-        (n_ops > 0 && !ops) || (kind != QKC_AC_AMPLITUDE && kind != QKC_AC_DENSITY && kind != QKC_AC_DENSITY_STEPS) ||
-        order < 0 || order > 3) {
+        (n_ops > 0 && !ops) || kind < QKC_AC_AMPLITUDE || kind > QKC_AC_TRAJECTORY || order < 0 || order > 3) {
         qkc_set_error_("qkc_plan: invalid argument");
         return QKC_ERR_ARG;
     }

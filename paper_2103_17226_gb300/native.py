@@ -21,6 +21,7 @@ _lib = None
 QKC_AC_AMPLITUDE = 0
 QKC_AC_DENSITY = 1
 QKC_AC_DENSITY_STEPS = 2  # one density AC per sampling step (backward light cones), qkc_sample and qkc_evaluate only
+QKC_AC_TRAJECTORY = 3  # doubled network with per-copy noise variables: |A(x, r)|^2 for an observed trajectory r
 STATUS = {0: "QKC_OK", 1: "QKC_ERR_ARG", 2: "QKC_ERR_FORMAT", 3: "QKC_ERR_NOMEM", 4: "QKC_ERR_CUDA",
           5: "QKC_ERR_TIMEOUT", 6: "QKC_ERR_UNSUPPORTED", 7: "QKC_ERR_TOO_LARGE"}
 
@@ -75,6 +76,7 @@ def lib():
         "qkc_marginals": [P, P, P, I64, P, P, P],
         "qkc_gradient": [P, P, P, P, I64, I64, P, P, P],
         "qkc_sample": [P, P, P, I64, I64, I64, P, P],
+        "qkc_sample_probs": [P, P, P, I64, I64, I64, P, P, P],
         "qkc_check_status": [P],
         "qkc_gibbs": [P, P, P, I64, P, I64, I64, P, P],
         "qkc_set_sampler": [P, I32, I64],
@@ -309,6 +311,18 @@ def sample(ac: AC, seeds, shots, max_shots: int, out=None, stream=None, total_sh
     _check(lib().qkc_sample(ac._h, _ptr(seeds), _ptr(shots), n_vec, max_shots, int(total_shots), _ptr(out),
                             _stream(stream)))
     return out
+
+
+def sample_probs(ac: AC, seeds, shots, max_shots: int, stream=None, total_shots: int = 0):
+    """qkc_sample_probs: (outcome indices [n_vectors][max_shots] int64, each sample's carried
+    probability P(x) [n_vectors][max_shots] float64)."""
+    import torch
+    n_vec = seeds.shape[0]
+    out = torch.zeros((n_vec, max_shots), dtype=torch.int64, device=seeds.device)
+    probs = torch.zeros((n_vec, max_shots), dtype=torch.float64, device=seeds.device)
+    _check(lib().qkc_sample_probs(ac._h, _ptr(seeds), _ptr(shots), n_vec, max_shots, int(total_shots), _ptr(out),
+                                  _ptr(probs), _stream(stream)))
+    return out, probs
 
 
 def set_sampler(ac: AC, mode: int, memo_budget_bytes: int = 0):

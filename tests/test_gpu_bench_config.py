@@ -7,9 +7,9 @@ estimated cheaper), the default column tile, 64 parameter vectors x 10000 sample
     difference must be a decision within the FP32 tie margin, judged by the FP64 AC oracle;
   * 2000 indices (8 vectors x 250) against the FP64 AC oracle's chain rule (acref);
   * p0 / P = P(x_j = 0 | x_<j) on 64 random prefixes against the oracle, relative 1e-5;
-  * chi-square of all 496 two-qubit and 100 random three-qubit marginal histograms of one
-    vector against the oracle's marginals, with a Kolmogorov-Smirnov check that the 596
-    p-values look uniform (each single test fails 1% of the time by construction).
+  * chi-square of all 496 two-qubit and 100 random three-qubit marginal histograms (each on
+    its own 1000 samples) against the oracle's marginals, with a Kolmogorov-Smirnov check that
+    the 596 independent p-values look uniform (each single test fails 1% of the time).
 The skewed case (angles within a few 1e-3 of 0 on half the qubits: conditionals of 1e-4 to
 1e-6) runs the memoised FP32 sampler against the FP64 per-group sampler, whose decisions are
 the oracle's: every difference must sit within the tie margin.  It exercises the carried
@@ -158,14 +158,15 @@ def _chi2_p(counts, exp, S):
 
 
 def test_bench_call_marginal_histograms(qaoa32, bench_samples):
-    """All 496 two-qubit and 100 random three-qubit marginal histograms of vector 3's 10000
-    samples against the oracle's marginals: chi-square p-values, and a KS test of their
-    uniformity (a 1% false-failure rate of each single test is expected, not a bug)."""
+    """All 496 two-qubit and 100 random three-qubit marginal histograms against the oracle's
+    marginals.  Each test gets its own 1000 samples -- test k uses vector k % 64, samples
+    1000 (k // 64) .. 1000 (k // 64) + 999 -- so the 596 chi-square p-values are independent
+    (the same samples shared by all pairs of a qubit would correlate them) and a
+    Kolmogorov-Smirnov test of their uniformity is valid.  A single test fails 1% of the time
+    by construction; the count below 0.01 and the KS statistic are what is checked."""
     from scipy.stats import kstest
     W = qaoa32
-    n, v, S = 32, 3, W["S"]
-    bits = bench_samples["bench"][v].astype(np.int64)
-    xs = [(bits >> (n - 1 - q)) & 1 for q in range(n)]
+    n, m_per = 32, 1000
     pairs = [(a, b) for a in range(n) for b in range(a + 1, n)]
     rng = I.SplitMix(57)
     triples = set()
@@ -173,27 +174,30 @@ def test_bench_call_marginal_histograms(qaoa32, bench_samples):
         tr = tuple(sorted({rng.randint(n) for _ in range(3)}))
         if len(tr) == 3:
             triples.add(tr)
-    triples = sorted(triples)
+    subs = pairs + sorted(triples)
+    assert len(subs) == 596 and len(subs) <= W["V"] * (W["S"] // m_per)
     tasks = []
-    for sub in pairs + triples:
+    for k, sub in enumerate(subs):
+        v = k % W["V"]
         for x in range(2 ** len(sub)):
             ev = [-1] * n
             for i, q in enumerate(sub):
                 ev[q] = (x >> (len(sub) - 1 - i)) & 1
             tasks.append(("up", W["angs"][v], ev))
     vals = R.run_many(W["dens"], tasks)
-    pv, k = [], 0
-    for sub in pairs + triples:
+    pv, i = [], 0
+    for k, sub in enumerate(subs):
+        v, sl = k % W["V"], k // W["V"]
+        bits = bench_samples["bench"][v, sl * m_per:(sl + 1) * m_per].astype(np.int64)
         m = 2 ** len(sub)
-        exp = np.array([vals[k + x].real for x in range(m)])
-        k += m
+        exp = np.array([vals[i + x].real for x in range(m)])
+        i += m
         assert abs(exp.sum() - 1.0) < 1e-12
-        idx = np.zeros(S, dtype=np.int64)
+        idx = np.zeros(m_per, dtype=np.int64)
         for q in sub:
-            idx = idx * 2 + xs[q]
-        pv.append(_chi2_p(np.bincount(idx, minlength=m).astype(float), exp, S))
+            idx = idx * 2 + ((bits >> (n - 1 - q)) & 1)
+        pv.append(_chi2_p(np.bincount(idx, minlength=m).astype(float), exp, m_per))
     pv = np.array(pv)
-    assert len(pv) == 596
     assert (pv < 0.01).sum() <= 16, np.sort(pv)[:20]  # binomial(596, 0.01) tail beyond 16: < 1e-4
     assert kstest(pv, "uniform").pvalue > 0.01
 
