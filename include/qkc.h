@@ -125,7 +125,8 @@ qkc_status qkc_plan(const qkc_op *ops, int32_t n_ops, int32_t n_qubits, int32_t 
  *   [0] magic 0x43414B51 ("QKAC")  [1] version = 1  [2] kind  [3] n_qubits
  *   [4] n_angles  [5] n_vars  [6] n_nodes  [7] n_edges  [8] n_levels
  *   [9] n_leaves  [10] root  [11] n_ind  [12] n_roots (kind
- *   QKC_AC_DENSITY_STEPS: n_qubits, else 0)  [13..15] 0
+ *   QKC_AC_DENSITY_STEPS: n_qubits, else 0)  [13] branch probabilities
+ *   (kind QKC_AC_TRAJECTORY: the noise indicator count, else 0)  [14..15] 0
  * then these arrays, each starting on an 8-byte boundary:
  *   var_card[n_vars] u32      cardinality of each indicator variable
  *   var_tag[n_vars]  i32      qubit index of an output variable, or -1-k for
@@ -141,6 +142,8 @@ qkc_status qkc_plan(const qkc_op *ops, int32_t n_ops, int32_t n_qubits, int32_t 
  *                             CONST: the value; IND: (1, 0)
  *   roots[n_roots] u32        (light-cone steps only) root of step j; the
  *                             last is the header's root
+ *   prior[header[13]] f64     (TRAJECTORY only) branch probability of every
+ *                             noise indicator value, in (variable, value) order
  * Level 0 holds exactly the leaves.  Nodes 0 .. n_ind-1 are the indicator
  * leaves lambda_{v=k} in (variable, value) order, one per value of every
  * variable.  MUL nodes have exactly two children; ADD nodes two or more.
@@ -264,7 +267,19 @@ qkc_status qkc_gradient(qkc_ac *ac, const int32_t *col_vec_dev, const int8_t *ev
  * For vector v, sample s, qubit j: u = (SplitMix64_k(seeds[v]) >> 11) 2^-53
  * with k = s*n_qubits + j + 1 (the k-th output of a SplitMix64 stream);
  * p0 = P(x_<j, X_j = 0), P = P(x_<j); x_j = 1 iff u * P >= p0, in float64.
- * Samples of one vector that share a prefix share one evaluation.
+ * Samples of one vector that share a prefix share one evaluation, and that one
+ * upward pass gives both branch probabilities of the step: the indicator of
+ * X_j = 1 is set to the imaginary unit, so the density polynomial (real and
+ * linear in qubit j's indicators) returns P(x_<j, X_j = 0) + i P(x_<j, X_j = 1)
+ * and P = their sum.  No probability is carried from one step to the next as a
+ * difference (whose relative error would double with every 1-branch).
+ * TRAJECTORY ACs (mixed-unitary channels only): every sample first draws its
+ * noise trajectory r -- for noise variable i, u = (SplitMix64_k(~seeds[v]) >> 11)
+ * 2^-53 with k = s*n_noise + i + 1, and r_i is the smallest value k with
+ * u < p_0 + ... + p_k (the branch probabilities stored in the AC), else the
+ * last -- and is then sampled as above with its noise variables observed at r,
+ * which draws P(x) = sum_r P(r) P(x | r) exactly.  Samples without any error
+ * share the groups of their vector; every other sample has groups of its own.
  * bits_dev [n_vectors][max_shots] uint64: outcome index of each sample
  * (entries s >= shots[v] are left untouched).  shots_dev [n_vectors] int32.
  * total_shots: a host-side upper bound on sum_v min(shots[v], max_shots) used
@@ -278,9 +293,9 @@ qkc_status qkc_sample(qkc_ac *ac, const uint64_t *seeds_dev, const int32_t *shot
 
 /*
  * qkc_sample_probs -- qkc_sample, and also probs_dev [n_vectors][max_shots] float64: for every
- * sample the probability P(x) of its outcome as the sampler carried it through the chain rule,
- * P(x_<j+1) = P(x_<j, X_j = 0) for a 0 and P(x_<j) - P(x_<j, X_j = 0) for a 1 (the numbers its
- * decisions compared).  Entries s >= shots[v] are left untouched; -1 marks a sample dropped by an
+ * sample the probability P(x) of its outcome as the sampler computed it: the branch probability
+ * P(x_<n-1, X_n-1 = x_n-1) of the last step's pass (for a TRAJECTORY AC, P(r, x) of the sample's
+ * trajectory).  Entries s >= shots[v] are left untouched; -1 marks a sample dropped by an
  * understated total_shots.  It lets a caller state each sample's probability (for example to
  * weight or score samples) and check the sampler's arithmetic against an exact P(x).
  */

@@ -189,13 +189,19 @@ __device__ __forceinline__ int ev_code(const EvSrc &e, const DevAC &ac, int64_t 
     }
     int q = var;  // the output variables are the qubits
     if (q < e.j) return (int)((e.prefix[col] >> (e.j - 1 - q)) & 1ull);
-    if (q == e.j && e.clamp) return 0;
+    if (q == e.j && e.clamp) return -3;
     return -1;
 }
-__device__ __forceinline__ double ind_value(int code, int val) {
-    if (code == -1) return 1.0;
-    if (code == -2) return val == 0 ? 1.0 : -1.0;
-    return code == val ? 1.0 : 0.0;
+// Indicator value for an evidence code: -1 free (1), -2 Pauli-Z sign (1, -1), k observed (1 at k);
+// -3 "split" (1 for value 0, the imaginary unit for value 1).  The density polynomial is real and
+// linear in each qubit's pair of indicators, so with qubit j split one upward pass returns
+// P(e, X_j = 0) + i P(e, X_j = 1): both branch probabilities of a sampling step, each computed
+// afresh (never one as a difference of two others).
+__device__ __forceinline__ double2 ind_value(int code, int val) {
+    if (code == -1) return make_double2(1.0, 0.0);
+    if (code == -2) return make_double2(val == 0 ? 1.0 : -1.0, 0.0);
+    if (code == -3) return val == 0 ? make_double2(1.0, 0.0) : make_double2(0.0, 1.0);
+    return make_double2(code == val ? 1.0 : 0.0, 0.0);
 }
 
 // FP32 leaves; also initialises the level-0 scale (0) and observed exponent.
@@ -213,7 +219,8 @@ __global__ void bind_leaves_f32(DevAC ac, const PassDesc *pd, int64_t pitch, flo
         int64_t gc = col0 + c;
         float2 v;
         if (i < ac.n_ind) {
-            v = make_float2((float)ind_value(ev_code(es, ac, gc, ac.ind_var[i]), ac.ind_val[i]), 0.0f);
+            const double2 lam = ind_value(ev_code(es, ac, gc, ac.ind_var[i]), ac.ind_val[i]);
+            v = make_float2((float)lam.x, (float)lam.y);
         } else if (i < ac.n_ind + ac.n_param) {
             v = pv[(int64_t)(i - ac.n_ind) * pv_pitch + vec_of(es, gc)];
         } else {
@@ -239,7 +246,7 @@ __global__ void bind_leaves_f64(DevAC ac, const PassDesc *pd, int64_t pitch, dou
         int64_t gc = col0 + c;
         double2 v;
         if (i < ac.n_ind) {
-            v = make_double2(ind_value(ev_code(es, ac, gc, ac.ind_var[i]), ac.ind_val[i]), 0.0);
+            v = ind_value(ev_code(es, ac, gc, ac.ind_var[i]), ac.ind_val[i]);
         } else if (i < ac.n_ind + ac.n_param) {
             v = pv[(int64_t)(i - ac.n_ind) * pv_pitch + vec_of(es, gc)];
         } else {
@@ -739,11 +746,14 @@ __device__ __forceinline__ C memo_leaf(const DevAC &ac, const MemoDesc &md, uint
     const uint8_t o = ac.op[n];
     if (o == OP_IND) {
         const int q = ac.ind_var[n], val = ac.ind_val[n];
-        double lam = 1.0;
+        double lam = 1.0, lim = 0.0;
         if (q < md.j) lam = ((int)(key & 1u) == val) ? 1.0 : 0.0;
-        else if (q == md.j && md.clamp) lam = (val == 0) ? 1.0 : 0.0;
+        else if (q == md.j && md.clamp) {  // split: 1 for X_j = 0, the imaginary unit for X_j = 1
+            lam = (val == 0) ? 1.0 : 0.0;
+            lim = (val == 0) ? 0.0 : 1.0;
+        }
         r.x = lam;
-        r.y = 0;
+        r.y = lim;
     } else if (o == OP_PARAM) {
         r = static_cast<const C *>(md.pv)[(int64_t)(n - ac.n_ind) * md.pv_pitch + vec];
     } else {
@@ -1327,12 +1337,6 @@ __global__ void sample_init(int64_t n_vec, int64_t max_shots, const int32_t *sho
     (void)shots;
 }
 
-__global__ void sample_set_total(const double2 *root, int64_t n_vec, double *g_P, const int32_t *n_active) {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (n_active) n_vec = min(n_vec, (int64_t)*n_active);
-    if (t < n_vec) g_P[t] = root[t].x;
-}
-
 // TRAJECTORY ACs (mixed-unitary channels, E_k = sqrt(p_k) U_k): the noise branches of every sample
 // are drawn from their state-independent probabilities, so P(x) = sum_r P(r) P(x | r) is sampled
 // exactly by drawing r first.  Uniform of sample s, noise variable i: (SplitMix64_k(~seed) >> 11)
@@ -1396,9 +1400,10 @@ __global__ void traj_groups(int64_t n_vec, int64_t max_shots, const int32_t *sho
 }
 __global__ void set_count(int32_t *dst, int32_t v) { *dst = v; }
 
-// Decide bit j of every live sample; mark the child group (2g + bit).
+// Decide bit j of every live sample; mark the child group (2g + bit).  pv[g] = (P(x_<j, X_j = 0),
+// P(x_<j, X_j = 1)) of the sample's group from this step's pass; P(x_<j) is their sum.
 __global__ void sample_decide(int64_t n_vec, int64_t max_shots, const int32_t *shots, const uint64_t *seeds, int j,
-                              int n_qubits, const double2 *p0v, const double *g_P, int32_t *s_group,
+                              int n_qubits, const double2 *pv, int32_t *s_group,
                               uint64_t *s_bits, int32_t *flag, const int32_t *g_count, int32_t *status) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n_vec * max_shots) return;
@@ -1409,7 +1414,7 @@ __global__ void sample_decide(int64_t n_vec, int64_t max_shots, const int32_t *s
         atomicExch(status, 1);
         return;
     }
-    double p0 = p0v[g].x, P = g_P[g];
+    const double p0 = pv[g].x, P = pv[g].x + pv[g].y;
     uint64_t k = (uint64_t)s * (uint64_t)n_qubits + (uint64_t)j + 1ull;
     double u = (double)(splitmix64_k(seeds[v], k) >> 11) * (1.0 / 9007199254740992.0);
     int bit = (u * P >= p0) ? 1 : 0;
@@ -1461,7 +1466,7 @@ __global__ void scan_sums(int32_t *bsum, int64_t nb) {
 // Build the next groups from the marked children and remap every sample.
 __global__ void sample_regroup(const int32_t *g_count_old, const int32_t *flag, const int32_t *pos,
                                const int32_t *bsum, const int32_t *g_vec, const uint64_t *g_prefix,
-                               const double *g_P, const double2 *p0v, int32_t *g_vec_n, uint64_t *g_prefix_n,
+                               const double2 *pv, int32_t *g_vec_n, uint64_t *g_prefix_n,
                                double *g_P_n, int32_t *g_count_new, int64_t nflag, const int32_t *g_traj,
                                int32_t *g_traj_n) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1475,8 +1480,7 @@ __global__ void sample_regroup(const int32_t *g_count_old, const int32_t *flag, 
     g_vec_n[id] = g_vec[g];
     g_prefix_n[id] = (g_prefix[g] << 1) | (uint64_t)bit;
     if (g_traj) g_traj_n[id] = g_traj[g];
-    double p0 = p0v[g].x, P = g_P[g];
-    g_P_n[id] = bit ? fmax(P - p0, 0.0) : p0;
+    g_P_n[id] = bit ? pv[g].y : pv[g].x;  // the child's probability P(x_<j+1), from this step's pass
 }
 __global__ void sample_remap(int64_t n_vec, int64_t max_shots, const int32_t *shots, const int32_t *pos,
                              const int32_t *bsum, int32_t *s_group, const uint64_t *s_bits, int64_t nflag,
@@ -3094,27 +3098,12 @@ static qkc_status sample_impl(qkc_ac *a, const uint64_t *seeds, const int32_t *s
         }
         return es;
     };
-    const int64_t bound0 = traj ? n_vec + live : n_vec;  // groups before the first step (host bound)
-    // P(empty prefix) for every vector: all indicators free
-    if (meta) {
-        if ((st = memo_pass(a, meta, 0, 0, n_vec, nullptr, n_vec, cur, s))) return st;
-        sample_set_total<<<(unsigned)((n_vec + TPB - 1) / TPB), TPB, 0, s>>>(a->d_root, n_vec, a->d_g_P[cur], nullptr);
-        a->launches += 2;
-        QKC_LAUNCH_CHECK();
-    } else {
-        const int32_t *na = traj ? a->d_gcount + cur : nullptr;
-        for (int64_t c0 = 0; c0 < bound0; c0 += a->tile) {
-            const int64_t nc = std::min<int64_t>(a->tile, bound0 - c0);
-            if ((st = run_up(a, group_ev(0, 0, na), c0, nc, s))) return st;
-            if ((st = run_roots(a, c0, nc, na, s))) return st;
-        }
-        sample_set_total<<<(unsigned)((bound0 + TPB - 1) / TPB), TPB, 0, s>>>(a->d_root, bound0, a->d_g_P[cur], na);
-        a->launches += 2;  // init + totals
-        QKC_LAUNCH_CHECK();
-    }
+    // groups before the first step (host bound); every step's pass gives both branch probabilities of
+    // each group, so no pass for P(empty prefix) is needed
+    const int64_t bound0 = traj ? n_vec + live : n_vec;
     int64_t bound = bound0;  // host upper bound of the group count
     for (int j = 0; j < nq; ++j) {
-        // p0 = P(prefix, X_j = 0) for every group (count on the device, bound on the host)
+        // (P(prefix, X_j = 0), P(prefix, X_j = 1)) for every group (count on the device, bound on the host)
         int32_t *gcount = a->d_gcount + cur;
         if (meta) {
             if ((st = memo_pass(a, meta, j, 1, n_vec, gcount, bound, cur, s))) return st;
@@ -3127,14 +3116,14 @@ static qkc_status sample_impl(qkc_ac *a, const uint64_t *seeds, const int32_t *s
         }
         const int64_t nflag = 2 * bound;
         QKC_CUDA(cudaMemsetAsync(a->d_flag, 0, sizeof(int32_t) * nflag, s));
-        sample_decide<<<gs, TPB, 0, s>>>(n_vec, max_shots, shots, seeds, j, nq, a->d_root, a->d_g_P[cur],
-                                         a->d_s_group, a->d_s_bits, a->d_flag, gcount, a->d_status);
+        sample_decide<<<gs, TPB, 0, s>>>(n_vec, max_shots, shots, seeds, j, nq, a->d_root, a->d_s_group,
+                                         a->d_s_bits, a->d_flag, gcount, a->d_status);
         const int64_t nb = (nflag + 1023) / 1024;
         scan_block<<<(unsigned)nb, 1024, 0, s>>>(a->d_flag, gcount, 2, a->d_pos, a->d_bsum);
         scan_sums<<<1, 1024, 0, s>>>(a->d_bsum, nb);
         const int nxt = cur ^ 1;
         sample_regroup<<<(unsigned)((nflag + TPB - 1) / TPB), TPB, 0, s>>>(
-            gcount, a->d_flag, a->d_pos, a->d_bsum, a->d_g_vec[cur], a->d_g_prefix[cur], a->d_g_P[cur], a->d_root,
+            gcount, a->d_flag, a->d_pos, a->d_bsum, a->d_g_vec[cur], a->d_g_prefix[cur], a->d_root,
             a->d_g_vec[nxt], a->d_g_prefix[nxt], a->d_g_P[nxt], a->d_gcount + nxt, nflag,
             traj ? a->d_g_traj[cur] : nullptr, traj ? a->d_g_traj[nxt] : nullptr);
         sample_remap<<<gs, TPB, 0, s>>>(n_vec, max_shots, shots, a->d_pos, a->d_bsum, a->d_s_group, a->d_s_bits,
