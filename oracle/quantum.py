@@ -330,5 +330,16 @@ def probabilities_many(circuit, angle_list, processes: int = 0):
     procs = processes or min(len(jobs), os.cpu_count() or 1)
     if procs <= 1:
         return [_probabilities_job(j) for j in jobs]
-    with ProcessPoolExecutor(procs, mp_context=mp.get_context("spawn")) as ex:
-        return list(ex.map(_probabilities_job, jobs))
+    # one thread per worker process: the workers already use the cores
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    os.environ.update({k: "1" for k in keys})
+    try:
+        with ProcessPoolExecutor(procs, mp_context=mp.get_context("spawn")) as ex:
+            return list(ex.map(_probabilities_job, jobs))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v

@@ -5,7 +5,8 @@ graph), its light-cone step AC in FP32, the default sampler (mode 1: memoised pa
 estimated cheaper), the default column tile, 64 parameter vectors x 10000 samples.  Checked
   * index for index against the whole density AC's per-group sampler (mode 0): every
     difference must be a decision within the FP32 tie margin, judged by the FP64 AC oracle;
-  * 2000 indices (8 vectors x 250) against the FP64 AC oracle's chain rule (acref);
+  * 2000 indices (8 vectors x 250) against the FP64 AC oracle's chain rule (acref), and each
+    of their probabilities P(x) as the sampler computed it;
   * p0 / P = P(x_j = 0 | x_<j) on 64 random prefixes against the oracle, relative 1e-5;
   * chi-square of all 496 two-qubit and 100 random three-qubit marginal histograms (each on
     its own 1000 samples) against the oracle's marginals, with a Kolmogorov-Smirnov check that
@@ -77,8 +78,10 @@ def bench_samples(cuda_ctx, qaoa32):
         ac = N().load_ac(cuda_ctx, b, precision=32)
         N().set_sampler(ac, mode)
         N().set_params(ac, t(W["angs"]))
-        bits = N().sample(ac, t(W["seeds"].astype(np.int64)), t(np.full(W["V"], W["S"], dtype=np.int32)), W["S"])
+        bits, probs = N().sample_probs(ac, t(W["seeds"].astype(np.int64)), t(np.full(W["V"], W["S"], dtype=np.int32)),
+                                       W["S"])
         out[key] = bits.cpu().numpy()
+        out[key + "_probs"] = probs.cpu().numpy()
         N().check_status(ac)
         ac.close()
         torch.cuda.empty_cache()
@@ -118,6 +121,30 @@ def test_bench_call_against_oracle_chain_rule(qaoa32, bench_samples):
             m = _margins(ref, W["angs"][v], int(W["seeds"][v]), 32, s_idx, got[s_idx], w[s_idx])
             assert max(m) <= TIE32, (v, m)
     assert mis <= 2, mis
+
+
+def test_bench_call_sample_probabilities(qaoa32, bench_samples):
+    """Each sample's probability P(x) as the bench call computed it (the last step's branch
+    probability) against the FP64 oracle, for the 2000 indices above: within the FP32 tie margin of
+    the last step, |dP(x)| <= 1e-5 P(x_<n-1)."""
+    W = qaoa32
+    n, k = 32, 250
+    vs = [0, 9, 18, 27, 36, 45, 54, 63]
+    tasks = []
+    for v in vs:
+        for s in range(k):
+            x = int(bench_samples["bench"][v, s])
+            bits = [(x >> (n - 1 - q)) & 1 for q in range(n)]
+            tasks.append(("up", W["angs"][v], bits))
+            tasks.append(("up", W["angs"][v], bits[:-1] + [-1]))
+    vals = R.run_many(W["dens"], tasks)
+    worst = 0.0
+    for i, v in enumerate(vs):
+        for s in range(k):
+            Px, Ppre = vals[2 * (i * k + s)].real, vals[2 * (i * k + s) + 1].real
+            err = abs(bench_samples["bench_probs"][v, s] - Px) / Ppre
+            worst = max(worst, err)
+    assert worst <= TIE32, worst
 
 
 def test_conditionals_relative_to_oracle(cuda_ctx, qaoa32):
