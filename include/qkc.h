@@ -368,7 +368,10 @@ qkc_status qkc_check_status(qkc_ac *ac);
  * capture.  Every call uses the same array and leaves its contents behind;
  * nothing a call reads is left over from an earlier call, but calls whose
  * work overlaps on the GPU (other streams, other host threads, other AC
- * handles) race on the array: serialise them.
+ * handles) race on the array: serialise them.  A call also rewrites the AC
+ * handle's own pass descriptor, so any other call on the same handle
+ * (qkc_evaluate, qkc_marginals, qkc_sample, ...) whose work overlaps it on
+ * another stream races with it too, as calls on one handle always do.
  */
 #define QKC_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
 qkc_status qkc_evaluate_static(qkc_ac *ac, const int32_t *col_vec_dev, const int8_t *evidence_dev,

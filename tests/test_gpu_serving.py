@@ -51,3 +51,36 @@ def test_alone_equals_mix_and_fp64_matches_oracle(cuda_ctx, kind):
         ref = Q.chain_rule_samples(P, r.seed, r.shots)
         mism += int((res64[r.rid].bits.astype(np.uint64) != ref).sum())
     assert mism == 0
+
+
+def test_mix_with_trajectory_ac_and_refused_requests(cuda_ctx):
+    """A TRAJECTORY AC (mixed-unitary noise, p=2) resident beside density ACs: its requests give the same
+    samples alone and in the mix, the FP64 one-request path matches the trajectory oracle, and a request
+    with more shots than a lane holds is refused and counted, not served."""
+    from oracle import trajectory as T
+    from paper_2103_17226_gb300 import native as N
+    from paper_2103_17226_gb300.serve import Request, Server, poisson_requests
+    circs, acs = _acs(1)
+    circs["qaoa6_p2"] = I.qaoa_maxcut(6, I.random_regular_graph(6, 3, 62), 2, I.NOISE_CFG2, name="qaoa6_p2")
+    acs["qaoa6_p2"] = N.compile(circs["qaoa6_p2"], N.QKC_AC_TRAJECTORY)
+    n_angles = {k: c.n_angles for k, c in circs.items()}
+    reqs = poisson_requests(list(acs), n_angles, rate_per_s=20000.0, duration_s=0.004, seed=9, shots_lo=50,
+                            shots_hi=1500)
+    big = Request(10 ** 6, "qaoa6_p2", np.zeros(n_angles["qaoa6_p2"]), 2000, 5, 0.0)  # more shots than a lane holds
+    srv = Server(cuda_ctx, acs, precision=32, lanes=2, max_batch=8, max_shots=1500, tile_columns=2048)
+    res, stats = srv.run(reqs + [big])
+    assert stats["completed"] == len(reqs) and stats["refused"] == 1 and big.rid not in res
+    assert stats["unfinished"] == 0
+    traj = [r for r in reqs if r.ac == "qaoa6_p2"]
+    assert len(traj) >= 5
+    alone = Server(cuda_ctx, acs, precision=32, lanes=1, max_batch=1, max_shots=1500, tile_columns=2048,
+                   serial=True)
+    res1, _ = alone.run([Request(r.rid, r.ac, r.angles, r.shots, r.seed, 0.0) for r in traj[:5]])
+    for r in traj[:5]:
+        assert np.array_equal(res1[r.rid].bits, res[r.rid].bits), r.rid
+    base = Server(cuda_ctx, acs, precision=64, lanes=1, max_batch=1, max_shots=1500, tile_columns=2048,
+                  serial=True)
+    res64, _ = base.run([Request(r.rid, r.ac, r.angles, r.shots, r.seed, 0.0) for r in traj[:3]])
+    for r in traj[:3]:
+        want = T.trajectory_samples(circs["qaoa6_p2"], r.angles, r.seed, r.shots)
+        assert np.array_equal(res64[r.rid].bits.astype(np.uint64), want), r.rid

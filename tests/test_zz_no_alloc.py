@@ -31,15 +31,24 @@ def test_static_scratch_matches_allocating_path_twice(cuda_ctx, prec):
     N.set_params(ac, torch.tensor(I.uniform_angles(V, c.n_angles, seed=31), device="cuda"))
     lib = N.lib()
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    # a first call: the library's module data (the fixed array among it) may be set up lazily on first use
+    ev, cv = _columns(4, 64, V, 0)
+    warm = torch.empty((64, 2), dtype=torch.float64, device="cuda")
+    assert lib.qkc_evaluate_static(ac._h, ctypes.c_void_p(cv.data_ptr()), ctypes.c_void_p(ev.data_ptr()), 64,
+                                   ctypes.c_void_p(warm.data_ptr()), stream) == 0, lib.qkc_last_error()
     # 20000 columns: several tiles of the fixed scratch; two different calls in a row
     for call, seed in enumerate((1, 2)):
         ev, cv = _columns(4, 20000, V, seed)
         want = N.evaluate(ac, cv, ev)
         got = torch.full_like(want, float("nan"))
+        torch.cuda.synchronize()
+        free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
         st = lib.qkc_evaluate_static(ac._h, ctypes.c_void_p(cv.data_ptr()), ctypes.c_void_p(ev.data_ptr()),
                                      ev.shape[0], ctypes.c_void_p(got.data_ptr()), stream)
         assert st == 0, lib.qkc_last_error()
         torch.cuda.synchronize()
+        # the property the entry point exists for: the call allocated no device memory
+        assert torch.cuda.mem_get_info()[0] == free0 and torch.cuda.memory_reserved() == reserved0, call
         assert torch.isfinite(got).all()
         assert (got - want).abs().max().item() < TOL[prec], call
 
