@@ -940,35 +940,47 @@ struct BChild {
     int2 s;    // their scale exponents; for a tabled tier-A child, first the two keys
 };
 
+// What a tier-B kernel needs of the memo and pass descriptors, read once into registers (a reference
+// into global memory would be re-read after every store, which the compiler cannot prove disjoint).
+struct BView {
+    const float4 *V4c;     // the lane's first column in row 0 of the value tile
+    const int *Sc;         // ... in level 0 of the scale words
+    const uint32_t *Kc;    // ... in row 0 of the group-key table
+    const float2 *VA;      // tier-A slots
+    const KeyPlan *kplan;  // key plans (untabled supports)
+    const uint64_t *prefix;
+    int64_t hp, pitch, kpitch, Vn, g0;
+    uint64_t vec0, vec1;   // the lane's two columns' vectors
+    int j;
+    bool two, narrow;
+};
+
 // Issue the loads of one child's two column values (tier B) or keys (tier-A, tabled); an
 // untabled tier-A child's keys are formed here from the group prefixes.
-__device__ __forceinline__ void bchild_issue(const uint4 r, BChild &c, const float4 *V4, const int *S, int64_t hp,
-                                             int64_t pitch, int64_t col, const MemoDesc &md, const EvSrc &es,
-                                             int64_t g0, bool two, bool narrow) {
+__device__ __forceinline__ void bchild_issue(const uint4 r, BChild &c, const BView &w) {
     if (r.x & 0x80000000u) {
-        c.v = __ldg(V4 + (int64_t)(r.x & 0x7fffffffu) * hp + (col >> 1));
-        c.s = __ldg(reinterpret_cast<const int2 *>(S + (int64_t)r.y * pitch + col));
+        c.v = __ldg(w.V4c + (int64_t)(r.x & 0x7fffffffu) * w.hp);
+        c.s = __ldg(reinterpret_cast<const int2 *>(w.Sc + (int64_t)r.y * w.pitch));
     } else {
         const int mid = (int)(r.y >> 8) - 1;
         if (mid >= 0) {  // tabled: this column pair's keys (col is even, the pitch a multiple of 64)
-            const uint2 kk = *reinterpret_cast<const uint2 *>(md.keys + (int64_t)mid * md.kpitch + col);
-            c.s = make_int2((int)kk.x, (int)(two ? kk.y : kk.x));  // no key past the last column
+            const uint2 kk = *reinterpret_cast<const uint2 *>(w.Kc + (int64_t)mid * w.kpitch);
+            c.s = make_int2((int)kk.x, (int)(w.two ? kk.y : kk.x));  // no key past the last column
         } else {  // the group prefixes in qubit order (bit q = x_q), compressed to the child's support
-            const KeyPlan *kp = md.kplan + (r.x - 1u);
-            const uint64_t pre0 = md.j ? __brevll(es.prefix[g0] << (64 - md.j)) : 0ull;
-            const uint64_t pre1 = md.j ? __brevll(es.prefix[two ? g0 + 1 : g0] << (64 - md.j)) : 0ull;
-            c.s = make_int2((int)plan_key(kp, pre0, narrow), (int)plan_key(kp, pre1, narrow));
+            const KeyPlan *kp = w.kplan + (r.x - 1u);
+            const uint64_t pre0 = w.j ? __brevll(w.prefix[w.g0] << (64 - w.j)) : 0ull;
+            const uint64_t pre1 = w.j ? __brevll(w.prefix[w.two ? w.g0 + 1 : w.g0] << (64 - w.j)) : 0ull;
+            c.s = make_int2((int)plan_key(kp, pre0, w.narrow), (int)plan_key(kp, pre1, w.narrow));
         }
     }
 }
 // Second stage for a tier-A child: its two slots, read by key.
-__device__ __forceinline__ void bchild_slots(const uint4 r, BChild &c, const float2 *VA, int64_t Vn, uint32_t vec0,
-                                             uint32_t vec1) {
+__device__ __forceinline__ void bchild_slots(const uint4 r, BChild &c, const BView &w) {
     if (r.x & 0x80000000u) return;
     const int kc = (int)(r.y & 0xffu);
-    const int64_t base = Vn * (int64_t)(((uint64_t)r.w << 32) | r.z);
-    const float2 a = VA[base + (int64_t)((((uint64_t)vec0) << kc) | (uint32_t)c.s.x)];
-    const float2 b = VA[base + (int64_t)((((uint64_t)vec1) << kc) | (uint32_t)c.s.y)];
+    const float2 *blk = w.VA + w.Vn * (int64_t)(((uint64_t)r.w << 32) | r.z);
+    const float2 a = blk[(w.vec0 << kc) | (uint32_t)c.s.x];
+    const float2 b = blk[(w.vec1 << kc) | (uint32_t)c.s.y];
     c.v = make_float4(a.x, a.y, b.x, b.y);
     c.s = make_int2(0, 0);
 }
@@ -983,7 +995,9 @@ constexpr int MEMO_B_BATCH = 2;
 // (tile rows and scale words, or group keys), then the tier-A slots by key, and only then are
 // the nodes combined and stored -- so a warp keeps several loads in flight instead of waiting
 // on one node's descriptor -> record -> value chain at a time.  The arithmetic (and its order)
-// is that of up_level_f32, so values equal the per-group sampler's bit for bit.
+// is that of up_level_f32, so values equal the per-group sampler's bit for bit.  The level's
+// largest exponent per column is tracked as the largest magnitude (the exponent is monotonic in
+// it) and taken once per item.
 // a.hi bit 0: the level reads unscaled tier-A values (its scale is at least 0); bit 1: this kernel
 // forms the level's scale itself (the items of the level's first node block write it).
 __global__ void __launch_bounds__(TPB, 3) memoB_level_f32(DevAC ac, LevelArgs a, const uint2 *bdesc, int64_t count,
@@ -994,20 +1008,27 @@ __global__ void __launch_bounds__(TPB, 3) memoB_level_f32(DevAC ac, LevelArgs a,
     __shared__ uint4 srec[TPB / 32][NBB][2];
     const int64_t ncols = desc_cols(*pd);
     if (ncols <= 0 || count <= 0) return;
-    const MemoDesc &md = *mdp;
-    const float2 *VA = static_cast<const float2 *>(md.VA);
-    const int64_t Vn = md.V;
-    const uint4 *brec = md.brec;
-    const bool narrow = md.j <= 32;
-    const EvSrc &es = pd->es;
+    const uint4 *brec = mdp->brec;
     const int64_t col0 = pd->col0;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int32_t *col_vec = pd->es.col_vec;
+    const int64_t n_vec = pd->es.n_vec;
+    BView w;
+    w.VA = static_cast<const float2 *>(mdp->VA);
+    w.kplan = mdp->kplan;
+    w.prefix = pd->es.prefix;
+    w.hp = a.pitch >> 1;
+    w.pitch = a.pitch;
+    w.kpitch = mdp->kpitch;
+    w.Vn = mdp->V;
+    w.j = mdp->j;
+    w.narrow = w.j <= 32;
+    const uint32_t *keys = mdp->keys;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     // work items (node block, column chunk) in 32 bits: blocks < 2^28, chunks < 2^26
     const uint32_t nchunks = (uint32_t)((ncols + 63) >> 6);
     const uint32_t nblk = (uint32_t)((count + NBB - 1) / NBB);
     const uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    const int64_t hp = a.pitch >> 1;
     float4 *V4 = reinterpret_cast<float4 *>(V);
     // item = node block * nchunks + column chunk, stepped by the warp count without division
     uint32_t blk = wid / nchunks, chunk = wid % nchunks;
@@ -1028,52 +1049,62 @@ __global__ void __launch_bounds__(TPB, 3) memoB_level_f32(DevAC ac, LevelArgs a,
         if (lane < nn) {
             const uint2 d = __ldg(bdesc + kb + lane);
             const uint32_t deg = d.y & 0xffffffu;
-            sdesc[w][lane] = d;
+            sdesc[wp][lane] = d;
             const uint4 r0 = __ldg(brec + d.x);
-            srec[w][lane][0] = r0;
-            srec[w][lane][1] = deg >= 2u ? __ldg(brec + d.x + 1) : r0;  // a node's own records only
+            srec[wp][lane][0] = r0;
+            srec[wp][lane][1] = deg >= 2u ? __ldg(brec + d.x + 1) : r0;  // a node's own records only
         }
         __syncwarp();
         if (col >= ncols) continue;
-        const bool two = col + 1 < ncols;
-        const int64_t g0 = col0 + col;
-        const uint32_t vec0 = (uint32_t)vec_of(es, g0), vec1 = (uint32_t)vec_of(es, two ? g0 + 1 : g0);
+        w.two = col + 1 < ncols;
+        w.g0 = col0 + col;
+        {
+            int64_t v0 = col_vec ? (int64_t)col_vec[w.g0] : w.g0;
+            int64_t v1 = col_vec ? (int64_t)col_vec[w.two ? w.g0 + 1 : w.g0] : (w.two ? w.g0 + 1 : w.g0);
+            v0 = v0 < 0 ? 0 : (v0 >= n_vec ? n_vec - 1 : v0);
+            v1 = v1 < 0 ? 0 : (v1 >= n_vec ? n_vec - 1 : v1);
+            w.vec0 = (uint64_t)v0;
+            w.vec1 = (uint64_t)v1;
+        }
+        w.V4c = reinterpret_cast<const float4 *>(V4) + (col >> 1);
+        w.Sc = S + col;
+        w.Kc = keys + col;
         int2 sL;
         if (a.hi & 2u) {
             sL.x = level_scale_col(ac, a.L, a.pitch, (int)(a.hi & 1u), S, obs, col);
-            sL.y = two ? level_scale_col(ac, a.L, a.pitch, (int)(a.hi & 1u), S, obs, col + 1) : sL.x;
+            sL.y = w.two ? level_scale_col(ac, a.L, a.pitch, (int)(a.hi & 1u), S, obs, col + 1) : sL.x;
             if (blk_i == 0) {
                 S[(int64_t)a.L * a.pitch + col] = sL.x;
-                if (two) S[(int64_t)a.L * a.pitch + col + 1] = sL.y;
+                if (w.two) S[(int64_t)a.L * a.pitch + col + 1] = sL.y;
             }
         } else {
             sL = *reinterpret_cast<const int2 *>(S + (int64_t)a.L * a.pitch + col);
         }
-        int m0 = -127, m1 = -127;
+        float mx0 = 0.f, mx1 = 0.f;  // largest |re|, |im| stored in each column
+        float4 *dst = V4 + (int64_t)(a.lo + kb) * w.hp + (col >> 1);
         for (int i0 = 0; i0 < nn; i0 += MEMO_B_BATCH) {
             BChild c[MEMO_B_BATCH][2];
             // 1. tile rows and scale words of tier-B children, group keys of tier-A children
 #pragma unroll
             for (int b = 0; b < MEMO_B_BATCH; ++b) {
                 if (i0 + b >= nn) break;
-                const uint32_t deg = sdesc[w][i0 + b].y & 0xffffffu;
-                bchild_issue(srec[w][i0 + b][0], c[b][0], V4, S, hp, a.pitch, col, md, es, g0, two, narrow);
-                if (deg >= 2u)
-                    bchild_issue(srec[w][i0 + b][1], c[b][1], V4, S, hp, a.pitch, col, md, es, g0, two, narrow);
+                const uint32_t deg = sdesc[wp][i0 + b].y & 0xffffffu;
+                bchild_issue(srec[wp][i0 + b][0], c[b][0], w);
+                if (deg >= 2u) bchild_issue(srec[wp][i0 + b][1], c[b][1], w);
             }
             // 2. the tier-A children's slots, by key
 #pragma unroll
             for (int b = 0; b < MEMO_B_BATCH; ++b) {
                 if (i0 + b >= nn) break;
-                const uint32_t deg = sdesc[w][i0 + b].y & 0xffffffu;
-                bchild_slots(srec[w][i0 + b][0], c[b][0], VA, Vn, vec0, vec1);
-                if (deg >= 2u) bchild_slots(srec[w][i0 + b][1], c[b][1], VA, Vn, vec0, vec1);
+                const uint32_t deg = sdesc[wp][i0 + b].y & 0xffffffu;
+                bchild_slots(srec[wp][i0 + b][0], c[b][0], w);
+                if (deg >= 2u) bchild_slots(srec[wp][i0 + b][1], c[b][1], w);
             }
             // 3. combine and store
 #pragma unroll
             for (int b = 0; b < MEMO_B_BATCH; ++b) {
                 if (i0 + b >= nn) break;
-                const uint2 dsc = sdesc[w][i0 + b];
+                const uint2 dsc = sdesc[wp][i0 + b];
                 const uint32_t deg = dsc.y & 0xffffffu, o = dsc.y >> 24;
                 float2 q0, q1;
                 if (o == OP_MUL) {
@@ -1093,18 +1124,19 @@ __global__ void __launch_bounds__(TPB, 3) memoB_level_f32(DevAC ac, LevelArgs a,
                     for (uint32_t e = 2; e < deg; ++e) {  // children beyond the second: one at a time
                         const uint4 r = __ldg(brec + dsc.x + e);
                         BChild x;
-                        bchild_issue(r, x, V4, S, hp, a.pitch, col, md, es, g0, two, narrow);
-                        bchild_slots(r, x, VA, Vn, vec0, vec1);
+                        bchild_issue(r, x, w);
+                        bchild_slots(r, x, w);
                         add(x);
                     }
                 }
-                V4[(int64_t)(a.lo + kb + i0 + b) * hp + (col >> 1)] = make_float4(q0.x, q0.y, q1.x, q1.y);
-                m0 = max(m0, exp_of(q0));
-                m1 = max(m1, exp_of(q1));
+                dst[(int64_t)(i0 + b) * w.hp] = make_float4(q0.x, q0.y, q1.x, q1.y);
+                mx0 = fmaxf(mx0, fmaxf(fabsf(q0.x), fabsf(q0.y)));
+                mx1 = fmaxf(mx1, fmaxf(fabsf(q1.x), fabsf(q1.y)));
             }
         }
+        const int m0 = (__float_as_int(mx0) >> 23) - 127, m1 = (__float_as_int(mx1) >> 23) - 127;
         atomicMax(obs + (int64_t)a.L * a.pitch + col, m0);
-        if (two) atomicMax(obs + (int64_t)a.L * a.pitch + col + 1, m1);
+        if (w.two) atomicMax(obs + (int64_t)a.L * a.pitch + col + 1, m1);
     }
 }
 
