@@ -78,11 +78,8 @@ constexpr int MEMO_APLANS = 7;  // log2 of the compress plans per step for scatt
 constexpr int MEMO_MARGIN = 2;  // early steps: memoise a node when its key space is >= 4x smaller than V 2^j
 
 // ------------------------------------------------------------------ device helpers
-__device__ __forceinline__ float pow2f(int k) {
-    if (k < -126) return 0.0f;
-    if (k > 127) k = 127;
-    return __int_as_float((k + 127) << 23);
-}
+// 2^k as a float: 0 below 2^-126, 2^127 above; no branches (the exponent field clamped to [0, 254])
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float(min(max(k + 127, 0), 254) << 23); }
 __device__ __forceinline__ int exp_of(float2 v) {
     // exponent field of max(|re|, |im|) minus the bias (-127 for zero / denormals)
     int a = __float_as_int(v.x) & 0x7fffffff, b = __float_as_int(v.y) & 0x7fffffff;
@@ -930,16 +927,6 @@ __device__ __forceinline__ int level_scale_col(const DevAC &ac, int L, int64_t p
     return s;
 }
 
-// One child of a tier-B node: its edge record (uint4) says where its two column values live.
-//   x bit 31 set: a tier-B child, x & 0x7fffffff = its row of the value tile, y = its level;
-//   else a tier-A child: x = 1 + its key plan, y = key width | (1 + group-key table row, 0 if
-//   the support is not tabled) << 8, (z, w) = its tier-A block offset in units (64 bits).
-// A tier-A slot holds an unscaled value: exponent 0.
-struct BChild {
-    float4 v;  // the two columns' values (x, y) and (z, w)
-    int2 s;    // their scale exponents; for a tabled tier-A child, first the two keys
-};
-
 // What a tier-B kernel needs of the memo and pass descriptors, read once into registers (a reference
 // into global memory would be re-read after every store, which the compiler cannot prove disjoint).
 struct BView {
@@ -950,54 +937,78 @@ struct BView {
     const KeyPlan *kplan;  // key plans (untabled supports)
     const uint64_t *prefix;
     int64_t hp, pitch, kpitch, Vn, g0;
-    uint64_t vec0, vec1;   // the lane's two columns' vectors
-    int j;
-    bool two, narrow;
+    uint32_t vec[4];       // the lane's four columns' vectors
+    int j, nv;             // nv: the lane's columns inside the tile (1..4)
+    bool narrow;
 };
 
-// Issue the loads of one child's two column values (tier B) or keys (tier-A, tabled); an
+// One child of a tier-B node for a lane's four columns: values and scale exponents (for a tabled
+// tier-A child, first its four keys).  Its edge record (uint4) says where the values live:
+//   x bit 31 set: a tier-B child, x & 0x7fffffff = its row of the value tile, y = its level;
+//   else a tier-A child: x = 1 + its key plan, y = key width | (1 + group-key table row, 0 if
+//   the support is not tabled) << 8, (z, w) = its tier-A block offset in units (64 bits).
+// A tier-A slot holds an unscaled value: exponent 0.
+struct BChild {
+    float4 a, b;  // columns 0-1 and 2-3: (re, im, re, im)
+    int4 s;
+};
+
+// Issue the loads of one child's four column values (tier B) or keys (tier-A, tabled); an
 // untabled tier-A child's keys are formed here from the group prefixes.
 __device__ __forceinline__ void bchild_issue(const uint4 r, BChild &c, const BView &w) {
     if (r.x & 0x80000000u) {
-        c.v = __ldg(w.V4c + (int64_t)(r.x & 0x7fffffffu) * w.hp);
-        c.s = __ldg(reinterpret_cast<const int2 *>(w.Sc + (int64_t)r.y * w.pitch));
+        const float4 *row = w.V4c + (int64_t)(r.x & 0x7fffffffu) * w.hp;
+        c.a = __ldg(row);
+        c.b = __ldg(row + 1);
+        c.s = __ldg(reinterpret_cast<const int4 *>(w.Sc + (int64_t)r.y * w.pitch));
     } else {
         const int mid = (int)(r.y >> 8) - 1;
-        if (mid >= 0) {  // tabled: this column pair's keys (col is even, the pitch a multiple of 64)
-            const uint2 kk = *reinterpret_cast<const uint2 *>(w.Kc + (int64_t)mid * w.kpitch);
-            c.s = make_int2((int)kk.x, (int)(w.two ? kk.y : kk.x));  // no key past the last column
+        if (mid >= 0) {  // tabled: the four columns' keys (col is a multiple of 4, so is the pitch)
+            const uint4 kk = *reinterpret_cast<const uint4 *>(w.Kc + (int64_t)mid * w.kpitch);
+            // no key is stored past the tile's last column: those columns reuse the first one's
+            c.s = make_int4((int)kk.x, (int)(w.nv > 1 ? kk.y : kk.x), (int)(w.nv > 2 ? kk.z : kk.x),
+                            (int)(w.nv > 3 ? kk.w : kk.x));
         } else {  // the group prefixes in qubit order (bit q = x_q), compressed to the child's support
             const KeyPlan *kp = w.kplan + (r.x - 1u);
-            const uint64_t pre0 = w.j ? __brevll(w.prefix[w.g0] << (64 - w.j)) : 0ull;
-            const uint64_t pre1 = w.j ? __brevll(w.prefix[w.two ? w.g0 + 1 : w.g0] << (64 - w.j)) : 0ull;
-            c.s = make_int2((int)plan_key(kp, pre0, w.narrow), (int)plan_key(kp, pre1, w.narrow));
+            int k[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int64_t g = w.g0 + (i < w.nv ? i : 0);
+                const uint64_t pre = w.j ? __brevll(w.prefix[g] << (64 - w.j)) : 0ull;
+                k[i] = (int)plan_key(kp, pre, w.narrow);
+            }
+            c.s = make_int4(k[0], k[1], k[2], k[3]);
         }
     }
 }
-// Second stage for a tier-A child: its two slots, read by key.
+// Second stage for a tier-A child: its four slots, read by key.
 __device__ __forceinline__ void bchild_slots(const uint4 r, BChild &c, const BView &w) {
     if (r.x & 0x80000000u) return;
     const int kc = (int)(r.y & 0xffu);
     const float2 *blk = w.VA + w.Vn * (int64_t)(((uint64_t)r.w << 32) | r.z);
-    const float2 a = blk[(w.vec0 << kc) | (uint32_t)c.s.x];
-    const float2 b = blk[(w.vec1 << kc) | (uint32_t)c.s.y];
-    c.v = make_float4(a.x, a.y, b.x, b.y);
-    c.s = make_int2(0, 0);
+    const float2 v0 = blk[((uint64_t)w.vec[0] << kc) | (uint32_t)c.s.x];
+    const float2 v1 = blk[((uint64_t)w.vec[1] << kc) | (uint32_t)c.s.y];
+    const float2 v2 = blk[((uint64_t)w.vec[2] << kc) | (uint32_t)c.s.z];
+    const float2 v3 = blk[((uint64_t)w.vec[3] << kc) | (uint32_t)c.s.w];
+    c.a = make_float4(v0.x, v0.y, v1.x, v1.y);
+    c.b = make_float4(v2.x, v2.y, v3.x, v3.y);
+    c.s = make_int4(0, 0, 0, 0);
 }
 
-// Tier-B nodes of one warp item whose child loads are issued together before any is combined.
-constexpr int MEMO_B_BATCH = 2;
+__device__ __forceinline__ float2 mul_scaled(float ax, float ay, float bx, float by, int e) {
+    return cscale(cmul(make_float2(ax, ay), make_float2(bx, by)), pow2f(e));
+}
 
 // One level of tier B (FP32): as up_level_f32 over a node list, tier-A children read by key.
-// A warp item is 32 tier-B nodes x 64 columns (float4 per lane = 2 columns).  The item's node
-// descriptors and first two edge records are staged in shared memory by one coalesced load,
-// then its nodes are taken MEMO_B_BATCH at a time: every child load of the batch is issued
-// (tile rows and scale words, or group keys), then the tier-A slots by key, and only then are
-// the nodes combined and stored -- so a warp keeps several loads in flight instead of waiting
-// on one node's descriptor -> record -> value chain at a time.  The arithmetic (and its order)
-// is that of up_level_f32, so values equal the per-group sampler's bit for bit.  The level's
-// largest exponent per column is tracked as the largest magnitude (the exponent is monotonic in
-// it) and taken once per item.
+// A warp item is 32 tier-B nodes x 128 columns, four consecutive columns per lane (two float4
+// per child row: a 1 KB segment per warp).  The item's node descriptors and first two edge
+// records are staged in shared memory by one coalesced load; then, per node, the loads of both
+// children are issued (tile rows and scale words, or group keys), then the tier-A slots by key,
+// and only then is the node combined and stored.  Four columns per lane spread the per-node work
+// (records, decoding, addresses) over twice the bytes of a two-column lane.  The arithmetic (and
+// its order) is that of up_level_f32, so values equal the per-group sampler's bit for bit.  The
+// level's largest exponent per column is tracked as the largest magnitude (the exponent is
+// monotonic in it) and taken once per item.
 // a.hi bit 0: the level reads unscaled tier-A values (its scale is at least 0); bit 1: this kernel
 // forms the level's scale itself (the items of the level's first node block write it).
 __global__ void __launch_bounds__(TPB, 3) memoB_level_f32(DevAC ac, LevelArgs a, const uint2 *bdesc, int64_t count,
@@ -1024,8 +1035,8 @@ __global__ void __launch_bounds__(TPB, 3) memoB_level_f32(DevAC ac, LevelArgs a,
     w.narrow = w.j <= 32;
     const uint32_t *keys = mdp->keys;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    // work items (node block, column chunk) in 32 bits: blocks < 2^28, chunks < 2^26
-    const uint32_t nchunks = (uint32_t)((ncols + 63) >> 6);
+    // work items (node block, column chunk) in 32 bits: blocks < 2^28, chunks < 2^25
+    const uint32_t nchunks = (uint32_t)((ncols + 127) >> 7);
     const uint32_t nblk = (uint32_t)((count + NBB - 1) / NBB);
     const uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -1034,7 +1045,7 @@ __global__ void __launch_bounds__(TPB, 3) memoB_level_f32(DevAC ac, LevelArgs a,
     uint32_t blk = wid / nchunks, chunk = wid % nchunks;
     const uint32_t dq = nw / nchunks, dr = nw % nchunks;
     while (blk < nblk) {
-        const int64_t col = (int64_t)chunk * 64 + lane * 2;
+        const int64_t col = (int64_t)chunk * 128 + lane * 4;
         const uint32_t blk_i = blk;
         chunk += dr;
         blk += dq;
@@ -1056,87 +1067,82 @@ __global__ void __launch_bounds__(TPB, 3) memoB_level_f32(DevAC ac, LevelArgs a,
         }
         __syncwarp();
         if (col >= ncols) continue;
-        w.two = col + 1 < ncols;
+        w.nv = (int)min((int64_t)4, ncols - col);
         w.g0 = col0 + col;
-        {
-            int64_t v0 = col_vec ? (int64_t)col_vec[w.g0] : w.g0;
-            int64_t v1 = col_vec ? (int64_t)col_vec[w.two ? w.g0 + 1 : w.g0] : (w.two ? w.g0 + 1 : w.g0);
-            v0 = v0 < 0 ? 0 : (v0 >= n_vec ? n_vec - 1 : v0);
-            v1 = v1 < 0 ? 0 : (v1 >= n_vec ? n_vec - 1 : v1);
-            w.vec0 = (uint64_t)v0;
-            w.vec1 = (uint64_t)v1;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t g = w.g0 + (i < w.nv ? i : 0);
+            int64_t v = col_vec ? (int64_t)col_vec[g] : g;
+            v = v < 0 ? 0 : (v >= n_vec ? n_vec - 1 : v);
+            w.vec[i] = (uint32_t)v;
         }
         w.V4c = reinterpret_cast<const float4 *>(V4) + (col >> 1);
         w.Sc = S + col;
         w.Kc = keys + col;
-        int2 sL;
+        int sl[4];
         if (a.hi & 2u) {
-            sL.x = level_scale_col(ac, a.L, a.pitch, (int)(a.hi & 1u), S, obs, col);
-            sL.y = w.two ? level_scale_col(ac, a.L, a.pitch, (int)(a.hi & 1u), S, obs, col + 1) : sL.x;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                sl[i] = i < w.nv ? level_scale_col(ac, a.L, a.pitch, (int)(a.hi & 1u), S, obs, col + i) : 0;
             if (blk_i == 0) {
-                S[(int64_t)a.L * a.pitch + col] = sL.x;
-                if (w.two) S[(int64_t)a.L * a.pitch + col + 1] = sL.y;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (i < w.nv) S[(int64_t)a.L * a.pitch + col + i] = sl[i];
             }
         } else {
-            sL = *reinterpret_cast<const int2 *>(S + (int64_t)a.L * a.pitch + col);
+            const int4 t4 = *reinterpret_cast<const int4 *>(S + (int64_t)a.L * a.pitch + col);
+            sl[0] = t4.x; sl[1] = t4.y; sl[2] = t4.z; sl[3] = t4.w;
         }
-        float mx0 = 0.f, mx1 = 0.f;  // largest |re|, |im| stored in each column
+        float mx[4] = {0.f, 0.f, 0.f, 0.f};  // largest |re|, |im| stored in each column
         float4 *dst = V4 + (int64_t)(a.lo + kb) * w.hp + (col >> 1);
-        for (int i0 = 0; i0 < nn; i0 += MEMO_B_BATCH) {
-            BChild c[MEMO_B_BATCH][2];
+        for (int i = 0; i < nn; ++i) {
+            const uint2 dsc = sdesc[wp][i];
+            const uint32_t deg = dsc.y & 0xffffffu, o = dsc.y >> 24;
+            const uint4 r0 = srec[wp][i][0], r1 = srec[wp][i][1];
+            BChild x, y;
             // 1. tile rows and scale words of tier-B children, group keys of tier-A children
-#pragma unroll
-            for (int b = 0; b < MEMO_B_BATCH; ++b) {
-                if (i0 + b >= nn) break;
-                const uint32_t deg = sdesc[wp][i0 + b].y & 0xffffffu;
-                bchild_issue(srec[wp][i0 + b][0], c[b][0], w);
-                if (deg >= 2u) bchild_issue(srec[wp][i0 + b][1], c[b][1], w);
-            }
+            bchild_issue(r0, x, w);
+            if (deg >= 2u) bchild_issue(r1, y, w);
             // 2. the tier-A children's slots, by key
-#pragma unroll
-            for (int b = 0; b < MEMO_B_BATCH; ++b) {
-                if (i0 + b >= nn) break;
-                const uint32_t deg = sdesc[wp][i0 + b].y & 0xffffffu;
-                bchild_slots(srec[wp][i0 + b][0], c[b][0], w);
-                if (deg >= 2u) bchild_slots(srec[wp][i0 + b][1], c[b][1], w);
-            }
+            bchild_slots(r0, x, w);
+            if (deg >= 2u) bchild_slots(r1, y, w);
             // 3. combine and store
+            float2 q[4];
+            if (o == OP_MUL) {
+                q[0] = mul_scaled(x.a.x, x.a.y, y.a.x, y.a.y, x.s.x + y.s.x - sl[0]);
+                q[1] = mul_scaled(x.a.z, x.a.w, y.a.z, y.a.w, x.s.y + y.s.y - sl[1]);
+                q[2] = mul_scaled(x.b.x, x.b.y, y.b.x, y.b.y, x.s.z + y.s.z - sl[2]);
+                q[3] = mul_scaled(x.b.z, x.b.w, y.b.z, y.b.w, x.s.w + y.s.w - sl[3]);
+            } else {
 #pragma unroll
-            for (int b = 0; b < MEMO_B_BATCH; ++b) {
-                if (i0 + b >= nn) break;
-                const uint2 dsc = sdesc[wp][i0 + b];
-                const uint32_t deg = dsc.y & 0xffffffu, o = dsc.y >> 24;
-                float2 q0, q1;
-                if (o == OP_MUL) {
-                    const BChild &x = c[b][0], &y = c[b][1];
-                    q0 = cscale(cmul(make_float2(x.v.x, x.v.y), make_float2(y.v.x, y.v.y)), pow2f(x.s.x + y.s.x - sL.x));
-                    q1 = cscale(cmul(make_float2(x.v.z, x.v.w), make_float2(y.v.z, y.v.w)), pow2f(x.s.y + y.s.y - sL.y));
-                } else {
-                    q0 = make_float2(0.f, 0.f);
-                    q1 = q0;
-                    auto add = [&](const BChild &x) {
-                        const float f0 = pow2f(x.s.x - sL.x), f1 = pow2f(x.s.y - sL.y);
-                        q0.x += x.v.x * f0; q0.y += x.v.y * f0;
-                        q1.x += x.v.z * f1; q1.y += x.v.w * f1;
-                    };
-                    add(c[b][0]);
-                    if (deg >= 2u) add(c[b][1]);
-                    for (uint32_t e = 2; e < deg; ++e) {  // children beyond the second: one at a time
-                        const uint4 r = __ldg(brec + dsc.x + e);
-                        BChild x;
-                        bchild_issue(r, x, w);
-                        bchild_slots(r, x, w);
-                        add(x);
-                    }
+                for (int k = 0; k < 4; ++k) q[k] = make_float2(0.f, 0.f);
+                auto add = [&](const BChild &c) {
+                    const float f0 = pow2f(c.s.x - sl[0]), f1 = pow2f(c.s.y - sl[1]);
+                    const float f2 = pow2f(c.s.z - sl[2]), f3 = pow2f(c.s.w - sl[3]);
+                    q[0].x += c.a.x * f0; q[0].y += c.a.y * f0;
+                    q[1].x += c.a.z * f1; q[1].y += c.a.w * f1;
+                    q[2].x += c.b.x * f2; q[2].y += c.b.y * f2;
+                    q[3].x += c.b.z * f3; q[3].y += c.b.w * f3;
+                };
+                add(x);
+                if (deg >= 2u) add(y);
+                for (uint32_t e = 2; e < deg; ++e) {  // children beyond the second: one at a time
+                    const uint4 r = __ldg(brec + dsc.x + e);
+                    BChild z;
+                    bchild_issue(r, z, w);
+                    bchild_slots(r, z, w);
+                    add(z);
                 }
-                dst[(int64_t)(i0 + b) * w.hp] = make_float4(q0.x, q0.y, q1.x, q1.y);
-                mx0 = fmaxf(mx0, fmaxf(fabsf(q0.x), fabsf(q0.y)));
-                mx1 = fmaxf(mx1, fmaxf(fabsf(q1.x), fabsf(q1.y)));
             }
+            float4 *d = dst + (int64_t)i * w.hp;
+            d[0] = make_float4(q[0].x, q[0].y, q[1].x, q[1].y);
+            d[1] = make_float4(q[2].x, q[2].y, q[3].x, q[3].y);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) mx[k] = fmaxf(mx[k], fmaxf(fabsf(q[k].x), fabsf(q[k].y)));
         }
-        const int m0 = (__float_as_int(mx0) >> 23) - 127, m1 = (__float_as_int(mx1) >> 23) - 127;
-        atomicMax(obs + (int64_t)a.L * a.pitch + col, m0);
-        if (w.two) atomicMax(obs + (int64_t)a.L * a.pitch + col + 1, m1);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (k < w.nv) atomicMax(obs + (int64_t)a.L * a.pitch + col + k, (__float_as_int(mx[k]) >> 23) - 127);
     }
 }
 
@@ -2906,7 +2912,7 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
                 level_scale_kernel<<<gs, TPB, 0, s>>>(d, (int)L, pitch, m->floor0[j][L], a->d_S, a->d_obs);
             // lo: the level's first tier-B row; hi: bit 0 reads tier-A values, bit 1 scale formed inline
             LevelArgs la{(uint32_t)b0, (uint32_t)m->floor0[j][L] | (inline_scale ? 2u : 0u), (int)L, pitch};
-            const int64_t cw = a->prec == 32 ? 64 : 32;
+            const int64_t cw = a->prec == 32 ? 128 : 32;  // columns per warp item
             const int64_t items = ((b1 - b0 + NBB - 1) / NBB) * ((pitch + cw - 1) / cw);
             // FP32: one wave of resident blocks, grid-striding over the items
             const unsigned g = grid_for(items * 32, TPB, (int64_t)sms * (a->prec == 32 ? a->ctx->memoB_blocks_per_sm : 8));
