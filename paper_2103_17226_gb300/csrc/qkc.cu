@@ -73,6 +73,8 @@ constexpr int OBS_EMPTY = -1000;
 constexpr int64_t MEMO_RUN_T = 1024;           // tier-A levels with at most this many threads per vector
                                                // are walked in runs by one launch
 constexpr int64_t MEMO_INLINE_SCALE_B = 4096;  // tier-B sets up to this size form level scales inline
+constexpr int64_t MEMO_RUN_B = 256;            // FP32 tier-B levels with at most this many nodes are walked
+                                               // in runs by one launch
 constexpr int MEMO_BKEYS = 32;  // per step, the distinct tier-A child supports whose group keys are tabled
 constexpr int MEMO_APLANS = 7;  // log2 of the compress plans per step for scattered tier-A key masks
 constexpr int MEMO_MARGIN = 2;  // early steps: memoise a node when its key space is >= 4x smaller than V 2^j
@@ -999,6 +1001,120 @@ __device__ __forceinline__ float2 mul_scaled(float ax, float ay, float bx, float
     return cscale(cmul(make_float2(ax, ay), make_float2(bx, by)), pow2f(e));
 }
 
+// The per-launch part of a tier-B kernel's view of its descriptors.
+__device__ __forceinline__ void bview_init(BView &w, const PassDesc *pd, const MemoDesc *mdp, int64_t pitch) {
+    w.VA = static_cast<const float2 *>(mdp->VA);
+    w.kplan = mdp->kplan;
+    w.prefix = pd->es.prefix;
+    w.hp = pitch >> 1;
+    w.pitch = pitch;
+    w.kpitch = mdp->kpitch;
+    w.Vn = mdp->V;
+    w.j = mdp->j;
+    w.narrow = w.j <= 32;
+}
+// The per-column part: the lane's four columns starting at tile column col (col < ncols).
+__device__ __forceinline__ void bview_cols(BView &w, int64_t col, int64_t ncols, int64_t col0, const int32_t *col_vec,
+                                           int64_t n_vec, const float4 *V4, const int *S, const uint32_t *keys) {
+    w.nv = (int)min((int64_t)4, ncols - col);
+    w.g0 = col0 + col;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t g = w.g0 + (i < w.nv ? i : 0);
+        int64_t v = col_vec ? (int64_t)col_vec[g] : g;
+        v = v < 0 ? 0 : (v >= n_vec ? n_vec - 1 : v);
+        w.vec[i] = (uint32_t)v;
+    }
+    w.V4c = V4 + (col >> 1);
+    w.Sc = S + col;
+    w.Kc = keys + col;
+}
+// Stage a node block's descriptors (first edge record, degree | op << 24) and first two edge records
+// in the warp's shared arrays (lane i: node i).
+__device__ __forceinline__ void bstage(uint2 *sd, uint4 (*sr)[2], const uint2 *bdesc, const uint4 *brec, int nn,
+                                       int lane) {
+    __syncwarp();
+    if (lane < nn) {
+        const uint2 d = __ldg(bdesc + lane);
+        const uint32_t deg = d.y & 0xffffffu;
+        sd[lane] = d;
+        const uint4 r0 = __ldg(brec + d.x);
+        sr[lane][0] = r0;
+        sr[lane][1] = deg >= 2u ? __ldg(brec + d.x + 1) : r0;  // a node's own records only
+    }
+    __syncwarp();
+}
+// The staged nodes 0 .. nn-1 for the lane's four columns: per node, both children's loads are issued
+// (tile rows and scale words, or group keys), then the tier-A slots by key, and only then is the node
+// combined and stored at dst[i * hp]; mx tracks each column's largest stored magnitude.
+__device__ __forceinline__ void bnodes(const uint2 *sd, const uint4 (*sr)[2], int nn, const int sl[4], float4 *dst,
+                                       const BView &w, const uint4 *brec, float mx[4]) {
+    for (int i = 0; i < nn; ++i) {
+        const uint2 dsc = sd[i];
+        const uint32_t deg = dsc.y & 0xffffffu, o = dsc.y >> 24;
+        const uint4 r0 = sr[i][0], r1 = sr[i][1];
+        BChild x, y;
+        bchild_issue(r0, x, w);
+        if (deg >= 2u) bchild_issue(r1, y, w);
+        bchild_slots(r0, x, w);
+        if (deg >= 2u) bchild_slots(r1, y, w);
+        float2 q[4];
+        if (o == OP_MUL) {
+            q[0] = mul_scaled(x.a.x, x.a.y, y.a.x, y.a.y, x.s.x + y.s.x - sl[0]);
+            q[1] = mul_scaled(x.a.z, x.a.w, y.a.z, y.a.w, x.s.y + y.s.y - sl[1]);
+            q[2] = mul_scaled(x.b.x, x.b.y, y.b.x, y.b.y, x.s.z + y.s.z - sl[2]);
+            q[3] = mul_scaled(x.b.z, x.b.w, y.b.z, y.b.w, x.s.w + y.s.w - sl[3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) q[k] = make_float2(0.f, 0.f);
+            auto add = [&](const BChild &c) {
+                const float f0 = pow2f(c.s.x - sl[0]), f1 = pow2f(c.s.y - sl[1]);
+                const float f2 = pow2f(c.s.z - sl[2]), f3 = pow2f(c.s.w - sl[3]);
+                q[0].x += c.a.x * f0; q[0].y += c.a.y * f0;
+                q[1].x += c.a.z * f1; q[1].y += c.a.w * f1;
+                q[2].x += c.b.x * f2; q[2].y += c.b.y * f2;
+                q[3].x += c.b.z * f3; q[3].y += c.b.w * f3;
+            };
+            add(x);
+            if (deg >= 2u) add(y);
+            for (uint32_t e = 2; e < deg; ++e) {  // children beyond the second: one at a time
+                const uint4 r = __ldg(brec + dsc.x + e);
+                BChild z;
+                bchild_issue(r, z, w);
+                bchild_slots(r, z, w);
+                add(z);
+            }
+        }
+        float4 *d = dst + (int64_t)i * w.hp;
+        d[0] = make_float4(q[0].x, q[0].y, q[1].x, q[1].y);
+        d[1] = make_float4(q[2].x, q[2].y, q[3].x, q[3].y);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) mx[k] = fmaxf(mx[k], fmaxf(fabsf(q[k].x), fabsf(q[k].y)));
+    }
+}
+// The level's scale exponent for the lane's columns: formed from its child levels (floor: the level
+// reads unscaled tier-A values) or read from S.
+__device__ __forceinline__ void blevel_scale(const DevAC &ac, int L, int64_t pitch, bool inline_scale, int floor_zero,
+                                             const int *S, const int *obs, int64_t col, int nv, int sl[4]) {
+    if (inline_scale) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) sl[i] = i < nv ? level_scale_col(ac, L, pitch, floor_zero, S, obs, col + i) : 0;
+    } else {
+        const int4 t4 = *reinterpret_cast<const int4 *>(S + (int64_t)L * pitch + col);
+        sl[0] = t4.x; sl[1] = t4.y; sl[2] = t4.z; sl[3] = t4.w;
+    }
+}
+__device__ __forceinline__ void bstore_scale(int *S, int L, int64_t pitch, int64_t col, int nv, const int sl[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        if (i < nv) S[(int64_t)L * pitch + col + i] = sl[i];
+}
+__device__ __forceinline__ void bobserve(int *obs, int L, int64_t pitch, int64_t col, int nv, const float mx[4]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (k < nv) atomicMax(obs + (int64_t)L * pitch + col + k, (__float_as_int(mx[k]) >> 23) - 127);
+}
+
 // One level of tier B (FP32): as up_level_f32 over a node list, tier-A children read by key.
 // A warp item is 32 tier-B nodes x 128 columns, four consecutive columns per lane (two float4
 // per child row: a 1 KB segment per warp).  The item's node descriptors and first two edge
@@ -1023,17 +1139,9 @@ __global__ void __launch_bounds__(TPB, 3) memoB_level_f32(DevAC ac, LevelArgs a,
     const int64_t col0 = pd->col0;
     const int32_t *col_vec = pd->es.col_vec;
     const int64_t n_vec = pd->es.n_vec;
-    BView w;
-    w.VA = static_cast<const float2 *>(mdp->VA);
-    w.kplan = mdp->kplan;
-    w.prefix = pd->es.prefix;
-    w.hp = a.pitch >> 1;
-    w.pitch = a.pitch;
-    w.kpitch = mdp->kpitch;
-    w.Vn = mdp->V;
-    w.j = mdp->j;
-    w.narrow = w.j <= 32;
     const uint32_t *keys = mdp->keys;
+    BView w;
+    bview_init(w, pd, mdp, a.pitch);
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     // work items (node block, column chunk) in 32 bits: blocks < 2^28, chunks < 2^25
     const uint32_t nchunks = (uint32_t)((ncols + 127) >> 7);
@@ -1053,96 +1161,72 @@ __global__ void __launch_bounds__(TPB, 3) memoB_level_f32(DevAC ac, LevelArgs a,
             chunk -= nchunks;
             ++blk;
         }
-        // stage the block's descriptors (first edge record, degree | op << 24) and first two records
         const int64_t kb = (int64_t)blk_i * NBB;
         const int nn = (int)min((int64_t)NBB, count - kb);
-        __syncwarp();
-        if (lane < nn) {
-            const uint2 d = __ldg(bdesc + kb + lane);
-            const uint32_t deg = d.y & 0xffffffu;
-            sdesc[wp][lane] = d;
-            const uint4 r0 = __ldg(brec + d.x);
-            srec[wp][lane][0] = r0;
-            srec[wp][lane][1] = deg >= 2u ? __ldg(brec + d.x + 1) : r0;  // a node's own records only
-        }
-        __syncwarp();
+        bstage(sdesc[wp], srec[wp], bdesc + kb, brec, nn, lane);
         if (col >= ncols) continue;
-        w.nv = (int)min((int64_t)4, ncols - col);
-        w.g0 = col0 + col;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int64_t g = w.g0 + (i < w.nv ? i : 0);
-            int64_t v = col_vec ? (int64_t)col_vec[g] : g;
-            v = v < 0 ? 0 : (v >= n_vec ? n_vec - 1 : v);
-            w.vec[i] = (uint32_t)v;
-        }
-        w.V4c = reinterpret_cast<const float4 *>(V4) + (col >> 1);
-        w.Sc = S + col;
-        w.Kc = keys + col;
+        bview_cols(w, col, ncols, col0, col_vec, n_vec, V4, S, keys);
         int sl[4];
-        if (a.hi & 2u) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                sl[i] = i < w.nv ? level_scale_col(ac, a.L, a.pitch, (int)(a.hi & 1u), S, obs, col + i) : 0;
-            if (blk_i == 0) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    if (i < w.nv) S[(int64_t)a.L * a.pitch + col + i] = sl[i];
+        blevel_scale(ac, a.L, a.pitch, (a.hi & 2u) != 0, (int)(a.hi & 1u), S, obs, col, w.nv, sl);
+        if ((a.hi & 2u) && blk_i == 0) bstore_scale(S, a.L, a.pitch, col, w.nv, sl);
+        float mx[4] = {0.f, 0.f, 0.f, 0.f};
+        bnodes(sdesc[wp], srec[wp], nn, sl, V4 + (int64_t)(a.lo + kb) * w.hp + (col >> 1), w, brec, mx);
+        bobserve(obs, a.L, a.pitch, col, w.nv, mx);
+    }
+}
+
+// A run of consecutive small tier-B levels in one launch: a block per 128-column chunk walks the
+// levels in order -- its warps split each level's node blocks and share the chunk's columns, with a
+// block barrier between levels (a level reads only lower levels of the same columns, and every
+// observed exponent it needs for its scale was recorded by this block) -- so a step whose tier B
+// is a chain of small levels costs one launch instead of one per level (and no scale launches).
+struct MemoBRunLevel {
+    uint32_t b0, count;  // first tier-B row of the level within the step, its tier-B nodes
+    int32_t L, floor0;   // level, whether it reads unscaled tier-A values
+};
+__global__ void __launch_bounds__(TPB, 3) memoB_run_f32(DevAC ac, const MemoBRunLevel *lv, int nlv,
+                                                      const uint2 *bdesc, const PassDesc *pd, const MemoDesc *mdp,
+                                                      int64_t pitch, float2 *__restrict__ V, int *__restrict__ S,
+                                                      int *__restrict__ obs) {
+    __shared__ uint2 sdesc[TPB / 32][NBB];
+    __shared__ uint4 srec[TPB / 32][NBB][2];
+    const int64_t ncols = desc_cols(*pd);
+    if (ncols <= 0) return;
+    const uint4 *brec = mdp->brec;
+    const int64_t col0 = pd->col0;
+    const int32_t *col_vec = pd->es.col_vec;
+    const int64_t n_vec = pd->es.n_vec;
+    const uint32_t *keys = mdp->keys;
+    BView w;
+    bview_init(w, pd, mdp, pitch);
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int nwb = (int)(blockDim.x >> 5);
+    float4 *V4 = reinterpret_cast<float4 *>(V);
+    const int64_t nchunks = (ncols + 127) >> 7;
+    for (int64_t chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+        const int64_t col = chunk * 128 + lane * 4;
+        const bool active = col < ncols;
+        if (active) bview_cols(w, col, ncols, col0, col_vec, n_vec, V4, S, keys);
+        for (int l = 0; l < nlv; ++l) {
+            const MemoBRunLevel L = lv[l];
+            int sl[4] = {0, 0, 0, 0};
+            float mx[4] = {0.f, 0.f, 0.f, 0.f};
+            bool any = false;
+            if (active) {
+                blevel_scale(ac, L.L, pitch, true, L.floor0, S, obs, col, w.nv, sl);
+                if (wp == 0) bstore_scale(S, L.L, pitch, col, w.nv, sl);
             }
-        } else {
-            const int4 t4 = *reinterpret_cast<const int4 *>(S + (int64_t)a.L * a.pitch + col);
-            sl[0] = t4.x; sl[1] = t4.y; sl[2] = t4.z; sl[3] = t4.w;
-        }
-        float mx[4] = {0.f, 0.f, 0.f, 0.f};  // largest |re|, |im| stored in each column
-        float4 *dst = V4 + (int64_t)(a.lo + kb) * w.hp + (col >> 1);
-        for (int i = 0; i < nn; ++i) {
-            const uint2 dsc = sdesc[wp][i];
-            const uint32_t deg = dsc.y & 0xffffffu, o = dsc.y >> 24;
-            const uint4 r0 = srec[wp][i][0], r1 = srec[wp][i][1];
-            BChild x, y;
-            // 1. tile rows and scale words of tier-B children, group keys of tier-A children
-            bchild_issue(r0, x, w);
-            if (deg >= 2u) bchild_issue(r1, y, w);
-            // 2. the tier-A children's slots, by key
-            bchild_slots(r0, x, w);
-            if (deg >= 2u) bchild_slots(r1, y, w);
-            // 3. combine and store
-            float2 q[4];
-            if (o == OP_MUL) {
-                q[0] = mul_scaled(x.a.x, x.a.y, y.a.x, y.a.y, x.s.x + y.s.x - sl[0]);
-                q[1] = mul_scaled(x.a.z, x.a.w, y.a.z, y.a.w, x.s.y + y.s.y - sl[1]);
-                q[2] = mul_scaled(x.b.x, x.b.y, y.b.x, y.b.y, x.s.z + y.s.z - sl[2]);
-                q[3] = mul_scaled(x.b.z, x.b.w, y.b.z, y.b.w, x.s.w + y.s.w - sl[3]);
-            } else {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) q[k] = make_float2(0.f, 0.f);
-                auto add = [&](const BChild &c) {
-                    const float f0 = pow2f(c.s.x - sl[0]), f1 = pow2f(c.s.y - sl[1]);
-                    const float f2 = pow2f(c.s.z - sl[2]), f3 = pow2f(c.s.w - sl[3]);
-                    q[0].x += c.a.x * f0; q[0].y += c.a.y * f0;
-                    q[1].x += c.a.z * f1; q[1].y += c.a.w * f1;
-                    q[2].x += c.b.x * f2; q[2].y += c.b.y * f2;
-                    q[3].x += c.b.z * f3; q[3].y += c.b.w * f3;
-                };
-                add(x);
-                if (deg >= 2u) add(y);
-                for (uint32_t e = 2; e < deg; ++e) {  // children beyond the second: one at a time
-                    const uint4 r = __ldg(brec + dsc.x + e);
-                    BChild z;
-                    bchild_issue(r, z, w);
-                    bchild_slots(r, z, w);
-                    add(z);
-                }
+            const int nb = (int)((L.count + NBB - 1) / NBB);
+            for (int b = wp; b < nb; b += nwb) {
+                const int64_t kb = (int64_t)b * NBB;
+                const int nn = (int)min((int64_t)NBB, (int64_t)L.count - kb);
+                bstage(sdesc[wp], srec[wp], bdesc + L.b0 + kb, brec, nn, lane);
+                if (active) bnodes(sdesc[wp], srec[wp], nn, sl, V4 + (int64_t)(L.b0 + kb) * w.hp + (col >> 1), w, brec, mx);
+                any = true;
             }
-            float4 *d = dst + (int64_t)i * w.hp;
-            d[0] = make_float4(q[0].x, q[0].y, q[1].x, q[1].y);
-            d[1] = make_float4(q[2].x, q[2].y, q[3].x, q[3].y);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) mx[k] = fmaxf(mx[k], fmaxf(fabsf(q[k].x), fabsf(q[k].y)));
+            if (active && any) bobserve(obs, L.L, pitch, col, w.nv, mx);
+            __syncthreads();
         }
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (k < w.nv) atomicMax(obs + (int64_t)a.L * a.pitch + col + k, (__float_as_int(mx[k]) >> 23) - 127);
     }
 }
 
@@ -1675,6 +1759,8 @@ struct qkc_ac {
         struct AItem { int L; int64_t off; int cnt; };  // one tier-A launch: level L, or a run of cnt levels
         std::vector<std::vector<AItem>> a_items;        // per step, in level order
         MemoARunLevel *d_runlv = nullptr;               // the runs' levels, all steps
+        std::vector<std::vector<AItem>> b_items;        // per step: tier-B launches (a level, or a run of cnt levels)
+        MemoBRunLevel *d_brunlv = nullptr;              // the tier-B runs' levels, all steps
         std::vector<std::vector<uint8_t>> floor0;               // per step, [D]
         std::vector<int64_t> a_base, b_base, offu_base, g_base;  // per step
         std::vector<double> a_bytes_slot, b_bytes_col;           // per step: algorithmic bytes per slot unit / column
@@ -1801,7 +1887,7 @@ extern "C" void qkc_free_ac(qkc_ac *a) {
     for (auto *m : a->memo) {
         if (!m) continue;
         cudaFree(m->d_a_nodes); cudaFree(m->d_a_grp); cudaFree(m->d_offu);
-        cudaFree(m->d_emask); cudaFree(m->d_runlv); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
+        cudaFree(m->d_emask); cudaFree(m->d_runlv); cudaFree(m->d_brunlv); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
         for (auto &g : m->gA) if (g.exec) cudaGraphExecDestroy(g.exec);
         for (auto &g : m->gB) if (g.exec) cudaGraphExecDestroy(g.exec);
         delete m;
@@ -2654,6 +2740,8 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
     std::vector<KeyPlan> kplan, aplan, bplan;
     std::vector<MemoARunLevel> runlv;
     m->a_items.assign(nq, {});
+    m->b_items.assign(nq, {});
+    std::vector<MemoBRunLevel> brunlv;
     std::vector<int32_t> plan_of;  // per node: its key plan in this step, -1 if none yet
     std::vector<int64_t> row_of;   // per node: its tier-B row in this step
     std::vector<char> reach;       // per node: reachable from this step's root
@@ -2802,6 +2890,32 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
             m->t_lvl[j][L] = th;
         }
         m->bp_cnt.push_back((int64_t)bplan.size() - m->bp_base[j]);
+        {  // tier-B launches: consecutive small levels form one run (FP32: a block per column chunk walks them)
+            std::vector<uint32_t> pend;
+            auto flush = [&]() {
+                if (pend.size() >= 2) {
+                    m->b_items[j].push_back({-1, (int64_t)brunlv.size(), (int)pend.size()});
+                    for (uint32_t L : pend)
+                        brunlv.push_back(MemoBRunLevel{(uint32_t)m->b_lvl[j][L],
+                                                       (uint32_t)(m->b_lvl[j][L + 1] - m->b_lvl[j][L]), (int32_t)L,
+                                                       (int32_t)m->floor0[j][L]});
+                } else if (pend.size() == 1) {
+                    m->b_items[j].push_back({(int)pend[0], 0, 0});
+                }
+                pend.clear();
+            };
+            for (uint32_t L = 1; L < D; ++L) {
+                const int64_t cnt = m->b_lvl[j][L + 1] - m->b_lvl[j][L];
+                if (cnt == 0) continue;
+                if (a->prec == 32 && cnt <= MEMO_RUN_B) {
+                    pend.push_back(L);
+                } else {
+                    flush();
+                    m->b_items[j].push_back({(int)L, 0, 0});
+                }
+            }
+            flush();
+        }
         {  // tier-A launches: consecutive small levels form one run (a block per vector walks them)
             std::vector<uint32_t> pend;
             auto flush = [&]() {
@@ -2846,13 +2960,14 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
         (*st = upload(&m->d_offu, offu.data(), offu.size(), dummy)) ||
         (*st = upload(&m->d_emask, emask.data(), emask.size(), dummy)) ||
         (*st = upload(&m->d_runlv, runlv.data(), runlv.size(), dummy)) ||
+        (*st = upload(&m->d_brunlv, brunlv.data(), brunlv.size(), dummy)) ||
         (*st = upload(&m->d_bdesc, bdesc.data(), bdesc.size(), dummy)) ||
         (*st = upload(&m->d_brec, brec.data(), brec.size(), dummy)) ||
         (*st = upload(&m->d_kplan, kplan.data(), kplan.size(), dummy)) ||
         (*st = upload(&m->d_aplan, aplan.data(), aplan.size(), dummy)) ||
         (*st = upload(&m->d_bplan, bplan.data(), bplan.size(), dummy))) {
         cudaFree(m->d_a_nodes); cudaFree(m->d_a_grp); cudaFree(m->d_offu);
-        cudaFree(m->d_emask); cudaFree(m->d_runlv); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
+        cudaFree(m->d_emask); cudaFree(m->d_runlv); cudaFree(m->d_brunlv); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
         delete m;
         return nullptr;
     }
@@ -2905,9 +3020,17 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
         if (a->prec == 32)
             obs_reset<<<(unsigned)(((int64_t)D * pitch + TPB - 1) / TPB), TPB, 0, s>>>(a->d_obs, (int64_t)D * pitch);
         const bool inline_scale = m->b_lvl[j][D] <= MEMO_INLINE_SCALE_B;
-        for (uint32_t L = 1; L < D; ++L) {
+        const uint2 *bd_j = m->d_bdesc + m->b_base[j];
+        for (const auto &it : m->b_items[j]) {
+            if (it.cnt > 0) {  // a run of small levels (FP32): a block per 128-column chunk walks them
+                const int64_t chunks = (pitch + 127) / 128;
+                const unsigned g = (unsigned)std::min<int64_t>(chunks, (int64_t)sms * a->ctx->memoB_blocks_per_sm);
+                memoB_run_f32<<<g, TPB, 0, s>>>(d, m->d_brunlv + it.off, it.cnt, bd_j, a->d_desc, a->d_mdesc, pitch,
+                                                 (float2 *)a->d_V, a->d_S, a->d_obs);
+                continue;
+            }
+            const uint32_t L = (uint32_t)it.L;
             const int64_t b0 = m->b_lvl[j][L], b1 = m->b_lvl[j][L + 1];
-            if (b1 == b0) continue;
             if (a->prec == 32 && !inline_scale)
                 level_scale_kernel<<<gs, TPB, 0, s>>>(d, (int)L, pitch, m->floor0[j][L], a->d_S, a->d_obs);
             // lo: the level's first tier-B row; hi: bit 0 reads tier-A values, bit 1 scale formed inline
@@ -2916,12 +3039,11 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
             const int64_t items = ((b1 - b0 + NBB - 1) / NBB) * ((pitch + cw - 1) / cw);
             // FP32: one wave of resident blocks, grid-striding over the items
             const unsigned g = grid_for(items * 32, TPB, (int64_t)sms * (a->prec == 32 ? a->ctx->memoB_blocks_per_sm : 8));
-            const uint2 *bd = m->d_bdesc + m->b_base[j] + b0;
             if (a->prec == 32)
-                memoB_level_f32<<<g, TPB, 0, s>>>(d, la, bd, b1 - b0, a->d_desc, a->d_mdesc, (float2 *)a->d_V, a->d_S,
-                                                   a->d_obs);
+                memoB_level_f32<<<g, TPB, 0, s>>>(d, la, bd_j + b0, b1 - b0, a->d_desc, a->d_mdesc, (float2 *)a->d_V,
+                                                   a->d_S, a->d_obs);
             else
-                memoB_level_f64<<<g, TPB, 0, s>>>(la, bd, b1 - b0, a->d_desc, a->d_mdesc, (double2 *)a->d_V);
+                memoB_level_f64<<<g, TPB, 0, s>>>(la, bd_j + b0, b1 - b0, a->d_desc, a->d_mdesc, (double2 *)a->d_V);
         }
     }
     memo_root<<<(unsigned)((pitch + TPB - 1) / TPB), TPB, 0, s>>>(a->d_mdesc, a->d_desc, a->roots[j], a->root_lev[j],
@@ -2934,7 +3056,7 @@ static int64_t memoB_launches(const qkc_ac *a, const qkc_ac::MemoMeta *m, int j)
         n += a->prec == 32 ? 1 : 0;
         n += m->bp_cnt[j] > 0;
         const int per = (a->prec == 32 && m->b_lvl[j][a->D] > MEMO_INLINE_SCALE_B) ? 2 : 1;
-        for (uint32_t L = 1; L < a->D; ++L) n += (m->b_lvl[j][L + 1] > m->b_lvl[j][L]) * per;
+        for (const auto &it : m->b_items[j]) n += it.cnt > 0 ? 1 : per;
     }
     return n;
 }
