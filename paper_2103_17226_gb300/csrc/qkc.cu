@@ -956,13 +956,23 @@ struct BChild {
 };
 
 // Issue the loads of one child's four column values (tier B) or keys (tier-A, tabled); an
-// untabled tier-A child's keys are formed here from the group prefixes.
+// untabled tier-A child's keys are formed here from the group prefixes.  NC: tier-B rows and scale
+// words through the read-only path (they were written by earlier launches); else plain loads (a run
+// reads rows it wrote itself).
+template <bool NC = true>
 __device__ __forceinline__ void bchild_issue(const uint4 r, BChild &c, const BView &w) {
     if (r.x & 0x80000000u) {
         const float4 *row = w.V4c + (int64_t)(r.x & 0x7fffffffu) * w.hp;
-        c.a = __ldg(row);
-        c.b = __ldg(row + 1);
-        c.s = __ldg(reinterpret_cast<const int4 *>(w.Sc + (int64_t)r.y * w.pitch));
+        const int4 *sc = reinterpret_cast<const int4 *>(w.Sc + (int64_t)r.y * w.pitch);
+        if (NC) {
+            c.a = __ldg(row);
+            c.b = __ldg(row + 1);
+            c.s = __ldg(sc);
+        } else {
+            c.a = row[0];
+            c.b = row[1];
+            c.s = *sc;
+        }
     } else {
         const int mid = (int)(r.y >> 8) - 1;
         if (mid >= 0) {  // tabled: the four columns' keys (col is a multiple of 4, so is the pitch)
@@ -1047,6 +1057,7 @@ __device__ __forceinline__ void bstage(uint2 *sd, uint4 (*sr)[2], const uint2 *b
 // The staged nodes 0 .. nn-1 for the lane's four columns: per node, both children's loads are issued
 // (tile rows and scale words, or group keys), then the tier-A slots by key, and only then is the node
 // combined and stored at dst[i * hp]; mx tracks each column's largest stored magnitude.
+template <bool NC = true>
 __device__ __forceinline__ void bnodes(const uint2 *sd, const uint4 (*sr)[2], int nn, const int sl[4], float4 *dst,
                                        const BView &w, const uint4 *brec, float mx[4]) {
     for (int i = 0; i < nn; ++i) {
@@ -1054,8 +1065,8 @@ __device__ __forceinline__ void bnodes(const uint2 *sd, const uint4 (*sr)[2], in
         const uint32_t deg = dsc.y & 0xffffffu, o = dsc.y >> 24;
         const uint4 r0 = sr[i][0], r1 = sr[i][1];
         BChild x, y;
-        bchild_issue(r0, x, w);
-        if (deg >= 2u) bchild_issue(r1, y, w);
+        bchild_issue<NC>(r0, x, w);
+        if (deg >= 2u) bchild_issue<NC>(r1, y, w);
         bchild_slots(r0, x, w);
         if (deg >= 2u) bchild_slots(r1, y, w);
         float2 q[4];
@@ -1080,7 +1091,7 @@ __device__ __forceinline__ void bnodes(const uint2 *sd, const uint4 (*sr)[2], in
             for (uint32_t e = 2; e < deg; ++e) {  // children beyond the second: one at a time
                 const uint4 r = __ldg(brec + dsc.x + e);
                 BChild z;
-                bchild_issue(r, z, w);
+                bchild_issue<NC>(r, z, w);
                 bchild_slots(r, z, w);
                 add(z);
             }
@@ -1175,16 +1186,16 @@ __global__ void __launch_bounds__(TPB, 3) memoB_level_f32(DevAC ac, LevelArgs a,
     }
 }
 
-// A run of consecutive small tier-B levels in one launch: a block per 128-column chunk walks the
-// levels in order -- its warps split each level's node blocks and share the chunk's columns, with a
-// block barrier between levels (a level reads only lower levels of the same columns, and every
-// observed exponent it needs for its scale was recorded by this block) -- so a step whose tier B
-// is a chain of small levels costs one launch instead of one per level (and no scale launches).
+// A run of consecutive small tier-B levels in one launch: a warp per 128-column chunk walks the levels
+// in order, every node of each level for its own columns.  A level reads only lower levels of the
+// same columns, and each lane reads back only what it wrote itself (tile rows, scale words, observed
+// exponents of its four columns), so no barrier is needed -- and a step whose tier B is a chain of
+// small levels costs one launch instead of one per level (and no scale launches).
 struct MemoBRunLevel {
     uint32_t b0, count;  // first tier-B row of the level within the step, its tier-B nodes
     int32_t L, floor0;   // level, whether it reads unscaled tier-A values
 };
-__global__ void __launch_bounds__(TPB, 3) memoB_run_f32(DevAC ac, const MemoBRunLevel *lv, int nlv,
+__global__ void __launch_bounds__(TPB, 2) memoB_run_f32(DevAC ac, const MemoBRunLevel *lv, int nlv,
                                                       const uint2 *bdesc, const PassDesc *pd, const MemoDesc *mdp,
                                                       int64_t pitch, float2 *__restrict__ V, int *__restrict__ S,
                                                       int *__restrict__ obs) {
@@ -1200,10 +1211,10 @@ __global__ void __launch_bounds__(TPB, 3) memoB_run_f32(DevAC ac, const MemoBRun
     BView w;
     bview_init(w, pd, mdp, pitch);
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    const int nwb = (int)(blockDim.x >> 5);
     float4 *V4 = reinterpret_cast<float4 *>(V);
     const int64_t nchunks = (ncols + 127) >> 7;
-    for (int64_t chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t chunk = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; chunk < nchunks; chunk += nw) {
         const int64_t col = chunk * 128 + lane * 4;
         const bool active = col < ncols;
         if (active) bview_cols(w, col, ncols, col0, col_vec, n_vec, V4, S, keys);
@@ -1211,21 +1222,17 @@ __global__ void __launch_bounds__(TPB, 3) memoB_run_f32(DevAC ac, const MemoBRun
             const MemoBRunLevel L = lv[l];
             int sl[4] = {0, 0, 0, 0};
             float mx[4] = {0.f, 0.f, 0.f, 0.f};
-            bool any = false;
             if (active) {
                 blevel_scale(ac, L.L, pitch, true, L.floor0, S, obs, col, w.nv, sl);
-                if (wp == 0) bstore_scale(S, L.L, pitch, col, w.nv, sl);
+                bstore_scale(S, L.L, pitch, col, w.nv, sl);
             }
-            const int nb = (int)((L.count + NBB - 1) / NBB);
-            for (int b = wp; b < nb; b += nwb) {
-                const int64_t kb = (int64_t)b * NBB;
-                const int nn = (int)min((int64_t)NBB, (int64_t)L.count - kb);
+            for (uint32_t kb = 0; kb < L.count; kb += NBB) {
+                const int nn = (int)min((uint32_t)NBB, L.count - kb);
                 bstage(sdesc[wp], srec[wp], bdesc + L.b0 + kb, brec, nn, lane);
-                if (active) bnodes(sdesc[wp], srec[wp], nn, sl, V4 + (int64_t)(L.b0 + kb) * w.hp + (col >> 1), w, brec, mx);
-                any = true;
+                if (active)
+                    bnodes<false>(sdesc[wp], srec[wp], nn, sl, V4 + (int64_t)(L.b0 + kb) * w.hp + (col >> 1), w, brec, mx);
             }
-            if (active && any) bobserve(obs, L.L, pitch, col, w.nv, mx);
-            __syncthreads();
+            if (active) bobserve(obs, L.L, pitch, col, w.nv, mx);
         }
     }
 }
@@ -2890,7 +2897,7 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
             m->t_lvl[j][L] = th;
         }
         m->bp_cnt.push_back((int64_t)bplan.size() - m->bp_base[j]);
-        {  // tier-B launches: consecutive small levels form one run (FP32: a block per column chunk walks them)
+        {  // tier-B launches: consecutive small levels form one run (FP32: a warp per column chunk walks them)
             std::vector<uint32_t> pend;
             auto flush = [&]() {
                 if (pend.size() >= 2) {
@@ -3022,9 +3029,9 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
         const bool inline_scale = m->b_lvl[j][D] <= MEMO_INLINE_SCALE_B;
         const uint2 *bd_j = m->d_bdesc + m->b_base[j];
         for (const auto &it : m->b_items[j]) {
-            if (it.cnt > 0) {  // a run of small levels (FP32): a block per 128-column chunk walks them
-                const int64_t chunks = (pitch + 127) / 128;
-                const unsigned g = (unsigned)std::min<int64_t>(chunks, (int64_t)sms * a->ctx->memoB_blocks_per_sm);
+            if (it.cnt > 0) {  // a run of small levels (FP32): a warp per 128-column chunk walks them
+                const int64_t chunks = (pitch + 127) / 128;  // a warp per chunk
+                const unsigned g = (unsigned)std::min<int64_t>((chunks + TPB / 32 - 1) / (TPB / 32), (int64_t)sms * 2);
                 memoB_run_f32<<<g, TPB, 0, s>>>(d, m->d_brunlv + it.off, it.cnt, bd_j, a->d_desc, a->d_mdesc, pitch,
                                                  (float2 *)a->d_V, a->d_S, a->d_obs);
                 continue;

@@ -87,6 +87,7 @@ class _Lane:
     batch: list = field(default_factory=list)
     max_shots_in_batch: int = 0
     event: torch.cuda.Event = None
+    start: torch.cuda.Event = None  # recorded before the batch's first copy: GPU time per batch
 
 
 class Server:
@@ -143,6 +144,8 @@ class Server:
             ln.h_seeds[i] = int(np.int64(np.uint64(r.seed)))
             ln.h_shots[i] = r.shots
         with torch.cuda.stream(ln.stream):
+            ln.start = torch.cuda.Event(enable_timing=True)
+            ln.start.record(ln.stream)
             ln.d_angles[:B].copy_(ln.h_angles[:B], non_blocking=True)
             ln.d_seeds[:B].copy_(ln.h_seeds[:B], non_blocking=True)
             ln.d_shots[:B].copy_(ln.h_shots[:B], non_blocking=True)
@@ -150,7 +153,7 @@ class Server:
             N.sample(ln.ac, ln.d_seeds[:B], ln.d_shots[:B], S, out=ln.d_bits[:B].view(-1)[:B * S].view(B, S),
                      stream=ln.stream, total_shots=sum(r.shots for r in reqs))
             ln.h_bits[:B].view(-1)[:B * S].copy_(ln.d_bits[:B].view(-1)[:B * S], non_blocking=True)
-            ln.event = torch.cuda.Event()
+            ln.event = torch.cuda.Event(enable_timing=True)
             ln.event.record(ln.stream)
         ln.batch = list(reqs)
         ln.max_shots_in_batch = S
@@ -166,6 +169,8 @@ class Server:
         nxt = 0
         t0 = time.perf_counter()
         busy = []
+        gpu_ms = {name: 0.0 for name in self.lanes}  # event time of the batches of each AC
+        batches = {name: 0 for name in self.lanes}
         while len(results) < len(order):
             now = time.perf_counter() - t0
             if time_limit is not None and now > time_limit:
@@ -179,6 +184,8 @@ class Server:
             for ln in busy:
                 if ln.event.query():
                     done = time.perf_counter() - t0
+                    gpu_ms[ln.name] += ln.start.elapsed_time(ln.event)
+                    batches[ln.name] += 1
                     S = ln.max_shots_in_batch
                     B = len(ln.batch)
                     bits = ln.h_bits[:B].view(-1)[:B * S].view(B, S).numpy()
@@ -225,7 +232,11 @@ class Server:
         stats = dict(completed=len(results), submitted=len(order), refused=len(refused), unfinished=len(unfinished),
                      elapsed_s=elapsed, samples=samples, samples_per_s=samples / elapsed if elapsed > 0 else 0.0,
                      p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3),
-                     latency_over="every admitted request (unfinished ones at their elapsed time)")
+                     latency_over="every admitted request (unfinished ones at their elapsed time)",
+                     # where the time goes: each batch's event time from its first copy to its last (lanes of
+                     # different ACs overlap, so the sum can exceed the elapsed time)
+                     batch_gpu_s={k: round(v / 1e3, 3) for k, v in gpu_ms.items()}, batches=batches,
+                     batch_gpu_s_total=round(sum(gpu_ms.values()) / 1e3, 3))
         return results, stats
 
 
