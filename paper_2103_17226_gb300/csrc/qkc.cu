@@ -73,7 +73,7 @@ constexpr int OBS_EMPTY = -1000;
 constexpr int64_t MEMO_RUN_T = 1024;           // tier-A levels with at most this many threads per vector
                                                // are walked in runs by one launch
 constexpr int64_t MEMO_INLINE_SCALE_B = 4096;  // tier-B sets up to this size form level scales inline
-constexpr int64_t MEMO_RUN_B = 256;            // FP32 tier-B levels with at most this many nodes are walked
+constexpr int64_t MEMO_RUN_B = NBB;            // FP32 tier-B levels of one node block (at most 32 nodes) are walked
                                                // in runs by one launch
 constexpr int MEMO_BKEYS = 32;  // per step, the distinct tier-A child supports whose group keys are tabled
 constexpr int MEMO_APLANS = 7;  // log2 of the compress plans per step for scattered tier-A key masks

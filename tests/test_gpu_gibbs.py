@@ -63,4 +63,4 @@ def test_gibbs_stationary_distribution(cuda_ctx):
     keep = P * chains > 5
     exp = P[keep] * chains
     obs = counts[keep] * exp.sum() / counts[keep].sum()
-    assert chisquare(obs, exp).pvalue > 1e-4
+    assert chisquare(obs, exp).pvalue > 0.01

@@ -220,7 +220,7 @@ def test_sampling_distribution_chi_square(cuda_ctx):
     keep = P * S > 5
     exp = P[keep] * S
     obs = counts[keep] * exp.sum() / counts[keep].sum()
-    assert chisquare(obs, exp).pvalue > 1e-3
+    assert chisquare(obs, exp).pvalue > 0.01
 
 
 def test_sampling_ragged_shots_and_untouched_tail(cuda_ctx):
@@ -380,7 +380,8 @@ def test_qaoa32_sampling_full_size_sampled(cuda_ctx):
         cv[k] = rng.randint(V)
     out = N().evaluate(ac, t(cv), t(ev)).cpu().numpy()
     for k in range(cols):
-        assert abs(out[k, 0] - ref.up(angs[cv[k]], ev[k]).real) < 1e-5
+        want = ref.up(angs[cv[k]], ev[k]).real  # ~2^-L: a relative bound (an absolute 1e-5 could not fail)
+        assert abs(out[k, 0] - want) <= 1e-5 * want
     # two-qubit marginal histograms of one vector
     v = 3
     for (a, bq) in [(0, 1), (5, 17), (30, 31)]:
@@ -395,7 +396,7 @@ def test_qaoa32_sampling_full_size_sampled(cuda_ctx):
         keep = exp * S > 5
         e = exp[keep] * S
         o = counts[keep] * e.sum() / counts[keep].sum()
-        assert chisquare(o, e).pvalue > 1e-4
+        assert chisquare(o, e).pvalue > 0.01
 
 
 def test_qaoa10_p2_amplitude_ac_full_batch(cuda_ctx):

@@ -218,7 +218,7 @@ def test_chain_rule_sampler_distribution():
     exp = P[keep] * shots
     obs = counts[keep].astype(float)
     obs = obs * exp.sum() / obs.sum()
-    assert chisquare(obs, exp).pvalue > 1e-3
+    assert chisquare(obs, exp).pvalue > 0.01
     # the decision rule itself: with a point mass every sample is that outcome
     Pm = np.zeros(16)
     Pm[0b1010] = 1.0

@@ -80,13 +80,13 @@ def test_trajectory_samples_follow_the_density_matrix():
     cnt = np.bincount(bits.astype(np.int64), minlength=P.size).astype(float)
     keep = P * S > 5
     e = P[keep] * S
-    assert chisquare(cnt[keep] * e.sum() / cnt[keep].sum(), e).pvalue > 1e-3
+    assert chisquare(cnt[keep] * e.sum() / cnt[keep].sum(), e).pvalue > 0.01
     # branch frequencies of every channel against its branch probabilities
     for i, op in enumerate(T.channels(c)):
         pr = np.array(T.branch_probabilities(op.kind, op.p))
         f = np.bincount([t[i] for t in trajs], minlength=len(pr)).astype(float)
         k2 = pr * S > 5
-        assert chisquare(f[k2] * (pr[k2] * S).sum() / f[k2].sum(), pr[k2] * S).pvalue > 1e-3
+        assert chisquare(f[k2] * (pr[k2] * S).sum() / f[k2].sum(), pr[k2] * S).pvalue > 0.01
 
 
 def test_trajectory_sampler_planted_mistake_is_caught():
