@@ -279,7 +279,8 @@ qkc_status qkc_gradient(qkc_ac *ac, const int32_t *col_vec_dev, const int8_t *ev
  * u < p_0 + ... + p_k (the branch probabilities stored in the AC), else the
  * last -- and is then sampled as above with its noise variables observed at r,
  * which draws P(x) = sum_r P(r) P(x | r) exactly.  Samples without any error
- * share the groups of their vector; every other sample has groups of its own.
+ * share the groups of their vector, and so do samples of one vector that drew
+ * the same error trajectory (found by hashing, then compared byte for byte).
  * bits_dev [n_vectors][max_shots] uint64: outcome index of each sample
  * (entries s >= shots[v] are left untouched).  shots_dev [n_vectors] int32.
  * total_shots: a host-side upper bound on sum_v min(shots[v], max_shots) used

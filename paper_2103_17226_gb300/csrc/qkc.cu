@@ -1499,12 +1499,56 @@ __global__ void traj_draw(int64_t n_vec, int64_t max_shots, const int32_t *shots
     err[t] = any;
 }
 
+// Samples of one vector that drew the same error trajectory share one group: every sample with an
+// error inserts (vector, trajectory) into an open-addressing table (one 64-bit word per slot: high
+// half of the key's hash, 1 + the first sample that claimed it); a sample whose trajectory equals a
+// claimed slot's byte for byte joins that sample.  rep[t] = the representative sample of t (t itself
+// when it claimed a slot, or when no slot was found within the probe limit: then it keeps its own
+// group, which is still exact).  Which equal sample represents a group may vary from run to run;
+// a group's values depend only on its vector, trajectory and prefix, so the samples do not.
+__global__ void traj_dedup(int64_t n_vec, int64_t max_shots, const int32_t *err, const int8_t *traj, int n_noise,
+                           unsigned long long *table, uint64_t tmask, int32_t *rep) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n_vec * max_shots) return;
+    rep[t] = (int32_t)t;
+    if (!err[t]) return;
+    const int64_t v = t / max_shots;
+    const int8_t *r = traj + t * n_noise;
+    uint64_t h = 0x9E3779B97F4A7C15ull * (uint64_t)(v + 1);
+    for (int i = 0; i < n_noise; ++i) {
+        h ^= (uint64_t)(uint8_t)r[i] + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+        h *= 0xBF58476D1CE4E5B9ull;
+    }
+    h ^= h >> 31;
+    const unsigned long long mine = ((unsigned long long)(h >> 32) << 32) | (unsigned long long)(t + 1);
+    uint64_t slot = h & tmask;
+    for (int probe = 0; probe < 4096; ++probe, slot = (slot + 1) & tmask) {
+        const unsigned long long cur = atomicCAS(table + slot, 0ull, mine);
+        if (cur == 0ull) return;  // claimed: t represents its (vector, trajectory)
+        if ((cur >> 32) != (h >> 32)) continue;
+        const int64_t o = (int64_t)(cur & 0xffffffffull) - 1;
+        if (o / max_shots != v) continue;
+        const int8_t *ro = traj + o * n_noise;
+        bool same = true;
+        for (int i = 0; i < n_noise && same; ++i) same = ro[i] == r[i];
+        if (same) {
+            rep[t] = (int32_t)o;
+            return;
+        }
+    }
+}
+__global__ void traj_rep_flags(int64_t n, const int32_t *err, const int32_t *rep, int32_t *flag) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n) flag[t] = (err[t] && rep[t] == (int32_t)t) ? 1 : 0;
+}
+
 // The first groups of a trajectory sampling call: group v holds vector v's samples whose trajectory
-// has no error (all share the branches 0), and every sample with an error gets a group of its own
-// (n_vec + its rank among them), carrying its trajectory.
+// has no error (all share the branches 0); the samples with one error trajectory (equal samples of a
+// vector) share a group, n_vec + the rank of their representative, carrying that trajectory.
 __global__ void traj_groups(int64_t n_vec, int64_t max_shots, const int32_t *shots, const int32_t *err,
-                            const int32_t *pos, const int32_t *bsum, int32_t *s_group, uint64_t *s_bits,
-                            int32_t *g_vec, uint64_t *g_prefix, int32_t *g_traj, int32_t *g_count) {
+                            const int32_t *rep, const int32_t *flag, const int32_t *pos, const int32_t *bsum,
+                            int32_t *s_group, uint64_t *s_bits, int32_t *g_vec, uint64_t *g_prefix, int32_t *g_traj,
+                            int32_t *g_count) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t n = n_vec * max_shots;
     if (t < n_vec) {
@@ -1512,7 +1556,7 @@ __global__ void traj_groups(int64_t n_vec, int64_t max_shots, const int32_t *sho
         g_prefix[t] = 0;
         g_traj[t] = -1;
     }
-    if (t == n - 1) *g_count = (int32_t)n_vec + pos[t] + bsum[t >> 10] + err[t];
+    if (t == n - 1) *g_count = (int32_t)n_vec + pos[t] + bsum[t >> 10] + flag[t];
     if (t >= n) return;
     const int64_t v = t / max_shots, s = t % max_shots;
     if (s >= shots[v]) return;
@@ -1521,11 +1565,14 @@ __global__ void traj_groups(int64_t n_vec, int64_t max_shots, const int32_t *sho
         s_group[t] = (int32_t)v;
         return;
     }
-    const int32_t g = (int32_t)n_vec + pos[t] + bsum[t >> 10];
+    const int32_t o = rep[t];
+    const int32_t g = (int32_t)n_vec + pos[o] + bsum[o >> 10];
     s_group[t] = g;
-    g_vec[g] = (int32_t)v;
-    g_prefix[g] = 0;
-    g_traj[g] = (int32_t)t;
+    if (o == (int32_t)t) {
+        g_vec[g] = (int32_t)v;
+        g_prefix[g] = 0;
+        g_traj[g] = (int32_t)t;
+    }
 }
 __global__ void set_count(int32_t *dst, int32_t v) { *dst = v; }
 
@@ -1716,6 +1763,9 @@ struct qkc_ac {
     int32_t *d_noise_off = nullptr; // [n_noise + 1] first value of each noise variable in d_cdf
     int8_t *d_traj = nullptr;       // [samples][n_noise] branch of every noise variable
     int32_t *d_err = nullptr;       // [samples] the sample's trajectory has a branch other than 0
+    int32_t *d_rep = nullptr;       // [samples] the sample representing its (vector, trajectory)
+    unsigned long long *d_table = nullptr;  // [table_size] dedup table of error trajectories
+    uint64_t table_size = 0;
     int32_t *d_g_traj[2] = {nullptr, nullptr};       // per group: sample whose trajectory it carries, -1: none
     int64_t traj_cap = 0;
     double2 *d_root = nullptr;  // [root_cap]
@@ -1865,8 +1915,8 @@ static void free_scratch(qkc_ac *a) {
         cudaFree(a->d_g_vec[i]); cudaFree(a->d_g_prefix[i]); cudaFree(a->d_g_P[i]); cudaFree(a->d_g_traj[i]);
         a->d_g_vec[i] = nullptr; a->d_g_prefix[i] = nullptr; a->d_g_P[i] = nullptr; a->d_g_traj[i] = nullptr;
     }
-    cudaFree(a->d_traj); cudaFree(a->d_err);
-    a->d_traj = nullptr; a->d_err = nullptr;
+    cudaFree(a->d_traj); cudaFree(a->d_err); cudaFree(a->d_rep); cudaFree(a->d_table);
+    a->d_traj = nullptr; a->d_err = a->d_rep = nullptr; a->d_table = nullptr; a->table_size = 0;
     a->vec_cap = a->tile = a->root_cap = a->samp_cap = a->grp_cap = a->traj_cap = 0;
 }
 
@@ -2697,10 +2747,17 @@ static qkc_status ensure_sampling(qkc_ac *a, int64_t n_samples, int64_t n_groups
         }
         cudaFree(a->d_traj);
         cudaFree(a->d_err);
+        cudaFree(a->d_rep);
+        cudaFree(a->d_table);
         a->d_traj = nullptr;
-        a->d_err = nullptr;
+        a->d_err = a->d_rep = nullptr;
+        a->d_table = nullptr;
+        a->table_size = 1;
+        while (a->table_size < 2 * (uint64_t)ns) a->table_size <<= 1;
         QKC_CUDA(dalloc(&a->d_traj, (size_t)ns * (size_t)std::max(1, a->n_noise)));
         QKC_CUDA(dalloc(&a->d_err, ns));
+        QKC_CUDA(dalloc(&a->d_rep, ns));
+        QKC_CUDA(dalloc(&a->d_table, a->table_size));
     }
     a->samp_cap = ns;
     a->grp_cap = ng;
@@ -3241,14 +3298,18 @@ static qkc_status sample_impl(qkc_ac *a, const uint64_t *seeds, const int32_t *s
         // one per sample with an error (rank by an exclusive scan of the error flags)
         traj_draw<<<gs, TPB, 0, s>>>(n_vec, max_shots, shots, seeds, a->n_noise, a->d_noise_off, a->d_cdf,
                                      a->d_traj, a->d_err);
+        QKC_CUDA(cudaMemsetAsync(a->d_table, 0, sizeof(unsigned long long) * a->table_size, s));
+        traj_dedup<<<gs, TPB, 0, s>>>(n_vec, max_shots, a->d_err, a->d_traj, a->n_noise, a->d_table,
+                                      a->table_size - 1, a->d_rep);
+        traj_rep_flags<<<gs, TPB, 0, s>>>(n_samp, a->d_err, a->d_rep, a->d_flag);
         set_count<<<1, 1, 0, s>>>(a->d_gcount + 1, (int32_t)n_samp);
         const int64_t nb = (n_samp + 1023) / 1024;
-        scan_block<<<(unsigned)nb, 1024, 0, s>>>(a->d_err, a->d_gcount + 1, 1, a->d_pos, a->d_bsum);
+        scan_block<<<(unsigned)nb, 1024, 0, s>>>(a->d_flag, a->d_gcount + 1, 1, a->d_pos, a->d_bsum);
         scan_sums<<<1, 1024, 0, s>>>(a->d_bsum, nb);
         traj_groups<<<std::max(gs, (unsigned)((n_vec + TPB - 1) / TPB)), TPB, 0, s>>>(
-            n_vec, max_shots, shots, a->d_err, a->d_pos, a->d_bsum, a->d_s_group, a->d_s_bits, a->d_g_vec[0],
-            a->d_g_prefix[0], a->d_g_traj[0], a->d_gcount);
-        a->launches += 5;
+            n_vec, max_shots, shots, a->d_err, a->d_rep, a->d_flag, a->d_pos, a->d_bsum, a->d_s_group, a->d_s_bits,
+            a->d_g_vec[0], a->d_g_prefix[0], a->d_g_traj[0], a->d_gcount);
+        a->launches += 7;
     } else {
         sample_init<<<std::max(gs, (unsigned)((n_vec + TPB - 1) / TPB)), TPB, 0, s>>>(
             n_vec, max_shots, shots, a->d_s_group, a->d_s_bits, a->d_g_vec[0], a->d_g_prefix[0], a->d_gcount);
