@@ -712,3 +712,32 @@ def test_qaoa40_sampling_wide_prefixes(cuda_ctx, prec):
         margins = mismatch_margins(pref, int(seeds_h[v]), outs["memo"][v, :k].astype(np.uint64), want, n)
         assert all(m <= TIE[prec] for m in margins), margins
         assert len(margins) <= (0 if prec == 64 else 1)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("kind", [1, 2])
+def test_sample_probs_are_outcome_probabilities(cuda_ctx, prec, kind):
+    """qkc_sample_probs: each sample's probability as the sampler computed it is P(x) of its outcome
+    (density AC and light-cone step AC), against the density matrix: FP64 within 1e-12, FP32 within
+    1e-5 of the last step's prefix probability; the indices equal qkc_sample's."""
+    c = I.workload("qaoa4_ring_p1")
+    V, S = 6, 500
+    angs = I.uniform_angles(V, c.n_angles, seed=21)
+    seeds = t(I.vector_seeds(V, 21).astype(np.int64))
+    shots = t(np.array([S, 1, 77, S, 250, 3], dtype=np.int32))
+    ac = N().load_ac(cuda_ctx, compiled("qaoa4_ring_p1", kind), precision=prec)
+    N().set_params(ac, t(angs))
+    bits, probs = N().sample_probs(ac, seeds, shots, S)
+    bits2 = N().sample(ac, seeds, shots, S)
+    bits, probs, bits2 = bits.cpu().numpy(), probs.cpu().numpy(), bits2.cpu().numpy()
+    sh = shots.cpu().numpy()
+    for v in range(V):
+        P = Q.probabilities(c, angs[v])
+        Pt = P.reshape((2,) * 4)
+        x = bits[v, :sh[v]]
+        assert np.array_equal(x, bits2[v, :sh[v]])
+        want = P[x]
+        pre = np.array([Pt[tuple((int(xx) >> (3 - k)) & 1 for k in range(3))].sum() for xx in x])
+        bound = 1e-12 if prec == 64 else 1e-5 * pre
+        assert (np.abs(probs[v, :sh[v]] - want) <= bound).all(), v
+        assert (probs[v, sh[v]:] == 0).all()  # entries past the shots are left untouched
