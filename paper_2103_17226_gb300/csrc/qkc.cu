@@ -275,10 +275,12 @@ __global__ void level_scale_kernel(DevAC ac, int L, int64_t pitch, int floor_zer
     obs[(int64_t)L * pitch + c] = OBS_EMPTY;
 }
 
-// Every level's observed exponent back to empty (a memoised pass computes only some levels).
-__global__ void obs_reset(int *obs, int64_t n) {
+// The observed exponents of the listed levels back to empty: a memoised pass computes only its
+// tier-B levels, and the level scales read the observed exponents of those levels and their child
+// levels alone.
+__global__ void obs_reset(int *obs, const int32_t *levels, int nlev, int64_t pitch) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) obs[i] = OBS_EMPTY;
+    if (i < (int64_t)nlev * pitch) obs[(int64_t)levels[i / pitch] * pitch + i % pitch] = OBS_EMPTY;
 }
 
 // ------------------------------------------------------------------ upward pass, one level
@@ -1186,18 +1188,20 @@ __global__ void __launch_bounds__(TPB, 3) memoB_level_f32(DevAC ac, LevelArgs a,
     }
 }
 
-// A run of consecutive small tier-B levels in one launch: a warp per 128-column chunk walks the levels
-// in order, every node of each level for its own columns.  A level reads only lower levels of the
-// same columns, and each lane reads back only what it wrote itself (tile rows, scale words, observed
-// exponents of its four columns), so no barrier is needed -- and a step whose tier B is a chain of
-// small levels costs one launch instead of one per level (and no scale launches).
+// A run of consecutive small tier-B levels in one launch: a warp per 32-column chunk (one column per
+// lane) walks the levels in order, every node of each level for its own columns.  A level reads only
+// lower levels of the same columns, and each lane reads back only what it wrote itself (tile rows,
+// scale words, observed exponents of its column), so no barrier is needed -- and a step whose tier B
+// is a chain of small levels costs one launch instead of one per level (and no scale launches).  One
+// column per lane gives four times the warps of the per-level kernel's items: these levels are too
+// small to fill the GPU otherwise, and each level waits on the one below it.
 struct MemoBRunLevel {
     uint32_t b0, count;  // first tier-B row of the level within the step, its tier-B nodes
     int32_t L, floor0;   // level, whether it reads unscaled tier-A values
 };
-__global__ void __launch_bounds__(TPB, 2) memoB_run_f32(DevAC ac, const MemoBRunLevel *lv, int nlv,
-                                                      const uint2 *bdesc, const PassDesc *pd, const MemoDesc *mdp,
-                                                      int64_t pitch, float2 *__restrict__ V, int *__restrict__ S,
+__global__ void __launch_bounds__(TPB) memoB_run_f32(DevAC ac, const MemoBRunLevel *lv, int nlv, const uint2 *bdesc,
+                                                      const PassDesc *pd, const MemoDesc *mdp, int64_t pitch,
+                                                      float2 *__restrict__ V, int *__restrict__ S,
                                                       int *__restrict__ obs) {
     __shared__ uint2 sdesc[TPB / 32][NBB];
     __shared__ uint4 srec[TPB / 32][NBB][2];
@@ -1208,31 +1212,81 @@ __global__ void __launch_bounds__(TPB, 2) memoB_run_f32(DevAC ac, const MemoBRun
     const int32_t *col_vec = pd->es.col_vec;
     const int64_t n_vec = pd->es.n_vec;
     const uint32_t *keys = mdp->keys;
-    BView w;
-    bview_init(w, pd, mdp, pitch);
+    const float2 *VA = static_cast<const float2 *>(mdp->VA);
+    const KeyPlan *kplan = mdp->kplan;
+    const uint64_t *prefix = pd->es.prefix;
+    const int64_t kpitch = mdp->kpitch, Vn = mdp->V;
+    const int j = mdp->j;
+    const bool narrow = j <= 32;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    float4 *V4 = reinterpret_cast<float4 *>(V);
-    const int64_t nchunks = (ncols + 127) >> 7;
+    const int64_t nchunks = (ncols + 31) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t chunk = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; chunk < nchunks; chunk += nw) {
-        const int64_t col = chunk * 128 + lane * 4;
+        const int64_t col = chunk * 32 + lane;
         const bool active = col < ncols;
-        if (active) bview_cols(w, col, ncols, col0, col_vec, n_vec, V4, S, keys);
+        const int64_t g = col0 + (active ? col : 0);
+        int64_t vv = col_vec ? (int64_t)col_vec[g] : g;
+        vv = vv < 0 ? 0 : (vv >= n_vec ? n_vec - 1 : vv);
+        const uint64_t vec = (uint64_t)vv;
+        // one child's value and scale exponent in this column (tier A: unscaled, exponent 0)
+        auto child = [&](const uint4 r, float2 &v, int &e) {
+            if (r.x & 0x80000000u) {
+                v = V[(int64_t)(r.x & 0x7fffffffu) * pitch + col];
+                e = S[(int64_t)r.y * pitch + col];
+            } else {
+                const int mid = (int)(r.y >> 8) - 1;
+                uint32_t key;
+                if (mid >= 0) {
+                    key = keys[(int64_t)mid * kpitch + col];
+                } else {
+                    const uint64_t pre = j ? __brevll(prefix[g] << (64 - j)) : 0ull;
+                    key = plan_key(kplan + (r.x - 1u), pre, narrow);
+                }
+                v = VA[Vn * (int64_t)(((uint64_t)r.w << 32) | r.z) + (int64_t)((vec << (r.y & 0xffu)) | key)];
+                e = 0;
+            }
+        };
         for (int l = 0; l < nlv; ++l) {
             const MemoBRunLevel L = lv[l];
-            int sl[4] = {0, 0, 0, 0};
-            float mx[4] = {0.f, 0.f, 0.f, 0.f};
+            int sl = 0;
             if (active) {
-                blevel_scale(ac, L.L, pitch, true, L.floor0, S, obs, col, w.nv, sl);
-                bstore_scale(S, L.L, pitch, col, w.nv, sl);
+                sl = level_scale_col(ac, L.L, pitch, L.floor0, S, obs, col);
+                S[(int64_t)L.L * pitch + col] = sl;
             }
+            float mx = 0.f;
             for (uint32_t kb = 0; kb < L.count; kb += NBB) {
                 const int nn = (int)min((uint32_t)NBB, L.count - kb);
                 bstage(sdesc[wp], srec[wp], bdesc + L.b0 + kb, brec, nn, lane);
-                if (active)
-                    bnodes<false>(sdesc[wp], srec[wp], nn, sl, V4 + (int64_t)(L.b0 + kb) * w.hp + (col >> 1), w, brec, mx);
+                if (!active) continue;
+                for (int i = 0; i < nn; ++i) {
+                    const uint2 dsc = sdesc[wp][i];
+                    const uint32_t deg = dsc.y & 0xffffffu, o = dsc.y >> 24;
+                    float2 x, y, q;
+                    int ex, ey;
+                    child(srec[wp][i][0], x, ex);
+                    if (deg >= 2u) child(srec[wp][i][1], y, ey);
+                    if (o == OP_MUL) {
+                        q = cscale(cmul(x, y), pow2f(ex + ey - sl));
+                    } else {
+                        const float f0 = pow2f(ex - sl);
+                        q = make_float2(x.x * f0, x.y * f0);
+                        if (deg >= 2u) {
+                            const float f1 = pow2f(ey - sl);
+                            q.x += y.x * f1; q.y += y.y * f1;
+                        }
+                        for (uint32_t e = 2; e < deg; ++e) {  // children beyond the second
+                            float2 z;
+                            int ez;
+                            child(__ldg(brec + dsc.x + e), z, ez);
+                            const float fz = pow2f(ez - sl);
+                            q.x += z.x * fz; q.y += z.y * fz;
+                        }
+                    }
+                    V[(int64_t)(L.b0 + kb + i) * pitch + col] = q;
+                    mx = fmaxf(mx, fmaxf(fabsf(q.x), fabsf(q.y)));
+                }
             }
-            if (active) bobserve(obs, L.L, pitch, col, w.nv, mx);
+            if (active) atomicMax(obs + (int64_t)L.L * pitch + col, (__float_as_int(mx) >> 23) - 127);
         }
     }
 }
@@ -1783,6 +1837,8 @@ struct qkc_ac {
     std::vector<uint64_t> sigma;
     std::vector<uint32_t> var_card;               // cardinality of every indicator variable
     std::vector<uint32_t> h_child_off, h_child;  // host copy of the structure (density ACs)
+    std::vector<uint32_t> h_cl_off;              // child-level lists per level (host copy)
+    std::vector<uint16_t> h_cl;
     std::vector<uint8_t> h_op;  // node ops (host copy, memoised-pass metadata)
     std::vector<int32_t> h_param_angle;  // angle slot of every parameter leaf
     // incremental re-evaluation: the dirty cone of every angle slot (built on first use), and
@@ -1817,6 +1873,8 @@ struct qkc_ac {
         std::vector<std::vector<AItem>> a_items;        // per step, in level order
         MemoARunLevel *d_runlv = nullptr;               // the runs' levels, all steps
         std::vector<std::vector<AItem>> b_items;        // per step: tier-B launches (a level, or a run of cnt levels)
+        std::vector<int64_t> rst_base, rst_cnt;         // per step: levels whose observed exponents are reset
+        int32_t *d_rst = nullptr;
         MemoBRunLevel *d_brunlv = nullptr;              // the tier-B runs' levels, all steps
         std::vector<std::vector<uint8_t>> floor0;               // per step, [D]
         std::vector<int64_t> a_base, b_base, offu_base, g_base;  // per step
@@ -1944,7 +2002,7 @@ extern "C" void qkc_free_ac(qkc_ac *a) {
     for (auto *m : a->memo) {
         if (!m) continue;
         cudaFree(m->d_a_nodes); cudaFree(m->d_a_grp); cudaFree(m->d_offu);
-        cudaFree(m->d_emask); cudaFree(m->d_runlv); cudaFree(m->d_brunlv); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
+        cudaFree(m->d_emask); cudaFree(m->d_runlv); cudaFree(m->d_brunlv); cudaFree(m->d_rst); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
         for (auto &g : m->gA) if (g.exec) cudaGraphExecDestroy(g.exec);
         for (auto &g : m->gB) if (g.exec) cudaGraphExecDestroy(g.exec);
         delete m;
@@ -2180,6 +2238,8 @@ extern "C" qkc_status qkc_load_ac(qkc_ctx *ctx, const uint8_t *bytes, uint64_t l
         qkc_free_ac(a);
         return st;
     }
+    a->h_cl_off = cloff;    // child-level lists per level (the memoised passes' resets)
+    a->h_cl = cl;
     a->h_child_off = coff;  // host copy of the structure (memoised passes, dirty cones)
     a->h_child = child;
     a->h_op = op;
@@ -2806,6 +2866,7 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
     m->a_items.assign(nq, {});
     m->b_items.assign(nq, {});
     std::vector<MemoBRunLevel> brunlv;
+    std::vector<int32_t> rst;
     std::vector<int32_t> plan_of;  // per node: its key plan in this step, -1 if none yet
     std::vector<int64_t> row_of;   // per node: its tier-B row in this step
     std::vector<char> reach;       // per node: reachable from this step's root
@@ -2954,7 +3015,7 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
             m->t_lvl[j][L] = th;
         }
         m->bp_cnt.push_back((int64_t)bplan.size() - m->bp_base[j]);
-        {  // tier-B launches: consecutive small levels form one run (FP32: a warp per column chunk walks them)
+        {  // tier-B launches: consecutive small levels form one run (FP32: a warp per 32-column chunk walks them)
             std::vector<uint32_t> pend;
             auto flush = [&]() {
                 if (pend.size() >= 2) {
@@ -3005,6 +3066,18 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
             }
             flush();
         }
+        {  // levels whose observed exponents this step's tier-B pass writes or reads
+            std::vector<char> need(D, 0);
+            for (uint32_t L = 1; L < D; ++L) {
+                if (m->b_lvl[j][L + 1] == m->b_lvl[j][L]) continue;
+                need[L] = 1;
+                for (uint32_t k = a->h_cl_off[L]; k < a->h_cl_off[L + 1]; ++k) need[a->h_cl[k]] = 1;
+            }
+            m->rst_base.push_back((int64_t)rst.size());
+            for (uint32_t L = 0; L < D; ++L)
+                if (need[L]) rst.push_back((int32_t)L);
+            m->rst_cnt.push_back((int64_t)rst.size() - m->rst_base[j]);
+        }
         m->root_row.push_back(row_of[a->roots[j]]);
         m->max_rows = std::max<int64_t>(m->max_rows, (int64_t)bn.size() - m->b_base[j]);
         m->a_bytes_slot.push_back(abytes * (double)a->elem());
@@ -3025,13 +3098,14 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
         (*st = upload(&m->d_emask, emask.data(), emask.size(), dummy)) ||
         (*st = upload(&m->d_runlv, runlv.data(), runlv.size(), dummy)) ||
         (*st = upload(&m->d_brunlv, brunlv.data(), brunlv.size(), dummy)) ||
+        (*st = upload(&m->d_rst, rst.data(), rst.size(), dummy)) ||
         (*st = upload(&m->d_bdesc, bdesc.data(), bdesc.size(), dummy)) ||
         (*st = upload(&m->d_brec, brec.data(), brec.size(), dummy)) ||
         (*st = upload(&m->d_kplan, kplan.data(), kplan.size(), dummy)) ||
         (*st = upload(&m->d_aplan, aplan.data(), aplan.size(), dummy)) ||
         (*st = upload(&m->d_bplan, bplan.data(), bplan.size(), dummy))) {
         cudaFree(m->d_a_nodes); cudaFree(m->d_a_grp); cudaFree(m->d_offu);
-        cudaFree(m->d_emask); cudaFree(m->d_runlv); cudaFree(m->d_brunlv); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
+        cudaFree(m->d_emask); cudaFree(m->d_runlv); cudaFree(m->d_brunlv); cudaFree(m->d_rst); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
         delete m;
         return nullptr;
     }
@@ -3081,14 +3155,15 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
         if (m->bp_cnt[j] > 0) memo_keys<<<gs, TPB, 0, s>>>(a->d_desc, a->d_mdesc);
         // FP32 scales: only levels with tier-B nodes are computed, so every level's observed
         // exponent starts empty and the scale kernel runs for those levels alone
-        if (a->prec == 32)
-            obs_reset<<<(unsigned)(((int64_t)D * pitch + TPB - 1) / TPB), TPB, 0, s>>>(a->d_obs, (int64_t)D * pitch);
+        if (a->prec == 32 && m->rst_cnt[j] > 0)
+            obs_reset<<<(unsigned)((m->rst_cnt[j] * pitch + TPB - 1) / TPB), TPB, 0, s>>>(
+                a->d_obs, m->d_rst + m->rst_base[j], (int)m->rst_cnt[j], pitch);
         const bool inline_scale = m->b_lvl[j][D] <= MEMO_INLINE_SCALE_B;
         const uint2 *bd_j = m->d_bdesc + m->b_base[j];
         for (const auto &it : m->b_items[j]) {
-            if (it.cnt > 0) {  // a run of small levels (FP32): a warp per 128-column chunk walks them
-                const int64_t chunks = (pitch + 127) / 128;  // a warp per chunk
-                const unsigned g = (unsigned)std::min<int64_t>((chunks + TPB / 32 - 1) / (TPB / 32), (int64_t)sms * 2);
+            if (it.cnt > 0) {  // a run of small levels (FP32): a warp per 32-column chunk walks them
+                const int64_t chunks = (pitch + 31) / 32;  // a warp per 32-column chunk
+                const unsigned g = (unsigned)std::min<int64_t>((chunks + TPB / 32 - 1) / (TPB / 32), (int64_t)sms * 8);
                 memoB_run_f32<<<g, TPB, 0, s>>>(d, m->d_brunlv + it.off, it.cnt, bd_j, a->d_desc, a->d_mdesc, pitch,
                                                  (float2 *)a->d_V, a->d_S, a->d_obs);
                 continue;
@@ -3117,7 +3192,7 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
 static int64_t memoB_launches(const qkc_ac *a, const qkc_ac::MemoMeta *m, int j) {
     int64_t n = 1;
     if (m->b_lvl[j][a->D] > 0) {
-        n += a->prec == 32 ? 1 : 0;
+        n += (a->prec == 32 && m->rst_cnt[j] > 0) ? 1 : 0;
         n += m->bp_cnt[j] > 0;
         const int per = (a->prec == 32 && m->b_lvl[j][a->D] > MEMO_INLINE_SCALE_B) ? 2 : 1;
         for (const auto &it : m->b_items[j]) n += it.cnt > 0 ? 1 : per;
