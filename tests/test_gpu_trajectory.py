@@ -147,3 +147,34 @@ def test_trajectory_full_batch_sampled(cuda_ctx, cfg2):
         want = T.trajectory_samples(W["c"], W["angs"][v], int(W["seeds"][v]), 100)
         m = _margins(W["c"], W["angs"][v], int(W["seeds"][v]), bits[v, :100].astype(np.uint64), want)
         assert all(x <= TIE[32] for x in m) and len(m) <= 1, m
+
+
+def test_trajectory_edge_cases(cuda_ctx):
+    """A circuit without channels compiled as a TRAJECTORY AC has no noise variables: every sample is
+    error-free, and its samples equal the density AC's bit for bit (FP64, same uniforms).  Ragged shot
+    counts leave the tail untouched; an understated shot total is reported, never read out of range."""
+    c0 = I.qaoa_maxcut(6, I.random_regular_graph(6, 3, seed=6), 2, None)
+    V = 4
+    angs = I.uniform_angles(V, c0.n_angles, seed=8)
+    seeds = t(I.vector_seeds(V, 8).astype(np.int64))
+    shots = t(np.array([300, 0, 17, 300], dtype=np.int32))
+    outs = []
+    for kind in (N().QKC_AC_DENSITY, N().QKC_AC_TRAJECTORY):
+        ac = N().load_ac(cuda_ctx, N().compile(c0, kind), precision=64)
+        assert ac.n_vars == 6
+        N().set_params(ac, t(angs))
+        out = torch.full((V, 300), -7, dtype=torch.int64, device="cuda")
+        N().sample(ac, seeds, shots, 300, out=out)
+        N().check_status(ac)
+        outs.append(out.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    assert (outs[1][1] == -7).all() and (outs[1][2, 17:] == -7).all()
+    # noisy: an understated total is caught by the status check
+    c = I.qaoa_maxcut(6, I.random_regular_graph(6, 3, seed=6), 1, I.NOISE_CFG2)
+    ac = N().load_ac(cuda_ctx, N().compile(c, N().QKC_AC_TRAJECTORY), precision=32)
+    N().set_params(ac, t(I.uniform_angles(V, c.n_angles, seed=8)))
+    N().sample(ac, seeds, shots, 300, total_shots=int(shots.sum().item()))
+    N().check_status(ac)
+    N().sample(ac, seeds, shots, 300, total_shots=50)
+    with pytest.raises(N().QKCError):
+        N().check_status(ac)
