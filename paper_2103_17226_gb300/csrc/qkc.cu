@@ -256,14 +256,16 @@ __global__ void bind_leaves_f64(DevAC ac, const PassDesc *pd, int64_t pitch, dou
 }
 
 // ------------------------------------------------------------------ per-level scale (FP32)
-// S[L][c] = max over the child levels L' of level L of S[L'][c] + obs[L'][c];
-// obs[L][c] reset.  Order-independent, so deterministic and per column.
-__global__ void level_scale_kernel(DevAC ac, int L, int64_t pitch, int floor_zero, int *S, int *obs) {
+// S[L][c] = max over the child levels L' of level L (the lists cl_off/cl: every child level in a
+// full pass, those holding tier-B nodes in a memoised one) of S[L'][c] + obs[L'][c]; obs[L][c]
+// reset.  Order-independent, so deterministic and per column.
+__global__ void level_scale_kernel(const uint32_t *cl_off, const uint16_t *cl, int L, int64_t pitch, int floor_zero,
+                                   int *S, int *obs) {
     int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= pitch) return;
     int s = INT_MIN;
-    for (uint32_t k = ac.cl_off[L]; k < ac.cl_off[L + 1]; ++k) {
-        int Lp = ac.cl[k];
+    for (uint32_t k = cl_off[L]; k < cl_off[L + 1]; ++k) {
+        int Lp = cl[k];
         int o = obs[(int64_t)Lp * pitch + c];
         if (o == OBS_EMPTY) continue;  // no value of that level in this column (its scale is unused)
         int cand = S[(int64_t)Lp * pitch + c] + o;
@@ -704,6 +706,8 @@ struct MemoDesc {
     int32_t nbm;
     uint32_t *keys;        // ... and their keys per group column of the tile: keys[row * kpitch + column]
     int64_t kpitch;
+    const uint32_t *bcl_off;  // per level: its child levels that hold tier-B nodes in this step,
+    const uint16_t *bcl;      // bcl[bcl_off[L] .. bcl_off[L + 1]) (the level scales read those alone)
 };
 
 __device__ __forceinline__ uint32_t plan_key(const KeyPlan *kp, uint64_t x, bool narrow) {
@@ -916,12 +920,14 @@ __global__ void memo_keys(const PassDesc *pd, const MemoDesc *mdp) {
 
 // One level of tier B (FP32): as up_level_f32 over a node list, tier-A children read by key.
 // The level's scale exponent in one column, from its child levels' scales and observed exponents
-// (the rule of level_scale_kernel: child levels with no value in the column are skipped).
-__device__ __forceinline__ int level_scale_col(const DevAC &ac, int L, int64_t pitch, int floor_zero, const int *S,
-                                               const int *obs, int64_t c) {
+// (the rule of level_scale_kernel: child levels with no value in the column are skipped).  A memoised
+// pass lists, per level, only the child levels that hold tier-B nodes in its step: the others are not
+// computed there, so they have no value in any column.
+__device__ __forceinline__ int level_scale_col(const uint32_t *cl_off, const uint16_t *cl, int L, int64_t pitch,
+                                               int floor_zero, const int *S, const int *obs, int64_t c) {
     int s = INT_MIN;
-    for (uint32_t k = ac.cl_off[L]; k < ac.cl_off[L + 1]; ++k) {
-        const int Lp = ac.cl[k];
+    for (uint32_t k = __ldg(cl_off + L), k1 = __ldg(cl_off + L + 1); k < k1; ++k) {
+        const int Lp = __ldg(cl + k);
         const int o = obs[(int64_t)Lp * pitch + c];
         if (o == OBS_EMPTY) continue;
         s = max(s, S[(int64_t)Lp * pitch + c] + o);
@@ -1107,11 +1113,12 @@ __device__ __forceinline__ void bnodes(const uint2 *sd, const uint4 (*sr)[2], in
 }
 // The level's scale exponent for the lane's columns: formed from its child levels (floor: the level
 // reads unscaled tier-A values) or read from S.
-__device__ __forceinline__ void blevel_scale(const DevAC &ac, int L, int64_t pitch, bool inline_scale, int floor_zero,
+__device__ __forceinline__ void blevel_scale(const MemoDesc *mdp, int L, int64_t pitch, bool inline_scale, int floor_zero,
                                              const int *S, const int *obs, int64_t col, int nv, int sl[4]) {
     if (inline_scale) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) sl[i] = i < nv ? level_scale_col(ac, L, pitch, floor_zero, S, obs, col + i) : 0;
+        for (int i = 0; i < 4; ++i)
+            sl[i] = i < nv ? level_scale_col(mdp->bcl_off, mdp->bcl, L, pitch, floor_zero, S, obs, col + i) : 0;
     } else {
         const int4 t4 = *reinterpret_cast<const int4 *>(S + (int64_t)L * pitch + col);
         sl[0] = t4.x; sl[1] = t4.y; sl[2] = t4.z; sl[3] = t4.w;
@@ -1180,7 +1187,7 @@ __global__ void __launch_bounds__(TPB, 3) memoB_level_f32(DevAC ac, LevelArgs a,
         if (col >= ncols) continue;
         bview_cols(w, col, ncols, col0, col_vec, n_vec, V4, S, keys);
         int sl[4];
-        blevel_scale(ac, a.L, a.pitch, (a.hi & 2u) != 0, (int)(a.hi & 1u), S, obs, col, w.nv, sl);
+        blevel_scale(mdp, a.L, a.pitch, (a.hi & 2u) != 0, (int)(a.hi & 1u), S, obs, col, w.nv, sl);
         if ((a.hi & 2u) && blk_i == 0) bstore_scale(S, a.L, a.pitch, col, w.nv, sl);
         float mx[4] = {0.f, 0.f, 0.f, 0.f};
         bnodes(sdesc[wp], srec[wp], nn, sl, V4 + (int64_t)(a.lo + kb) * w.hp + (col >> 1), w, brec, mx);
@@ -1188,18 +1195,101 @@ __global__ void __launch_bounds__(TPB, 3) memoB_level_f32(DevAC ac, LevelArgs a,
     }
 }
 
-// A run of consecutive small tier-B levels in one launch: a warp per 32-column chunk (one column per
+// A run of consecutive small tier-B levels in one launch: a warp per 64-column chunk (two columns per
 // lane) walks the levels in order, every node of each level for its own columns.  A level reads only
 // lower levels of the same columns, and each lane reads back only what it wrote itself (tile rows,
-// scale words, observed exponents of its column), so no barrier is needed -- and a step whose tier B
-// is a chain of small levels costs one launch instead of one per level (and no scale launches).  One
-// column per lane gives four times the warps of the per-level kernel's items: these levels are too
-// small to fill the GPU otherwise, and each level waits on the one below it.
+// scale words, observed exponents of its columns), so no barrier is needed -- and a step whose tier B
+// is a chain of small levels costs one launch instead of one per level (and no scale launches).  The
+// nodes of a level are taken two at a time: the loads of both nodes' children are issued before
+// either is combined, so a lane has four child rows in flight.  The arithmetic (and its order) is
+// that of up_level_f32.  Each lane owns its columns, so the levels' observed exponents are stored,
+// not reduced.
 struct MemoBRunLevel {
     uint32_t b0, count;  // first tier-B row of the level within the step, its tier-B nodes
     int32_t L, floor0;   // level, whether it reads unscaled tier-A values
 };
-__global__ void __launch_bounds__(TPB) memoB_run_f32(DevAC ac, const MemoBRunLevel *lv, int nlv, const uint2 *bdesc,
+// A run lane's view: its two columns.
+struct RView {
+    float4 *V4c;           // the lane's columns in row 0 of the value tile
+    const int *Sc;         // ... in level 0 of the scale words
+    const uint32_t *Kc;    // ... in row 0 of the group-key table
+    const float2 *VA;      // tier-A slots
+    const KeyPlan *kplan;  // key plans (untabled supports)
+    const uint64_t *pre;   // the group prefixes, at the lane's first column
+    uint32_t hp, pitch, kpitch, Vn;
+    uint32_t vec0, vec1;   // the columns' vectors
+    int j;
+    bool narrow, two;      // two: the second column is inside the tile
+};
+// One child of a run-level node for the lane's two columns (the edge record as for BChild).
+struct RChild {
+    float4 v;  // (re, im) of column 0, then of column 1
+    int2 s;    // scale exponents; for a tier-A child, first its keys
+};
+// An untabled tier-A child's keys in the lane's two columns: the group prefixes in qubit order
+// (bit q = x_q), compressed to the child's support (rare: out of line).
+__device__ __noinline__ int2 rkeys_untabled(const KeyPlan *kp, const uint64_t *pre, int j, bool two, bool narrow) {
+    const uint64_t p0 = j ? __brevll(pre[0] << (64 - j)) : 0ull;
+    const uint64_t p1 = j ? __brevll(pre[two ? 1 : 0] << (64 - j)) : 0ull;
+    return make_int2((int)plan_key(kp, p0, narrow), (int)plan_key(kp, p1, narrow));
+}
+__device__ __forceinline__ void rchild_issue(const uint4 r, RChild &c, const RView &w) {
+    if (r.x & 0x80000000u) {  // rows written by this launch or earlier ones: plain loads
+        c.v = w.V4c[(int64_t)(r.x & 0x7fffffffu) * w.hp];
+        c.s = *reinterpret_cast<const int2 *>(w.Sc + (int64_t)r.y * w.pitch);
+    } else {
+        const int mid = (int)(r.y >> 8) - 1;
+        if (mid >= 0) {  // no key is stored past the tile's last column: that column reuses the first one's
+            const uint2 kk = *reinterpret_cast<const uint2 *>(w.Kc + (int64_t)mid * w.kpitch);
+            c.s = make_int2((int)kk.x, (int)(w.two ? kk.y : kk.x));
+        } else {
+            c.s = rkeys_untabled(w.kplan + (r.x - 1u), w.pre, w.j, w.two, w.narrow);
+        }
+    }
+}
+__device__ __forceinline__ void rchild_slots(const uint4 r, RChild &c, const RView &w) {
+    if (r.x & 0x80000000u) return;
+    const int kc = (int)(r.y & 0xffu);
+    const float2 *blk = w.VA + w.Vn * (int64_t)(((uint64_t)r.w << 32) | r.z);
+    const float2 v0 = blk[((uint64_t)w.vec0 << kc) | (uint32_t)c.s.x];
+    const float2 v1 = blk[((uint64_t)w.vec1 << kc) | (uint32_t)c.s.y];
+    c.v = make_float4(v0.x, v0.y, v1.x, v1.y);
+    c.s = make_int2(0, 0);
+}
+// A node's value in the lane's two columns from its loaded children x (and y: degree >= 2); children
+// beyond the second are loaded here, one at a time (X: the node may have more than two).
+template <bool X>
+__device__ __forceinline__ float4 rcombine(uint2 dsc, const RChild &x, const RChild &y, int sl0, int sl1,
+                                           const uint4 *brec, const RView &w) {
+    const uint32_t deg = dsc.y & 0xffffffu, o = dsc.y >> 24;
+    float2 q0, q1;
+    if (o == OP_MUL) {
+        q0 = mul_scaled(x.v.x, x.v.y, y.v.x, y.v.y, x.s.x + y.s.x - sl0);
+        q1 = mul_scaled(x.v.z, x.v.w, y.v.z, y.v.w, x.s.y + y.s.y - sl1);
+    } else {
+        float f0 = pow2f(x.s.x - sl0), f1 = pow2f(x.s.y - sl1);
+        q0 = make_float2(x.v.x * f0, x.v.y * f0);
+        q1 = make_float2(x.v.z * f1, x.v.w * f1);
+        if (deg >= 2u) {
+            f0 = pow2f(y.s.x - sl0);
+            f1 = pow2f(y.s.y - sl1);
+            q0.x += y.v.x * f0; q0.y += y.v.y * f0;
+            q1.x += y.v.z * f1; q1.y += y.v.w * f1;
+        }
+        for (uint32_t e = 2; X && e < deg; ++e) {  // children beyond the second
+            const uint4 r = __ldg(brec + dsc.x + e);
+            RChild z;
+            rchild_issue(r, z, w);
+            rchild_slots(r, z, w);
+            f0 = pow2f(z.s.x - sl0);
+            f1 = pow2f(z.s.y - sl1);
+            q0.x += z.v.x * f0; q0.y += z.v.y * f0;
+            q1.x += z.v.z * f1; q1.y += z.v.w * f1;
+        }
+    }
+    return make_float4(q0.x, q0.y, q1.x, q1.y);
+}
+__global__ void __launch_bounds__(TPB, 4) memoB_run_f32(const MemoBRunLevel *lv, int nlv, const uint2 *bdesc,
                                                       const PassDesc *pd, const MemoDesc *mdp, int64_t pitch,
                                                       float2 *__restrict__ V, int *__restrict__ S,
                                                       int *__restrict__ obs) {
@@ -1211,82 +1301,101 @@ __global__ void __launch_bounds__(TPB) memoB_run_f32(DevAC ac, const MemoBRunLev
     const int64_t col0 = pd->col0;
     const int32_t *col_vec = pd->es.col_vec;
     const int64_t n_vec = pd->es.n_vec;
-    const uint32_t *keys = mdp->keys;
-    const float2 *VA = static_cast<const float2 *>(mdp->VA);
-    const KeyPlan *kplan = mdp->kplan;
     const uint64_t *prefix = pd->es.prefix;
-    const int64_t kpitch = mdp->kpitch, Vn = mdp->V;
+    const uint32_t *cl_off = mdp->bcl_off;
+    const uint16_t *cl = mdp->bcl;
     const int j = mdp->j;
-    const bool narrow = j <= 32;
+    RView w;
+    w.VA = static_cast<const float2 *>(mdp->VA);
+    w.kplan = mdp->kplan;
+    w.hp = (uint32_t)(pitch >> 1);
+    w.pitch = (uint32_t)pitch;
+    w.kpitch = (uint32_t)mdp->kpitch;
+    w.Vn = (uint32_t)mdp->V;
+    w.j = j;
+    w.narrow = j <= 32;
+    const uint32_t *keys = mdp->keys;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    const int64_t nchunks = (ncols + 31) >> 5;
+    const int64_t nchunks = (ncols + 63) >> 6;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    float4 *V4 = reinterpret_cast<float4 *>(V);
     for (int64_t chunk = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; chunk < nchunks; chunk += nw) {
-        const int64_t col = chunk * 32 + lane;
+        const int64_t col = chunk * 64 + lane * 2;  // even, and the pitch is a multiple of 64
         const bool active = col < ncols;
-        const int64_t g = col0 + (active ? col : 0);
-        int64_t vv = col_vec ? (int64_t)col_vec[g] : g;
-        vv = vv < 0 ? 0 : (vv >= n_vec ? n_vec - 1 : vv);
-        const uint64_t vec = (uint64_t)vv;
-        // one child's value and scale exponent in this column (tier A: unscaled, exponent 0)
-        auto child = [&](const uint4 r, float2 &v, int &e) {
-            if (r.x & 0x80000000u) {
-                v = V[(int64_t)(r.x & 0x7fffffffu) * pitch + col];
-                e = S[(int64_t)r.y * pitch + col];
-            } else {
-                const int mid = (int)(r.y >> 8) - 1;
-                uint32_t key;
-                if (mid >= 0) {
-                    key = keys[(int64_t)mid * kpitch + col];
-                } else {
-                    const uint64_t pre = j ? __brevll(prefix[g] << (64 - j)) : 0ull;
-                    key = plan_key(kplan + (r.x - 1u), pre, narrow);
-                }
-                v = VA[Vn * (int64_t)(((uint64_t)r.w << 32) | r.z) + (int64_t)((vec << (r.y & 0xffu)) | key)];
-                e = 0;
-            }
-        };
+        w.two = col + 1 < ncols;
+        const int64_t g0 = col0 + (active ? col : 0), g1 = w.two ? g0 + 1 : g0;
+        int64_t v0 = col_vec ? (int64_t)col_vec[g0] : g0, v1 = col_vec ? (int64_t)col_vec[g1] : g1;
+        v0 = v0 < 0 ? 0 : (v0 >= n_vec ? n_vec - 1 : v0);
+        v1 = v1 < 0 ? 0 : (v1 >= n_vec ? n_vec - 1 : v1);
+        w.vec0 = (uint32_t)v0;
+        w.vec1 = (uint32_t)v1;
+        w.pre = prefix + g0;
+        w.V4c = V4 + (col >> 1);
+        w.Sc = S + col;
+        w.Kc = keys + col;
         for (int l = 0; l < nlv; ++l) {
             const MemoBRunLevel L = lv[l];
-            int sl = 0;
+            int sl0 = 0, sl1 = 0;
             if (active) {
-                sl = level_scale_col(ac, L.L, pitch, L.floor0, S, obs, col);
-                S[(int64_t)L.L * pitch + col] = sl;
+                sl0 = level_scale_col(cl_off, cl, L.L, pitch, L.floor0, S, obs, col);
+                sl1 = w.two ? level_scale_col(cl_off, cl, L.L, pitch, L.floor0, S, obs, col + 1) : 0;
             }
-            float mx = 0.f;
+            float mx0 = 0.f, mx1 = 0.f;
             for (uint32_t kb = 0; kb < L.count; kb += NBB) {
                 const int nn = (int)min((uint32_t)NBB, L.count - kb);
                 bstage(sdesc[wp], srec[wp], bdesc + L.b0 + kb, brec, nn, lane);
                 if (!active) continue;
-                for (int i = 0; i < nn; ++i) {
-                    const uint2 dsc = sdesc[wp][i];
-                    const uint32_t deg = dsc.y & 0xffffffu, o = dsc.y >> 24;
-                    float2 x, y, q;
-                    int ex, ey;
-                    child(srec[wp][i][0], x, ex);
-                    if (deg >= 2u) child(srec[wp][i][1], y, ey);
-                    if (o == OP_MUL) {
-                        q = cscale(cmul(x, y), pow2f(ex + ey - sl));
+                float4 *dst = w.V4c + (int64_t)(L.b0 + kb) * w.hp;
+                for (int i = 0; i < nn;) {  // two nodes at a time where both have at most two children
+                    const uint2 d0 = sdesc[wp][i];
+                    const uint2 d1 = sdesc[wp][i + 1 < nn ? i + 1 : i];
+                    const uint32_t deg0 = d0.y & 0xffffffu, deg1 = d1.y & 0xffffffu;
+                    RChild x0, y0;
+                    y0.v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    y0.s = make_int2(0, 0);
+                    if (i + 1 < nn && deg0 <= 2u && deg1 <= 2u) {
+                        RChild x1, y1;
+                        y1.v = make_float4(0.f, 0.f, 0.f, 0.f);
+                        y1.s = make_int2(0, 0);
+                        rchild_issue(srec[wp][i][0], x0, w);
+                        if (deg0 == 2u) rchild_issue(srec[wp][i][1], y0, w);
+                        rchild_issue(srec[wp][i + 1][0], x1, w);
+                        if (deg1 == 2u) rchild_issue(srec[wp][i + 1][1], y1, w);
+                        rchild_slots(srec[wp][i][0], x0, w);
+                        if (deg0 == 2u) rchild_slots(srec[wp][i][1], y0, w);
+                        rchild_slots(srec[wp][i + 1][0], x1, w);
+                        if (deg1 == 2u) rchild_slots(srec[wp][i + 1][1], y1, w);
+                        const float4 q = rcombine<false>(d0, x0, y0, sl0, sl1, brec, w);
+                        const float4 p = rcombine<false>(d1, x1, y1, sl0, sl1, brec, w);
+                        dst[(int64_t)i * w.hp] = q;
+                        dst[(int64_t)(i + 1) * w.hp] = p;
+                        mx0 = fmaxf(mx0, fmaxf(fmaxf(fabsf(q.x), fabsf(q.y)), fmaxf(fabsf(p.x), fabsf(p.y))));
+                        mx1 = fmaxf(mx1, fmaxf(fmaxf(fabsf(q.z), fabsf(q.w)), fmaxf(fabsf(p.z), fabsf(p.w))));
+                        i += 2;
                     } else {
-                        const float f0 = pow2f(ex - sl);
-                        q = make_float2(x.x * f0, x.y * f0);
-                        if (deg >= 2u) {
-                            const float f1 = pow2f(ey - sl);
-                            q.x += y.x * f1; q.y += y.y * f1;
-                        }
-                        for (uint32_t e = 2; e < deg; ++e) {  // children beyond the second
-                            float2 z;
-                            int ez;
-                            child(__ldg(brec + dsc.x + e), z, ez);
-                            const float fz = pow2f(ez - sl);
-                            q.x += z.x * fz; q.y += z.y * fz;
-                        }
+                        rchild_issue(srec[wp][i][0], x0, w);
+                        if (deg0 >= 2u) rchild_issue(srec[wp][i][1], y0, w);
+                        rchild_slots(srec[wp][i][0], x0, w);
+                        if (deg0 >= 2u) rchild_slots(srec[wp][i][1], y0, w);
+                        const float4 q = rcombine<true>(d0, x0, y0, sl0, sl1, brec, w);
+                        dst[(int64_t)i * w.hp] = q;
+                        mx0 = fmaxf(mx0, fmaxf(fabsf(q.x), fabsf(q.y)));
+                        mx1 = fmaxf(mx1, fmaxf(fabsf(q.z), fabsf(q.w)));
+                        i += 1;
                     }
-                    V[(int64_t)(L.b0 + kb + i) * pitch + col] = q;
-                    mx = fmaxf(mx, fmaxf(fabsf(q.x), fabsf(q.y)));
                 }
             }
-            if (active) atomicMax(obs + (int64_t)L.L * pitch + col, (__float_as_int(mx) >> 23) - 127);
+            if (active) {
+                int *sw = S + (int64_t)L.L * pitch + col, *ow = obs + (int64_t)L.L * pitch + col;
+                const int e0 = (__float_as_int(mx0) >> 23) - 127, e1 = (__float_as_int(mx1) >> 23) - 127;
+                if (w.two) {
+                    *reinterpret_cast<int2 *>(sw) = make_int2(sl0, sl1);
+                    *reinterpret_cast<int2 *>(ow) = make_int2(e0, e1);
+                } else {
+                    sw[0] = sl0;
+                    ow[0] = e0;
+                }
+            }
         }
     }
 }
@@ -1875,6 +1984,8 @@ struct qkc_ac {
         std::vector<std::vector<AItem>> b_items;        // per step: tier-B launches (a level, or a run of cnt levels)
         std::vector<int64_t> rst_base, rst_cnt;         // per step: levels whose observed exponents are reset
         int32_t *d_rst = nullptr;
+        uint32_t *d_bclo = nullptr;                     // per step, per level (D + 1 entries a step): where
+        uint16_t *d_bcl = nullptr;                      // its child levels holding tier-B nodes start in d_bcl
         MemoBRunLevel *d_brunlv = nullptr;              // the tier-B runs' levels, all steps
         std::vector<std::vector<uint8_t>> floor0;               // per step, [D]
         std::vector<int64_t> a_base, b_base, offu_base, g_base;  // per step
@@ -2002,7 +2113,7 @@ extern "C" void qkc_free_ac(qkc_ac *a) {
     for (auto *m : a->memo) {
         if (!m) continue;
         cudaFree(m->d_a_nodes); cudaFree(m->d_a_grp); cudaFree(m->d_offu);
-        cudaFree(m->d_emask); cudaFree(m->d_runlv); cudaFree(m->d_brunlv); cudaFree(m->d_rst); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
+        cudaFree(m->d_emask); cudaFree(m->d_runlv); cudaFree(m->d_brunlv); cudaFree(m->d_rst); cudaFree(m->d_bclo); cudaFree(m->d_bcl); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
         for (auto &g : m->gA) if (g.exec) cudaGraphExecDestroy(g.exec);
         for (auto &g : m->gB) if (g.exec) cudaGraphExecDestroy(g.exec);
         delete m;
@@ -2439,11 +2550,11 @@ static void launch_up_sequence(qkc_ac *a, cudaStream_t s, void *V, int *S, int *
     const unsigned gs = (unsigned)((pitch + TPB - 1) / TPB);
     if (a->prec == 32) {
         // level 0: leaves (S[0] = 0 and obs[0] reset by the scale kernel, then observed)
-        level_scale_kernel<<<gs, TPB, 0, s>>>(d, 0, pitch, 0, S, obs);
+        level_scale_kernel<<<gs, TPB, 0, s>>>(d.cl_off, d.cl, 0, pitch, 0, S, obs);
         bind_leaves_f32<<<grid_for((int64_t)a->n_leaves * pitch), TPB, 0, s>>>(d, pd, pitch, (float2 *)V, obs,
                                                                               (int)a->n_leaves);
         for (uint32_t L = 1; L < a->D; ++L) {
-            level_scale_kernel<<<gs, TPB, 0, s>>>(d, (int)L, pitch, 0, S, obs);
+            level_scale_kernel<<<gs, TPB, 0, s>>>(d.cl_off, d.cl, (int)L, pitch, 0, S, obs);
             LevelArgs la{a->level_off[L], a->level_off[L + 1], (int)L, pitch};
             const int64_t items = ((int64_t)(la.hi - la.lo + NB - 1) / NB) * ((pitch + 63) / 64);
             up_level_f32<<<grid_for(items * 32, TPB, (int64_t)sms * 8), TPB, 0, s>>>(d, la, pd, (float2 *)V, S, obs);
@@ -2867,6 +2978,8 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
     m->b_items.assign(nq, {});
     std::vector<MemoBRunLevel> brunlv;
     std::vector<int32_t> rst;
+    std::vector<uint16_t> bcl;
+    std::vector<uint32_t> bclo;
     std::vector<int32_t> plan_of;  // per node: its key plan in this step, -1 if none yet
     std::vector<int64_t> row_of;   // per node: its tier-B row in this step
     std::vector<char> reach;       // per node: reachable from this step's root
@@ -3066,16 +3179,22 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
             }
             flush();
         }
-        {  // levels whose observed exponents this step's tier-B pass writes or reads
-            std::vector<char> need(D, 0);
-            for (uint32_t L = 1; L < D; ++L) {
-                if (m->b_lvl[j][L + 1] == m->b_lvl[j][L]) continue;
-                need[L] = 1;
-                for (uint32_t k = a->h_cl_off[L]; k < a->h_cl_off[L + 1]; ++k) need[a->h_cl[k]] = 1;
+        {  // level scales: per level with tier-B nodes, its child levels that hold tier-B nodes in this
+           // step (no other level is computed here); observed exponents reset: the levels of per-level
+           // launches that form their scales inline (they take a maximum over node blocks; a run stores
+           // its levels' exponents, and the scale kernel resets its own level)
+            auto has_b = [&](uint32_t L) { return m->b_lvl[j][L + 1] > m->b_lvl[j][L]; };
+            for (uint32_t L = 0; L < D; ++L) {
+                bclo.push_back((uint32_t)bcl.size());
+                if (L == 0 || !has_b(L)) continue;
+                for (uint32_t k = a->h_cl_off[L]; k < a->h_cl_off[L + 1]; ++k)
+                    if (has_b((uint32_t)a->h_cl[k])) bcl.push_back(a->h_cl[k]);
             }
+            bclo.push_back((uint32_t)bcl.size());
             m->rst_base.push_back((int64_t)rst.size());
-            for (uint32_t L = 0; L < D; ++L)
-                if (need[L]) rst.push_back((int32_t)L);
+            if (a->prec == 32 && m->b_lvl[j][D] <= MEMO_INLINE_SCALE_B)
+                for (const auto &it : m->b_items[j])
+                    if (it.cnt == 0) rst.push_back((int32_t)it.L);
             m->rst_cnt.push_back((int64_t)rst.size() - m->rst_base[j]);
         }
         m->root_row.push_back(row_of[a->roots[j]]);
@@ -3099,13 +3218,15 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
         (*st = upload(&m->d_runlv, runlv.data(), runlv.size(), dummy)) ||
         (*st = upload(&m->d_brunlv, brunlv.data(), brunlv.size(), dummy)) ||
         (*st = upload(&m->d_rst, rst.data(), rst.size(), dummy)) ||
+        (*st = upload(&m->d_bclo, bclo.data(), bclo.size(), dummy)) ||
+        (*st = upload(&m->d_bcl, bcl.data(), bcl.size(), dummy)) ||
         (*st = upload(&m->d_bdesc, bdesc.data(), bdesc.size(), dummy)) ||
         (*st = upload(&m->d_brec, brec.data(), brec.size(), dummy)) ||
         (*st = upload(&m->d_kplan, kplan.data(), kplan.size(), dummy)) ||
         (*st = upload(&m->d_aplan, aplan.data(), aplan.size(), dummy)) ||
         (*st = upload(&m->d_bplan, bplan.data(), bplan.size(), dummy))) {
         cudaFree(m->d_a_nodes); cudaFree(m->d_a_grp); cudaFree(m->d_offu);
-        cudaFree(m->d_emask); cudaFree(m->d_runlv); cudaFree(m->d_brunlv); cudaFree(m->d_rst); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
+        cudaFree(m->d_emask); cudaFree(m->d_runlv); cudaFree(m->d_brunlv); cudaFree(m->d_rst); cudaFree(m->d_bclo); cudaFree(m->d_bcl); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
         delete m;
         return nullptr;
     }
@@ -3160,18 +3281,20 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
                 a->d_obs, m->d_rst + m->rst_base[j], (int)m->rst_cnt[j], pitch);
         const bool inline_scale = m->b_lvl[j][D] <= MEMO_INLINE_SCALE_B;
         const uint2 *bd_j = m->d_bdesc + m->b_base[j];
+        const uint32_t *cl_off_j = m->d_bclo + (size_t)j * (D + 1);
         for (const auto &it : m->b_items[j]) {
-            if (it.cnt > 0) {  // a run of small levels (FP32): a warp per 32-column chunk walks them
-                const int64_t chunks = (pitch + 31) / 32;  // a warp per 32-column chunk
+            if (it.cnt > 0) {  // a run of small levels (FP32): a warp per 64-column chunk walks them
+                const int64_t chunks = (pitch + 63) / 64;
                 const unsigned g = (unsigned)std::min<int64_t>((chunks + TPB / 32 - 1) / (TPB / 32), (int64_t)sms * 8);
-                memoB_run_f32<<<g, TPB, 0, s>>>(d, m->d_brunlv + it.off, it.cnt, bd_j, a->d_desc, a->d_mdesc, pitch,
+                memoB_run_f32<<<g, TPB, 0, s>>>(m->d_brunlv + it.off, it.cnt, bd_j, a->d_desc, a->d_mdesc, pitch,
                                                  (float2 *)a->d_V, a->d_S, a->d_obs);
                 continue;
             }
             const uint32_t L = (uint32_t)it.L;
             const int64_t b0 = m->b_lvl[j][L], b1 = m->b_lvl[j][L + 1];
             if (a->prec == 32 && !inline_scale)
-                level_scale_kernel<<<gs, TPB, 0, s>>>(d, (int)L, pitch, m->floor0[j][L], a->d_S, a->d_obs);
+                level_scale_kernel<<<gs, TPB, 0, s>>>(cl_off_j, m->d_bcl, (int)L, pitch, m->floor0[j][L], a->d_S,
+                                                      a->d_obs);
             // lo: the level's first tier-B row; hi: bit 0 reads tier-A values, bit 1 scale formed inline
             LevelArgs la{(uint32_t)b0, (uint32_t)m->floor0[j][L] | (inline_scale ? 2u : 0u), (int)L, pitch};
             const int64_t cw = a->prec == 32 ? 128 : 32;  // columns per warp item
@@ -3246,7 +3369,7 @@ static qkc_status memo_pass(qkc_ac *a, qkc_ac::MemoMeta *m, int j, int clamp, in
     MemoDesc md{n_vec,    j,         clamp, jmask, a->d_pv, a->vec_cap, a->d_VA, m->d_offu + m->offu_base[j],
                 a->d_sigma, m->d_emask + (size_t)j * a->E, m->d_brec + m->br_base[j],
                 m->d_kplan + m->kp_base[j], m->d_aplan + m->ap_base[j], m->d_bplan + m->bp_base[j],
-                (int32_t)m->bp_cnt[j], a->d_keys, a->tile};
+                (int32_t)m->bp_cnt[j], a->d_keys, a->tile, m->d_bclo + (size_t)j * (a->D + 1), m->d_bcl};
     set_memo_desc<<<1, 1, 0, s>>>(a->d_mdesc, md);
     ++a->launches;
     const size_t ra = a->recs.size();
