@@ -68,10 +68,13 @@ namespace {
 enum : uint8_t { OP_IND = 0, OP_PARAM = 1, OP_CONST = 2, OP_ADD = 3, OP_MUL = 4 };
 constexpr int NB = 8;          // nodes per warp item
 constexpr int NBB = 32;        // tier-B nodes per warp item (memoised passes)
+static_assert(NBB == 32, "memoB_level_f32 splits a node block of 32 by shifts");
 constexpr int TPB = 256;       // threads per block
 constexpr int OBS_EMPTY = -1000;
 constexpr int64_t MEMO_RUN_T = 1024;           // tier-A levels with at most this many threads per vector
                                                // are walked in runs by one launch
+constexpr int64_t MEMO_ALL_T = 4096;           // every step's tier A in one launch (a block per step and
+                                               // vector) when no tier-A level is wider than this
 constexpr int64_t MEMO_INLINE_SCALE_B = 4096;  // tier-B sets up to this size form level scales inline
 constexpr int64_t MEMO_RUN_B = NBB;            // FP32 tier-B levels of one node block (at most 32 nodes) are walked
                                                // in runs by one launch
@@ -904,6 +907,35 @@ __global__ void __launch_bounds__(TPB) memoA_run(DevAC ac, const MemoDesc *mdp, 
     }
 }
 
+// Every step's tier A in one launch, when every step's slots are resident side by side: a block per
+// (step, vector) walks all of the step's tier-A levels (each level's slots by the block's threads,
+// then a barrier).  Tier A depends on the parameters alone, not on the sampled prefixes, and each
+// step's levels form a chain of small dependent levels; so the steps run concurrently instead of one
+// chain per step.  Pairs are taken in `order` (the steps with the most tier-A work first).
+struct MemoAStep {
+    int64_t node_base, grp_base;  // the step's first tier-A node and group
+    uint32_t lv0, lv1;            // its tier-A levels in the level list
+};
+template <typename C>
+__global__ void __launch_bounds__(TPB) memoA_all(DevAC ac, const MemoDesc *mdesc, const uint32_t *nodes,
+                                                  const MemoAGroup *grp, const MemoARunLevel *lv,
+                                                  const MemoAStep *steps, const int32_t *order, int nq, int64_t V) {
+    for (int64_t p = blockIdx.x; p < (int64_t)nq * V; p += gridDim.x) {
+        const int j = order[p / V];
+        const int64_t vec = p % V;
+        const MemoDesc md = mdesc[j];
+        C *VA = static_cast<C *>(md.VA);
+        const MemoAStep st = steps[j];
+        for (uint32_t l = st.lv0; l < st.lv1; ++l) {
+            const MemoARunLevel L = lv[l];
+            for (uint32_t t = threadIdx.x; t < L.T; t += blockDim.x)
+                memoA_slot<C>(ac, md, VA, nodes + st.node_base + L.i0, grp + st.grp_base + L.g0, (int)L.ng, L.u0,
+                              vec, t);
+            __syncthreads();
+        }
+    }
+}
+
 // The group-key table of one tile: for every group column and tabled support, the column's
 // prefix bits on that support, packed (read by tier-B nodes for their tier-A children).  Only
 // columns below the tile's group count are written.
@@ -1148,9 +1180,9 @@ __device__ __forceinline__ void bobserve(int *obs, int L, int64_t pitch, int64_t
 // a.hi bit 0: the level reads unscaled tier-A values (its scale is at least 0); bit 1: this kernel
 // forms the level's scale itself (the items of the level's first node block write it).
 __global__ void __launch_bounds__(TPB, 3) memoB_level_f32(DevAC ac, LevelArgs a, const uint2 *bdesc, int64_t count,
-                                                        const PassDesc *pd, const MemoDesc *mdp,
-                                                        float2 *__restrict__ V, int *__restrict__ S,
-                                                        int *__restrict__ obs) {
+                                                        const PassDesc *pd,
+                                                        const MemoDesc *mdp, float2 *__restrict__ V,
+                                                        int *__restrict__ S, int *__restrict__ obs) {
     __shared__ uint2 sdesc[TPB / 32][NBB];
     __shared__ uint4 srec[TPB / 32][NBB][2];
     const int64_t ncols = desc_cols(*pd);
@@ -1163,35 +1195,60 @@ __global__ void __launch_bounds__(TPB, 3) memoB_level_f32(DevAC ac, LevelArgs a,
     BView w;
     bview_init(w, pd, mdp, a.pitch);
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    // work items (node block, column chunk) in 32 bits: blocks < 2^28, chunks < 2^25
+    // Work items (node block of 32, 128-column chunk), node-block major, dealt round-robin over the
+    // warps: at any time the warps share a node block, so its tier-A children stay in L2.  Whole
+    // rounds take whole items; the items left (fewer than a round) are cut into 2^sub_log2 parts of
+    // 32 >> sub_log2 nodes, so that the last round is not a few warps doing whole items.
     const uint32_t nchunks = (uint32_t)((ncols + 127) >> 7);
-    const uint32_t nblk = (uint32_t)((count + NBB - 1) / NBB);
+    const uint32_t cnt = (uint32_t)count;
+    const uint32_t nblk = (cnt + NBB - 1) / NBB;
+    const uint32_t items = nblk * nchunks;  // < 2^32 (the level's rows of the tile would exceed 4 TB)
     const uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t full = items / nw * nw, rem = items - full;
     float4 *V4 = reinterpret_cast<float4 *>(V);
-    // item = node block * nchunks + column chunk, stepped by the warp count without division
-    uint32_t blk = wid / nchunks, chunk = wid % nchunks;
-    const uint32_t dq = nw / nchunks, dr = nw % nchunks;
-    while (blk < nblk) {
+    // one item: nodes n0 .. n0 + nn - 1 of the level in chunk `chunk`
+    auto item = [&](uint32_t n0, int nn, uint32_t chunk) {
         const int64_t col = (int64_t)chunk * 128 + lane * 4;
-        const uint32_t blk_i = blk;
-        chunk += dr;
-        blk += dq;
-        if (chunk >= nchunks) {
-            chunk -= nchunks;
-            ++blk;
-        }
-        const int64_t kb = (int64_t)blk_i * NBB;
-        const int nn = (int)min((int64_t)NBB, count - kb);
-        bstage(sdesc[wp], srec[wp], bdesc + kb, brec, nn, lane);
-        if (col >= ncols) continue;
+        bstage(sdesc[wp], srec[wp], bdesc + n0, brec, nn, lane);
+        if (col >= ncols) return;
         bview_cols(w, col, ncols, col0, col_vec, n_vec, V4, S, keys);
         int sl[4];
         blevel_scale(mdp, a.L, a.pitch, (a.hi & 2u) != 0, (int)(a.hi & 1u), S, obs, col, w.nv, sl);
-        if ((a.hi & 2u) && blk_i == 0) bstore_scale(S, a.L, a.pitch, col, w.nv, sl);
+        if ((a.hi & 2u) && n0 == 0) bstore_scale(S, a.L, a.pitch, col, w.nv, sl);
         float mx[4] = {0.f, 0.f, 0.f, 0.f};
-        bnodes(sdesc[wp], srec[wp], nn, sl, V4 + (int64_t)(a.lo + kb) * w.hp + (col >> 1), w, brec, mx);
+        bnodes(sdesc[wp], srec[wp], nn, sl, V4 + (int64_t)(a.lo + n0) * w.hp + (col >> 1), w, brec, mx);
         bobserve(obs, a.L, a.pitch, col, w.nv, mx);
+    };
+    {  // whole rounds: item = node block * nchunks + chunk, stepped by the warp count without division
+        uint32_t blk = wid / nchunks, chunk = wid % nchunks;
+        const uint32_t dq = nw / nchunks, dr = nw % nchunks;
+        for (uint32_t it = wid; it < full; it += nw) {
+            const uint32_t b = blk, c = chunk;
+            chunk += dr;
+            blk += dq;
+            if (chunk >= nchunks) {
+                chunk -= nchunks;
+                ++blk;
+            }
+            item(b * NBB, (int)min((uint32_t)NBB, cnt - b * NBB), c);
+        }
+    }
+    if (rem == 0) return;
+    // the last, partial round in parts: the part size that needs the fewest node-times, at about
+    // three per item of overhead
+    uint32_t sub_log2 = 0, best = 0xffffffffu;
+    for (uint32_t sl = 0; sl <= 3; ++sl) {
+        const uint32_t cost = (((rem << sl) + nw - 1) / nw) * ((uint32_t)(NBB >> sl) + 3u);
+        if (cost < best) best = cost, sub_log2 = sl;
+    }
+    const uint32_t nsub = rem << sub_log2;
+    for (uint32_t t = wid; t < nsub; t += nw) {
+        const uint32_t it = full + (t >> sub_log2);
+        const uint32_t blk = it / nchunks, chunk = it - blk * nchunks;
+        const uint32_t n0 = blk * NBB + ((t & ((1u << sub_log2) - 1u)) << (5 - sub_log2));
+        if (n0 >= cnt) continue;  // an empty part of the level's last node block (warp-uniform)
+        item(n0, (int)min((uint32_t)NBB >> sub_log2, cnt - n0), chunk);
     }
 }
 
@@ -1962,7 +2019,7 @@ struct qkc_ac {
     int64_t eval_cols = 0;
     const int32_t *eval_colvec = nullptr;
     uint64_t *d_sigma = nullptr;
-    MemoDesc *d_mdesc = nullptr;
+    MemoDesc *d_mdesc = nullptr;  // one memo descriptor per step
     // a captured launch sequence and the buffers it was captured with: the scratch generation changes
     // with every reallocation of a buffer a sequence names (values, scales, adjoints, roots), so a
     // graph is captured again whenever any of them moved, not only the value tile
@@ -1976,6 +2033,11 @@ struct qkc_ac {
     struct MemoMeta {
         int cap = 0;
         int64_t max_units = 0;
+        std::vector<int64_t> unit_base{0};  // per step: its first unit when every step's slots are resident
+        MemoARunLevel *d_alllv = nullptr;   // every step's tier-A levels (memoA_all)
+        MemoAStep *d_asteps = nullptr;      // per step: its bases and levels in d_alllv
+        int32_t *d_aorder = nullptr;        // the steps by tier-A work, largest first
+        int64_t all_T = 0;                  // the largest threads per vector of any tier-A level
         std::vector<std::vector<int64_t>> a_lvl, u_lvl, b_lvl, g_lvl;  // per step, [D + 1]
         std::vector<std::vector<int64_t>> t_lvl;                        // per step and level: tier-A threads
         struct AItem { int L; int64_t off; int cnt; };  // one tier-A launch: level L, or a run of cnt levels
@@ -2113,7 +2175,7 @@ extern "C" void qkc_free_ac(qkc_ac *a) {
     for (auto *m : a->memo) {
         if (!m) continue;
         cudaFree(m->d_a_nodes); cudaFree(m->d_a_grp); cudaFree(m->d_offu);
-        cudaFree(m->d_emask); cudaFree(m->d_runlv); cudaFree(m->d_brunlv); cudaFree(m->d_rst); cudaFree(m->d_bclo); cudaFree(m->d_bcl); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
+        cudaFree(m->d_emask); cudaFree(m->d_runlv); cudaFree(m->d_brunlv); cudaFree(m->d_rst); cudaFree(m->d_alllv); cudaFree(m->d_asteps); cudaFree(m->d_aorder); cudaFree(m->d_bclo); cudaFree(m->d_bcl); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
         for (auto &g : m->gA) if (g.exec) cudaGraphExecDestroy(g.exec);
         for (auto &g : m->gB) if (g.exec) cudaGraphExecDestroy(g.exec);
         delete m;
@@ -2371,7 +2433,7 @@ extern "C" qkc_status qkc_load_ac(qkc_ctx *ctx, const uint8_t *bytes, uint64_t l
         qkc_free_ac(a);
         return st;
     }
-    if (cudaMalloc((void **)&a->d_mdesc, sizeof(MemoDesc)) != cudaSuccess ||
+    if (cudaMalloc((void **)&a->d_mdesc, sizeof(MemoDesc) * std::max<size_t>(1, a->n_qubits)) != cudaSuccess ||
         cudaMalloc((void **)&a->d_desc, sizeof(PassDesc)) != cudaSuccess ||
         cudaMalloc((void **)&a->d_status, sizeof(int32_t)) != cudaSuccess ||
         cudaMemset(a->d_status, 0, sizeof(int32_t)) != cudaSuccess) {
@@ -2977,6 +3039,8 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
     m->a_items.assign(nq, {});
     m->b_items.assign(nq, {});
     std::vector<MemoBRunLevel> brunlv;
+    std::vector<MemoARunLevel> alllv;
+    std::vector<MemoAStep> asteps;
     std::vector<int32_t> rst;
     std::vector<uint16_t> bcl;
     std::vector<uint32_t> bclo;
@@ -3154,6 +3218,18 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
             }
             flush();
         }
+        {  // every tier-A level of the step, in order (memoA_all)
+            MemoAStep st{m->a_base[j], m->g_base[j], (uint32_t)alllv.size(), 0u};
+            for (uint32_t L = 0; L < D; ++L) {
+                if (m->a_lvl[j][L + 1] == m->a_lvl[j][L]) continue;
+                alllv.push_back(MemoARunLevel{(uint32_t)m->a_lvl[j][L], (uint32_t)m->g_lvl[j][L],
+                                              (uint32_t)(m->g_lvl[j][L + 1] - m->g_lvl[j][L]),
+                                              (uint32_t)m->t_lvl[j][L], m->u_lvl[j][L]});
+                m->all_T = std::max<int64_t>(m->all_T, m->t_lvl[j][L]);
+            }
+            st.lv1 = (uint32_t)alllv.size();
+            asteps.push_back(st);
+        }
         {  // tier-A launches: consecutive small levels form one run (a block per vector walks them)
             std::vector<uint32_t> pend;
             auto flush = [&]() {
@@ -3204,12 +3280,17 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
         m->a_edges_slot.push_back(aedges);
         m->b_edges_col.push_back(bedges);
         m->max_units = std::max(m->max_units, units);
+        m->unit_base.push_back(m->unit_base.back() + units);
     }
     if (m->max_units >= 0xffffffffll) {  // block offsets are stored in 32 bits per edge
         delete m;
         *st = QKC_OK;
         return nullptr;
     }
+    std::vector<int32_t> aorder(nq);  // steps by tier-A work, largest first (memoA_all)
+    for (int j = 0; j < nq; ++j) aorder[j] = j;
+    std::stable_sort(aorder.begin(), aorder.end(),
+                     [&](int x, int y) { return m->a_bytes_slot[x] > m->a_bytes_slot[y]; });
     int64_t dummy = 0;
     if ((*st = upload(&m->d_a_nodes, an.data(), an.size(), dummy)) ||
         (*st = upload(&m->d_a_grp, grp.data(), grp.size(), dummy)) ||
@@ -3219,6 +3300,9 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
         (*st = upload(&m->d_brunlv, brunlv.data(), brunlv.size(), dummy)) ||
         (*st = upload(&m->d_rst, rst.data(), rst.size(), dummy)) ||
         (*st = upload(&m->d_bclo, bclo.data(), bclo.size(), dummy)) ||
+        (*st = upload(&m->d_alllv, alllv.data(), alllv.size(), dummy)) ||
+        (*st = upload(&m->d_asteps, asteps.data(), asteps.size(), dummy)) ||
+        (*st = upload(&m->d_aorder, aorder.data(), aorder.size(), dummy)) ||
         (*st = upload(&m->d_bcl, bcl.data(), bcl.size(), dummy)) ||
         (*st = upload(&m->d_bdesc, bdesc.data(), bdesc.size(), dummy)) ||
         (*st = upload(&m->d_brec, brec.data(), brec.size(), dummy)) ||
@@ -3226,7 +3310,7 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
         (*st = upload(&m->d_aplan, aplan.data(), aplan.size(), dummy)) ||
         (*st = upload(&m->d_bplan, bplan.data(), bplan.size(), dummy))) {
         cudaFree(m->d_a_nodes); cudaFree(m->d_a_grp); cudaFree(m->d_offu);
-        cudaFree(m->d_emask); cudaFree(m->d_runlv); cudaFree(m->d_brunlv); cudaFree(m->d_rst); cudaFree(m->d_bclo); cudaFree(m->d_bcl); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
+        cudaFree(m->d_emask); cudaFree(m->d_runlv); cudaFree(m->d_brunlv); cudaFree(m->d_rst); cudaFree(m->d_alllv); cudaFree(m->d_asteps); cudaFree(m->d_aorder); cudaFree(m->d_bclo); cudaFree(m->d_bcl); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
         delete m;
         return nullptr;
     }
@@ -3239,6 +3323,7 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
 // their grids do not depend on the number of vectors or columns.
 static void launch_memoA_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, cudaStream_t s) {
     const DevAC d = a->dev();
+    const MemoDesc *md_j = a->d_mdesc + j;
     const unsigned g = (unsigned)(a->ctx->sm_count * 16);
     const unsigned gr = (unsigned)(a->ctx->sm_count * 4);  // run kernels: a block per vector, grid-stride
     const uint32_t *nodes_j = m->d_a_nodes + m->a_base[j];
@@ -3246,9 +3331,9 @@ static void launch_memoA_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
     for (const auto &it : m->a_items[j]) {
         if (it.cnt > 0) {
             if (a->prec == 32)
-                memoA_run<float2><<<gr, TPB, 0, s>>>(d, a->d_mdesc, nodes_j, grp_j, m->d_runlv + it.off, it.cnt);
+                memoA_run<float2><<<gr, TPB, 0, s>>>(d, md_j, nodes_j, grp_j, m->d_runlv + it.off, it.cnt);
             else
-                memoA_run<double2><<<gr, TPB, 0, s>>>(d, a->d_mdesc, nodes_j, grp_j, m->d_runlv + it.off, it.cnt);
+                memoA_run<double2><<<gr, TPB, 0, s>>>(d, md_j, nodes_j, grp_j, m->d_runlv + it.off, it.cnt);
             continue;
         }
         const uint32_t L = (uint32_t)it.L;
@@ -3258,8 +3343,8 @@ static void launch_memoA_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
         const uint32_t *nodes = nodes_j + i0;
         const MemoAGroup *gp = grp_j + m->g_lvl[j][L];
         const int ng = (int)(m->g_lvl[j][L + 1] - m->g_lvl[j][L]);
-        if (a->prec == 32) memoA_level<float2><<<g, TPB, 0, s>>>(d, a->d_mdesc, nodes, gp, ng, u0, T);
-        else memoA_level<double2><<<g, TPB, 0, s>>>(d, a->d_mdesc, nodes, gp, ng, u0, T);
+        if (a->prec == 32) memoA_level<float2><<<g, TPB, 0, s>>>(d, md_j, nodes, gp, ng, u0, T);
+        else memoA_level<double2><<<g, TPB, 0, s>>>(d, md_j, nodes, gp, ng, u0, T);
     }
 }
 static int64_t memoA_launches(const qkc_ac *a, const qkc_ac::MemoMeta *m, int j) {
@@ -3268,12 +3353,13 @@ static int64_t memoA_launches(const qkc_ac *a, const qkc_ac::MemoMeta *m, int j)
 }
 static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, cudaStream_t s) {
     const DevAC d = a->dev();
+    const MemoDesc *md_j = a->d_mdesc + j;
     const int sms = a->ctx->sm_count;
     const uint32_t D = a->D;
     const int64_t pitch = a->tile;
     if (m->b_lvl[j][D] > 0) {
         const unsigned gs = (unsigned)((pitch + TPB - 1) / TPB);
-        if (m->bp_cnt[j] > 0) memo_keys<<<gs, TPB, 0, s>>>(a->d_desc, a->d_mdesc);
+        if (m->bp_cnt[j] > 0) memo_keys<<<gs, TPB, 0, s>>>(a->d_desc, md_j);
         // FP32 scales: only levels with tier-B nodes are computed, so every level's observed
         // exponent starts empty and the scale kernel runs for those levels alone
         if (a->prec == 32 && m->rst_cnt[j] > 0)
@@ -3286,7 +3372,7 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
             if (it.cnt > 0) {  // a run of small levels (FP32): a warp per 64-column chunk walks them
                 const int64_t chunks = (pitch + 63) / 64;
                 const unsigned g = (unsigned)std::min<int64_t>((chunks + TPB / 32 - 1) / (TPB / 32), (int64_t)sms * 8);
-                memoB_run_f32<<<g, TPB, 0, s>>>(m->d_brunlv + it.off, it.cnt, bd_j, a->d_desc, a->d_mdesc, pitch,
+                memoB_run_f32<<<g, TPB, 0, s>>>(m->d_brunlv + it.off, it.cnt, bd_j, a->d_desc, md_j, pitch,
                                                  (float2 *)a->d_V, a->d_S, a->d_obs);
                 continue;
             }
@@ -3297,18 +3383,19 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
                                                       a->d_obs);
             // lo: the level's first tier-B row; hi: bit 0 reads tier-A values, bit 1 scale formed inline
             LevelArgs la{(uint32_t)b0, (uint32_t)m->floor0[j][L] | (inline_scale ? 2u : 0u), (int)L, pitch};
-            const int64_t cw = a->prec == 32 ? 128 : 32;  // columns per warp item
-            const int64_t items = ((b1 - b0 + NBB - 1) / NBB) * ((pitch + cw - 1) / cw);
-            // FP32: one wave of resident blocks, grid-striding over the items
-            const unsigned g = grid_for(items * 32, TPB, (int64_t)sms * (a->prec == 32 ? a->ctx->memoB_blocks_per_sm : 8));
-            if (a->prec == 32)
-                memoB_level_f32<<<g, TPB, 0, s>>>(d, la, bd_j + b0, b1 - b0, a->d_desc, a->d_mdesc, (float2 *)a->d_V,
+            if (a->prec == 32) {  // at most one wave of resident blocks (the kernel splits the last round)
+                const int64_t items = ((b1 - b0 + NBB - 1) / NBB) * ((pitch + 127) / 128);
+                const unsigned g = grid_for(items * 8 * 32, TPB, (int64_t)sms * a->ctx->memoB_blocks_per_sm);
+                memoB_level_f32<<<g, TPB, 0, s>>>(d, la, bd_j + b0, b1 - b0, a->d_desc, md_j, (float2 *)a->d_V,
                                                    a->d_S, a->d_obs);
-            else
-                memoB_level_f64<<<g, TPB, 0, s>>>(la, bd_j + b0, b1 - b0, a->d_desc, a->d_mdesc, (double2 *)a->d_V);
+            } else {  // a warp per 32 nodes x 32 columns, grid-striding
+                const int64_t items = ((b1 - b0 + NBB - 1) / NBB) * ((pitch + 31) / 32);
+                const unsigned g = grid_for(items * 32, TPB, (int64_t)sms * 8);
+                memoB_level_f64<<<g, TPB, 0, s>>>(la, bd_j + b0, b1 - b0, a->d_desc, md_j, (double2 *)a->d_V);
+            }
         }
     }
-    memo_root<<<(unsigned)((pitch + TPB - 1) / TPB), TPB, 0, s>>>(a->d_mdesc, a->d_desc, a->roots[j], a->root_lev[j],
+    memo_root<<<(unsigned)((pitch + TPB - 1) / TPB), TPB, 0, s>>>(md_j, a->d_desc, a->roots[j], a->root_lev[j],
                                                                   m->root_row[j], a->d_V,
                                                                   a->d_S, pitch, a->prec == 32, a->d_root);
 }
@@ -3359,28 +3446,67 @@ static qkc_status memo_graph(qkc_ac *a, qkc_ac::MemoMeta *m, int j, bool partB, 
     return QKC_OK;
 }
 
-// One memoised upward pass of step j over `bound` group columns (device count n_active).
-static qkc_status memo_pass(qkc_ac *a, qkc_ac::MemoMeta *m, int j, int clamp, int64_t n_vec,
-                            const int32_t *n_active, int64_t bound, int cur, cudaStream_t s) {
+// Step j's memo descriptor (into a->d_mdesc + j).  resident: every step's tier-A slots are held at
+// once, step j's from unit unit_base[j]; else every step's start at unit 0.
+static void set_memo_step(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, int clamp, int64_t n_vec, bool resident,
+                          cudaStream_t s) {
     const uint64_t jmask = j == 0 ? 0ull : (j >= 64 ? ~0ull : ((1ull << j) - 1ull));
-    qkc_status st;
-    cudaGraphExec_t gA, gB;
-    if ((st = memo_graph(a, m, j, false, &gA)) || (st = memo_graph(a, m, j, true, &gB))) return st;
-    MemoDesc md{n_vec,    j,         clamp, jmask, a->d_pv, a->vec_cap, a->d_VA, m->d_offu + m->offu_base[j],
+    char *VA = static_cast<char *>(a->d_VA) + (resident ? n_vec * m->unit_base[j] * (int64_t)a->elem() : 0);
+    MemoDesc md{n_vec,    j,         clamp, jmask, a->d_pv, a->vec_cap, VA, m->d_offu + m->offu_base[j],
                 a->d_sigma, m->d_emask + (size_t)j * a->E, m->d_brec + m->br_base[j],
                 m->d_kplan + m->kp_base[j], m->d_aplan + m->ap_base[j], m->d_bplan + m->bp_base[j],
                 (int32_t)m->bp_cnt[j], a->d_keys, a->tile, m->d_bclo + (size_t)j * (a->D + 1), m->d_bcl};
-    set_memo_desc<<<1, 1, 0, s>>>(a->d_mdesc, md);
+    set_memo_desc<<<1, 1, 0, s>>>(a->d_mdesc + j, md);
     ++a->launches;
+}
+
+// The tier-A passes of every step at once (their slots resident side by side): memoA_all, a block
+// per (step, vector), after every step's memo descriptor is set.
+static qkc_status memo_tierA_all(qkc_ac *a, qkc_ac::MemoMeta *m, int clamp, int64_t n_vec, cudaStream_t s) {
+    const int nq = (int)a->n_qubits;
+    qkc_status st;
+    for (int j = 0; j < nq; ++j) set_memo_step(a, m, j, clamp, n_vec, true, s);
     const size_t ra = a->recs.size();
     if ((st = rec_begin(a, 3, nullptr, 0, 0, s))) return st;
     if (ra < a->recs.size()) {
-        a->recs[ra].fixed_bytes = (double)n_vec * m->a_bytes_slot[j];
-        a->recs[ra].fixed_edges = (double)n_vec * m->a_edges_slot[j];
+        for (int j = 0; j < nq; ++j) {
+            a->recs[ra].fixed_bytes += (double)n_vec * m->a_bytes_slot[j];
+            a->recs[ra].fixed_edges += (double)n_vec * m->a_edges_slot[j];
+        }
     }
-    QKC_CUDA(cudaGraphLaunch(gA, s));  // tier A: once per step
-    a->launches += memoA_launches(a, m, j);
+    const DevAC d = a->dev();
+    const unsigned g = (unsigned)std::min<int64_t>((int64_t)nq * n_vec, (int64_t)a->ctx->sm_count * 8);
+    if (a->prec == 32)
+        memoA_all<float2><<<g, TPB, 0, s>>>(d, a->d_mdesc, m->d_a_nodes, m->d_a_grp, m->d_alllv, m->d_asteps,
+                                            m->d_aorder, nq, n_vec);
+    else
+        memoA_all<double2><<<g, TPB, 0, s>>>(d, a->d_mdesc, m->d_a_nodes, m->d_a_grp, m->d_alllv, m->d_asteps,
+                                             m->d_aorder, nq, n_vec);
+    ++a->launches;
     if ((st = rec_end(a, ra, s))) return st;
+    QKC_LAUNCH_CHECK();
+    return QKC_OK;
+}
+
+// One memoised upward pass of step j over `bound` group columns (device count n_active); with
+// resident slots, its tier A was computed beforehand (memo_tierA_all).
+static qkc_status memo_pass(qkc_ac *a, qkc_ac::MemoMeta *m, int j, int clamp, int64_t n_vec,
+                            const int32_t *n_active, int64_t bound, int cur, bool resident, cudaStream_t s) {
+    qkc_status st;
+    cudaGraphExec_t gA = nullptr, gB;
+    if ((!resident && (st = memo_graph(a, m, j, false, &gA))) || (st = memo_graph(a, m, j, true, &gB))) return st;
+    set_memo_step(a, m, j, clamp, n_vec, resident, s);
+    if (!resident) {
+        const size_t ra = a->recs.size();
+        if ((st = rec_begin(a, 3, nullptr, 0, 0, s))) return st;
+        if (ra < a->recs.size()) {
+            a->recs[ra].fixed_bytes = (double)n_vec * m->a_bytes_slot[j];
+            a->recs[ra].fixed_edges = (double)n_vec * m->a_edges_slot[j];
+        }
+        QKC_CUDA(cudaGraphLaunch(gA, s));  // tier A: once per step
+        a->launches += memoA_launches(a, m, j);
+        if ((st = rec_end(a, ra, s))) return st;
+    }
     const size_t ri = a->recs.size();
     if ((st = rec_begin(a, 2, n_active, 0, bound, s))) return st;
     if (ri < a->recs.size()) {
@@ -3446,14 +3572,16 @@ static qkc_status sample_impl(qkc_ac *a, const uint64_t *seeds, const int32_t *s
         for (int cap = (int)a->memo.size() - 1; cap >= 1 && !meta; --cap)
             if (a->memo[cap] && n_vec * a->memo[cap]->max_units * (int64_t)a->elem() <= a->va_bytes) meta = a->memo[cap];
     }
+    auto memo_budget = [&]() {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); fr = 0; }
+        return a->memo_budget > 0 ? (double)a->memo_budget
+                                  : std::min(0.40 * (double)a->ctx->total_mem, 0.6 * (double)(fr + (size_t)a->va_bytes));
+    };
     if (memo_ok && !meta) {
         int ks = 0;
         while (ks < 24 && (2ll << ks) <= max_shots) ++ks;  // floor(log2(max_shots))
-        size_t fr = 0, tot = 0;
-        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); fr = 0; }
-        double budget = a->memo_budget > 0 ? (double)a->memo_budget
-                                            : std::min(0.40 * (double)a->ctx->total_mem,
-                                                       0.6 * (double)(fr + (size_t)a->va_bytes));
+        const double budget = memo_budget();
         for (int cap = ks - 1; cap >= 1 && !meta; --cap) {
             qkc_ac::MemoMeta *m = memo_meta(a, cap, &st);
             if (st) return st;
@@ -3486,6 +3614,26 @@ static qkc_status sample_impl(qkc_ac *a, const uint64_t *seeds, const int32_t *s
             groups = std::min(2.0 * groups, (double)live);
         }
         if (memo >= plain) meta = nullptr;
+    }
+    // every step's tier-A slots at once, when they fit the budget and no tier-A level is wide: the
+    // steps' tier-A passes then run concurrently in one launch before the first step
+    bool resident = false;
+    if (meta && nq > 1 && meta->all_T <= MEMO_ALL_T) {
+        const int64_t need = n_vec * meta->unit_base[nq] * (int64_t)a->elem();
+        if (need <= a->va_bytes) {
+            resident = true;
+        } else if ((double)need <= memo_budget()) {
+            void *p = nullptr;
+            if (cudaMalloc(&p, (size_t)need) == cudaSuccess) {
+                QKC_CUDA(cudaDeviceSynchronize());
+                cudaFree(a->d_VA);
+                a->d_VA = p;
+                a->va_bytes = need;
+                resident = true;
+            } else {
+                cudaGetLastError();
+            }
+        }
     }
     if (steps && (st = ensure_tile(a, std::max(n_samp, n_vec),
                                    meta ? (uint32_t)std::max<int64_t>(1, meta->max_rows) : 0u)))
@@ -3524,6 +3672,7 @@ static qkc_status sample_impl(qkc_ac *a, const uint64_t *seeds, const int32_t *s
         }
         return es;
     };
+    if (resident && (st = memo_tierA_all(a, meta, 1, n_vec, s))) return st;
     // groups before the first step (host bound); every step's pass gives both branch probabilities of
     // each group, so no pass for P(empty prefix) is needed
     const int64_t bound0 = traj ? n_vec + live : n_vec;
@@ -3532,7 +3681,7 @@ static qkc_status sample_impl(qkc_ac *a, const uint64_t *seeds, const int32_t *s
         // (P(prefix, X_j = 0), P(prefix, X_j = 1)) for every group (count on the device, bound on the host)
         int32_t *gcount = a->d_gcount + cur;
         if (meta) {
-            if ((st = memo_pass(a, meta, j, 1, n_vec, gcount, bound, cur, s))) return st;
+            if ((st = memo_pass(a, meta, j, 1, n_vec, gcount, bound, cur, resident, s))) return st;
         } else {
             for (int64_t c0 = 0; c0 < bound; c0 += a->tile) {
                 const int64_t nc = std::min<int64_t>(a->tile, bound - c0);
