@@ -1346,10 +1346,14 @@ __device__ __forceinline__ float4 rcombine(uint2 dsc, const RChild &x, const RCh
     }
     return make_float4(q0.x, q0.y, q1.x, q1.y);
 }
+// fuse bit 0: the run is the step's first tier-B launch and forms the tile's group keys itself (what
+// memo_keys does, for the lane's columns); bit 1: the run holds the step's root (tier-B row rrow on
+// level Lroot) and writes each column's root value (what memo_root does).
 __global__ void __launch_bounds__(TPB, 4) memoB_run_f32(const MemoBRunLevel *lv, int nlv, const uint2 *bdesc,
                                                       const PassDesc *pd, const MemoDesc *mdp, int64_t pitch,
                                                       float2 *__restrict__ V, int *__restrict__ S,
-                                                      int *__restrict__ obs) {
+                                                      int *__restrict__ obs, int fuse, int64_t rrow, int Lroot,
+                                                      double2 *__restrict__ out) {
     __shared__ uint2 sdesc[TPB / 32][NBB];
     __shared__ uint4 srec[TPB / 32][NBB][2];
     const int64_t ncols = desc_cols(*pd);
@@ -1371,11 +1375,28 @@ __global__ void __launch_bounds__(TPB, 4) memoB_run_f32(const MemoBRunLevel *lv,
     w.Vn = (uint32_t)mdp->V;
     w.j = j;
     w.narrow = j <= 32;
-    const uint32_t *keys = mdp->keys;
+    uint32_t *keys = mdp->keys;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int64_t nchunks = (ncols + 63) >> 6;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     float4 *V4 = reinterpret_cast<float4 *>(V);
+    if (fuse & 1) {  // the group keys of the lane's columns (the same chunks as below), per tabled support
+        const KeyPlan *bplan = mdp->bplan;
+        const int nbm = mdp->nbm;
+        const bool narrow = j <= 32;
+        for (int64_t chunk = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; chunk < nchunks; chunk += nw) {
+            const int64_t col = chunk * 64 + lane * 2;
+            if (col >= ncols) continue;
+            const bool two = col + 1 < ncols;
+            const uint64_t p0 = j ? __brevll(prefix[col0 + col] << (64 - j)) : 0ull;
+            const uint64_t p1 = two && j ? __brevll(prefix[col0 + col + 1] << (64 - j)) : 0ull;
+            for (int r = 0; r < nbm; ++r) {
+                uint32_t *kr = keys + (int64_t)r * mdp->kpitch + col;
+                kr[0] = plan_key(bplan + r, p0, narrow);
+                if (two) kr[1] = plan_key(bplan + r, p1, narrow);
+            }
+        }
+    }
     for (int64_t chunk = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; chunk < nchunks; chunk += nw) {
         const int64_t col = chunk * 64 + lane * 2;  // even, and the pitch is a multiple of 64
         const bool active = col < ncols;
@@ -1453,6 +1474,13 @@ __global__ void __launch_bounds__(TPB, 4) memoB_run_f32(const MemoBRunLevel *lv,
                     ow[0] = e0;
                 }
             }
+        }
+        if ((fuse & 2) && active) {  // the root's value in the lane's columns, unscaled to FP64
+            const float4 q = w.V4c[rrow * (int64_t)w.hp];
+            const int *sr = S + (int64_t)Lroot * pitch + col;
+            const int64_t gc = col0 + col;
+            out[gc] = make_double2(ldexp((double)q.x, sr[0]), ldexp((double)q.y, sr[0]));
+            if (w.two) out[gc + 1] = make_double2(ldexp((double)q.z, sr[1]), ldexp((double)q.w, sr[1]));
         }
     }
 }
@@ -2064,6 +2092,8 @@ struct qkc_ac {
                                         // key width, group-key table row and block offset; see BChild)
         std::vector<int64_t> br_base;   // per step: first edge record
         std::vector<int64_t> root_row;  // per step: the root's tier-B row, -1 when the root is tier A
+        std::vector<int> fuse;          // per step: its first tier-B run forms the group keys (bit 0), its
+                                        // last run writes the root values (bit 1)
         int64_t max_rows = 0;           // tier-B nodes of the largest step (rows of the value tile)
         KeyPlan *d_kplan = nullptr;     // key plans of the tier-A children of tier-B nodes, per step
         KeyPlan *d_aplan = nullptr;     // key plans of scattered child-key masks of tier-A nodes, per step
@@ -3217,6 +3247,13 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
                 }
             }
             flush();
+            int fz = 0;
+            const auto &bi = m->b_items[j];
+            if (!bi.empty() && bi.front().cnt > 0 && m->bp_cnt[j] > 0) fz |= 1;
+            if (!bi.empty() && bi.back().cnt > 0 && row_of[a->roots[j]] >= 0 &&
+                brunlv.back().L == (int32_t)a->root_lev[j])
+                fz |= 2;
+            m->fuse.push_back(fz);
         }
         {  // every tier-A level of the step, in order (memoA_all)
             MemoAStep st{m->a_base[j], m->g_base[j], (uint32_t)alllv.size(), 0u};
@@ -3359,7 +3396,7 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
     const int64_t pitch = a->tile;
     if (m->b_lvl[j][D] > 0) {
         const unsigned gs = (unsigned)((pitch + TPB - 1) / TPB);
-        if (m->bp_cnt[j] > 0) memo_keys<<<gs, TPB, 0, s>>>(a->d_desc, md_j);
+        if (m->bp_cnt[j] > 0 && !(m->fuse[j] & 1)) memo_keys<<<gs, TPB, 0, s>>>(a->d_desc, md_j);
         // FP32 scales: only levels with tier-B nodes are computed, so every level's observed
         // exponent starts empty and the scale kernel runs for those levels alone
         if (a->prec == 32 && m->rst_cnt[j] > 0)
@@ -3368,12 +3405,16 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
         const bool inline_scale = m->b_lvl[j][D] <= MEMO_INLINE_SCALE_B;
         const uint2 *bd_j = m->d_bdesc + m->b_base[j];
         const uint32_t *cl_off_j = m->d_bclo + (size_t)j * (D + 1);
-        for (const auto &it : m->b_items[j]) {
+        const size_t nit = m->b_items[j].size();
+        for (size_t ii = 0; ii < nit; ++ii) {
+            const auto &it = m->b_items[j][ii];
             if (it.cnt > 0) {  // a run of small levels (FP32): a warp per 64-column chunk walks them
                 const int64_t chunks = (pitch + 63) / 64;
                 const unsigned g = (unsigned)std::min<int64_t>((chunks + TPB / 32 - 1) / (TPB / 32), (int64_t)sms * 8);
+                const int fz = (ii == 0 ? (m->fuse[j] & 1) : 0) | (ii + 1 == nit ? (m->fuse[j] & 2) : 0);
                 memoB_run_f32<<<g, TPB, 0, s>>>(m->d_brunlv + it.off, it.cnt, bd_j, a->d_desc, md_j, pitch,
-                                                 (float2 *)a->d_V, a->d_S, a->d_obs);
+                                                 (float2 *)a->d_V, a->d_S, a->d_obs, fz, m->root_row[j],
+                                                 a->root_lev[j], a->d_root);
                 continue;
             }
             const uint32_t L = (uint32_t)it.L;
@@ -3395,15 +3436,16 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
             }
         }
     }
-    memo_root<<<(unsigned)((pitch + TPB - 1) / TPB), TPB, 0, s>>>(md_j, a->d_desc, a->roots[j], a->root_lev[j],
-                                                                  m->root_row[j], a->d_V,
-                                                                  a->d_S, pitch, a->prec == 32, a->d_root);
+    if (!(m->fuse[j] & 2))
+        memo_root<<<(unsigned)((pitch + TPB - 1) / TPB), TPB, 0, s>>>(md_j, a->d_desc, a->roots[j], a->root_lev[j],
+                                                                      m->root_row[j], a->d_V, a->d_S, pitch,
+                                                                      a->prec == 32, a->d_root);
 }
 static int64_t memoB_launches(const qkc_ac *a, const qkc_ac::MemoMeta *m, int j) {
-    int64_t n = 1;
+    int64_t n = (m->fuse[j] & 2) ? 0 : 1;
     if (m->b_lvl[j][a->D] > 0) {
         n += (a->prec == 32 && m->rst_cnt[j] > 0) ? 1 : 0;
-        n += m->bp_cnt[j] > 0;
+        n += m->bp_cnt[j] > 0 && !(m->fuse[j] & 1);
         const int per = (a->prec == 32 && m->b_lvl[j][a->D] > MEMO_INLINE_SCALE_B) ? 2 : 1;
         for (const auto &it : m->b_items[j]) n += it.cnt > 0 ? 1 : per;
     }
