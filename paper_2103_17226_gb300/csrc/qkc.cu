@@ -77,7 +77,9 @@ constexpr int64_t MEMO_ALL_T = 4096;           // every step's tier A in one lau
                                                // vector) when no tier-A level is wider than this
 constexpr int64_t MEMO_INLINE_SCALE_B = 4096;  // tier-B sets up to this size form level scales inline
 constexpr int64_t MEMO_RUN_B = NBB;            // FP32 tier-B levels of one node block (at most 32 nodes) are walked
-                                               // in runs by one launch
+                                               // in runs by one launch ...
+constexpr int MEMO_RUN_LV = 16;                // ... of at most 16 levels and 512 nodes (shared memory)
+constexpr int64_t MEMO_RUN_NODES = 512;
 constexpr int MEMO_BKEYS = 32;  // per step, the distinct tier-A child supports whose group keys are tabled
 constexpr int MEMO_APLANS = 7;  // log2 of the compress plans per step for scattered tier-A key masks
 constexpr int MEMO_MARGIN = 2;  // early steps: memoise a node when its key space is >= 4x smaller than V 2^j
@@ -1349,16 +1351,34 @@ __device__ __forceinline__ float4 rcombine(uint2 dsc, const RChild &x, const RCh
 // fuse bit 0: the run is the step's first tier-B launch and forms the tile's group keys itself (what
 // memo_keys does, for the lane's columns); bit 1: the run holds the step's root (tier-B row rrow on
 // level Lroot) and writes each column's root value (what memo_root does).
+// The block stages the whole run's node descriptors and first two edge records in shared memory once
+// (dynamic shared memory: 40 bytes per node), and each warp keeps, per run level and column, the level's
+// scale plus observed exponent there, so a level's scale reads global memory only for child levels
+// outside the run: a level then costs its nodes' child loads alone.
 __global__ void __launch_bounds__(TPB, 4) memoB_run_f32(const MemoBRunLevel *lv, int nlv, const uint2 *bdesc,
                                                       const PassDesc *pd, const MemoDesc *mdp, int64_t pitch,
                                                       float2 *__restrict__ V, int *__restrict__ S,
                                                       int *__restrict__ obs, int fuse, int64_t rrow, int Lroot,
                                                       double2 *__restrict__ out) {
-    __shared__ uint2 sdesc[TPB / 32][NBB];
-    __shared__ uint4 srec[TPB / 32][NBB][2];
+    extern __shared__ uint4 run_smem[];
+    __shared__ MemoBRunLevel slv[MEMO_RUN_LV];
     const int64_t ncols = desc_cols(*pd);
     if (ncols <= 0) return;
     const uint4 *brec = mdp->brec;
+    // the run's rows are consecutive: [base, base + ntot)
+    const uint32_t base = lv[0].b0, ntot = lv[nlv - 1].b0 + lv[nlv - 1].count - base;
+    uint4 *srec = run_smem;                                              // [ntot][2]
+    uint2 *sdesc = reinterpret_cast<uint2 *>(srec + 2 * (size_t)ntot);  // [ntot]
+    int *se = reinterpret_cast<int *>(sdesc + ntot);                     // [nlv][warps][64]
+    for (uint32_t i = threadIdx.x; i < ntot; i += blockDim.x) {
+        const uint2 d = __ldg(bdesc + base + i);
+        const uint4 r0 = __ldg(brec + d.x);
+        sdesc[i] = d;
+        srec[2 * i] = r0;
+        srec[2 * i + 1] = (d.y & 0xffffffu) >= 2u ? __ldg(brec + d.x + 1) : r0;
+    }
+    if (threadIdx.x < nlv) slv[threadIdx.x] = lv[threadIdx.x];
+    __syncthreads();
     const int64_t col0 = pd->col0;
     const int32_t *col_vec = pd->es.col_vec;
     const int64_t n_vec = pd->es.n_vec;
@@ -1380,6 +1400,8 @@ __global__ void __launch_bounds__(TPB, 4) memoB_run_f32(const MemoBRunLevel *lv,
     const int64_t nchunks = (ncols + 63) >> 6;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     float4 *V4 = reinterpret_cast<float4 *>(V);
+    int2 *se_w = reinterpret_cast<int2 *>(se) + (size_t)wp * 32 + lane;  // level l at se_w[l * warps * 32]
+    const int se_step = (TPB / 32) * 32;
     if (fuse & 1) {  // the group keys of the lane's columns (the same chunks as below), per tabled support
         const KeyPlan *bplan = mdp->bplan;
         const int nbm = mdp->nbm;
@@ -1399,9 +1421,9 @@ __global__ void __launch_bounds__(TPB, 4) memoB_run_f32(const MemoBRunLevel *lv,
     }
     for (int64_t chunk = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; chunk < nchunks; chunk += nw) {
         const int64_t col = chunk * 64 + lane * 2;  // even, and the pitch is a multiple of 64
-        const bool active = col < ncols;
+        if (col >= ncols) continue;  // the lane has no column (no barrier follows)
         w.two = col + 1 < ncols;
-        const int64_t g0 = col0 + (active ? col : 0), g1 = w.two ? g0 + 1 : g0;
+        const int64_t g0 = col0 + col, g1 = w.two ? g0 + 1 : g0;
         int64_t v0 = col_vec ? (int64_t)col_vec[g0] : g0, v1 = col_vec ? (int64_t)col_vec[g1] : g1;
         v0 = v0 < 0 ? 0 : (v0 >= n_vec ? n_vec - 1 : v0);
         v1 = v1 < 0 ? 0 : (v1 >= n_vec ? n_vec - 1 : v1);
@@ -1412,70 +1434,89 @@ __global__ void __launch_bounds__(TPB, 4) memoB_run_f32(const MemoBRunLevel *lv,
         w.Sc = S + col;
         w.Kc = keys + col;
         for (int l = 0; l < nlv; ++l) {
-            const MemoBRunLevel L = lv[l];
-            int sl0 = 0, sl1 = 0;
-            if (active) {
-                sl0 = level_scale_col(cl_off, cl, L.L, pitch, L.floor0, S, obs, col);
-                sl1 = w.two ? level_scale_col(cl_off, cl, L.L, pitch, L.floor0, S, obs, col + 1) : 0;
-            }
-            float mx0 = 0.f, mx1 = 0.f;
-            for (uint32_t kb = 0; kb < L.count; kb += NBB) {
-                const int nn = (int)min((uint32_t)NBB, L.count - kb);
-                bstage(sdesc[wp], srec[wp], bdesc + L.b0 + kb, brec, nn, lane);
-                if (!active) continue;
-                float4 *dst = w.V4c + (int64_t)(L.b0 + kb) * w.hp;
-                for (int i = 0; i < nn;) {  // two nodes at a time where both have at most two children
-                    const uint2 d0 = sdesc[wp][i];
-                    const uint2 d1 = sdesc[wp][i + 1 < nn ? i + 1 : i];
-                    const uint32_t deg0 = d0.y & 0xffffffu, deg1 = d1.y & 0xffffffu;
-                    RChild x0, y0;
-                    y0.v = make_float4(0.f, 0.f, 0.f, 0.f);
-                    y0.s = make_int2(0, 0);
-                    if (i + 1 < nn && deg0 <= 2u && deg1 <= 2u) {
-                        RChild x1, y1;
-                        y1.v = make_float4(0.f, 0.f, 0.f, 0.f);
-                        y1.s = make_int2(0, 0);
-                        rchild_issue(srec[wp][i][0], x0, w);
-                        if (deg0 == 2u) rchild_issue(srec[wp][i][1], y0, w);
-                        rchild_issue(srec[wp][i + 1][0], x1, w);
-                        if (deg1 == 2u) rchild_issue(srec[wp][i + 1][1], y1, w);
-                        rchild_slots(srec[wp][i][0], x0, w);
-                        if (deg0 == 2u) rchild_slots(srec[wp][i][1], y0, w);
-                        rchild_slots(srec[wp][i + 1][0], x1, w);
-                        if (deg1 == 2u) rchild_slots(srec[wp][i + 1][1], y1, w);
-                        const float4 q = rcombine<false>(d0, x0, y0, sl0, sl1, brec, w);
-                        const float4 p = rcombine<false>(d1, x1, y1, sl0, sl1, brec, w);
-                        dst[(int64_t)i * w.hp] = q;
-                        dst[(int64_t)(i + 1) * w.hp] = p;
-                        mx0 = fmaxf(mx0, fmaxf(fmaxf(fabsf(q.x), fabsf(q.y)), fmaxf(fabsf(p.x), fabsf(p.y))));
-                        mx1 = fmaxf(mx1, fmaxf(fmaxf(fabsf(q.z), fabsf(q.w)), fmaxf(fabsf(p.z), fabsf(p.w))));
-                        i += 2;
-                    } else {
-                        rchild_issue(srec[wp][i][0], x0, w);
-                        if (deg0 >= 2u) rchild_issue(srec[wp][i][1], y0, w);
-                        rchild_slots(srec[wp][i][0], x0, w);
-                        if (deg0 >= 2u) rchild_slots(srec[wp][i][1], y0, w);
-                        const float4 q = rcombine<true>(d0, x0, y0, sl0, sl1, brec, w);
-                        dst[(int64_t)i * w.hp] = q;
-                        mx0 = fmaxf(mx0, fmaxf(fabsf(q.x), fabsf(q.y)));
-                        mx1 = fmaxf(mx1, fmaxf(fabsf(q.z), fabsf(q.w)));
-                        i += 1;
-                    }
-                }
-            }
-            if (active) {
-                int *sw = S + (int64_t)L.L * pitch + col, *ow = obs + (int64_t)L.L * pitch + col;
-                const int e0 = (__float_as_int(mx0) >> 23) - 127, e1 = (__float_as_int(mx1) >> 23) - 127;
-                if (w.two) {
-                    *reinterpret_cast<int2 *>(sw) = make_int2(sl0, sl1);
-                    *reinterpret_cast<int2 *>(ow) = make_int2(e0, e1);
+            const MemoBRunLevel L = slv[l];
+            // the level's scale (the rule of level_scale_col): child levels of this run from shared
+            // memory, the others from their scale and observed-exponent words
+            int s0 = INT_MIN, s1 = INT_MIN;
+            for (uint32_t k = __ldg(cl_off + L.L), k1 = __ldg(cl_off + L.L + 1); k < k1; ++k) {
+                const int Lp = __ldg(cl + k);
+                int r = l - 1;
+                while (r >= 0 && slv[r].L != Lp) --r;
+                if (r >= 0) {
+                    const int2 e = se_w[r * se_step];
+                    s0 = max(s0, e.x);
+                    s1 = max(s1, e.y);
                 } else {
-                    sw[0] = sl0;
-                    ow[0] = e0;
+                    const int2 o = *reinterpret_cast<const int2 *>(obs + (int64_t)Lp * pitch + col);
+                    const int2 sc = *reinterpret_cast<const int2 *>(S + (int64_t)Lp * pitch + col);
+                    if (o.x != OBS_EMPTY) s0 = max(s0, sc.x + o.x);
+                    if (o.y != OBS_EMPTY) s1 = max(s1, sc.y + o.y);
                 }
+            }
+            if (s0 == INT_MIN) s0 = 0;
+            if (s1 == INT_MIN) s1 = 0;
+            if (L.floor0) {
+                s0 = max(s0, 0);
+                s1 = max(s1, 0);
+            }
+            if (!w.two) s1 = 0;
+            const int sl0 = s0, sl1 = s1;
+            float mx0 = 0.f, mx1 = 0.f;
+            const uint32_t r0 = L.b0 - base;
+            float4 *dst = w.V4c + (int64_t)L.b0 * w.hp;
+            const int nn = (int)L.count;
+            for (int i = 0; i < nn;) {  // two nodes at a time where both have at most two children
+                const uint2 d0 = sdesc[r0 + i];
+                const uint2 d1 = sdesc[r0 + (i + 1 < nn ? i + 1 : i)];
+                const uint32_t deg0 = d0.y & 0xffffffu, deg1 = d1.y & 0xffffffu;
+                const uint4 *q0r = srec + 2 * (size_t)(r0 + i);
+                RChild x0, y0;
+                y0.v = make_float4(0.f, 0.f, 0.f, 0.f);
+                y0.s = make_int2(0, 0);
+                if (i + 1 < nn && deg0 <= 2u && deg1 <= 2u) {
+                    const uint4 *q1r = q0r + 2;
+                    RChild x1, y1;
+                    y1.v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    y1.s = make_int2(0, 0);
+                    rchild_issue(q0r[0], x0, w);
+                    if (deg0 == 2u) rchild_issue(q0r[1], y0, w);
+                    rchild_issue(q1r[0], x1, w);
+                    if (deg1 == 2u) rchild_issue(q1r[1], y1, w);
+                    rchild_slots(q0r[0], x0, w);
+                    if (deg0 == 2u) rchild_slots(q0r[1], y0, w);
+                    rchild_slots(q1r[0], x1, w);
+                    if (deg1 == 2u) rchild_slots(q1r[1], y1, w);
+                    const float4 q = rcombine<false>(d0, x0, y0, sl0, sl1, brec, w);
+                    const float4 p = rcombine<false>(d1, x1, y1, sl0, sl1, brec, w);
+                    dst[(int64_t)i * w.hp] = q;
+                    dst[(int64_t)(i + 1) * w.hp] = p;
+                    mx0 = fmaxf(mx0, fmaxf(fmaxf(fabsf(q.x), fabsf(q.y)), fmaxf(fabsf(p.x), fabsf(p.y))));
+                    mx1 = fmaxf(mx1, fmaxf(fmaxf(fabsf(q.z), fabsf(q.w)), fmaxf(fabsf(p.z), fabsf(p.w))));
+                    i += 2;
+                } else {
+                    rchild_issue(q0r[0], x0, w);
+                    if (deg0 >= 2u) rchild_issue(q0r[1], y0, w);
+                    rchild_slots(q0r[0], x0, w);
+                    if (deg0 >= 2u) rchild_slots(q0r[1], y0, w);
+                    const float4 q = rcombine<true>(d0, x0, y0, sl0, sl1, brec, w);
+                    dst[(int64_t)i * w.hp] = q;
+                    mx0 = fmaxf(mx0, fmaxf(fabsf(q.x), fabsf(q.y)));
+                    mx1 = fmaxf(mx1, fmaxf(fabsf(q.z), fabsf(q.w)));
+                    i += 1;
+                }
+            }
+            int *sw = S + (int64_t)L.L * pitch + col, *ow = obs + (int64_t)L.L * pitch + col;
+            const int e0 = (__float_as_int(mx0) >> 23) - 127, e1 = (__float_as_int(mx1) >> 23) - 127;
+            se_w[l * se_step] = make_int2(sl0 + e0, sl1 + e1);
+            if (w.two) {
+                *reinterpret_cast<int2 *>(sw) = make_int2(sl0, sl1);
+                *reinterpret_cast<int2 *>(ow) = make_int2(e0, e1);
+            } else {
+                sw[0] = sl0;
+                ow[0] = e0;
             }
         }
-        if ((fuse & 2) && active) {  // the root's value in the lane's columns, unscaled to FP64
+        if (fuse & 2) {  // the root's value in the lane's columns, unscaled to FP64
             const float4 q = w.V4c[rrow * (int64_t)w.hp];
             const int *sr = S + (int64_t)Lroot * pitch + col;
             const int64_t gc = col0 + col;
@@ -1483,6 +1524,10 @@ __global__ void __launch_bounds__(TPB, 4) memoB_run_f32(const MemoBRunLevel *lv,
             if (w.two) out[gc + 1] = make_double2(ldexp((double)q.z, sr[1]), ldexp((double)q.w, sr[1]));
         }
     }
+}
+// Dynamic shared memory of a run of nlv levels and ntot nodes.
+static size_t run_smem_bytes(int nlv, int64_t ntot) {
+    return (size_t)ntot * (2 * sizeof(uint4) + sizeof(uint2)) + (size_t)nlv * (TPB / 32) * 32 * sizeof(int2);
 }
 
 // One level of tier B (FP64, unscaled).
@@ -2068,7 +2113,8 @@ struct qkc_ac {
         int64_t all_T = 0;                  // the largest threads per vector of any tier-A level
         std::vector<std::vector<int64_t>> a_lvl, u_lvl, b_lvl, g_lvl;  // per step, [D + 1]
         std::vector<std::vector<int64_t>> t_lvl;                        // per step and level: tier-A threads
-        struct AItem { int L; int64_t off; int cnt; };  // one tier-A launch: level L, or a run of cnt levels
+        struct AItem { int L; int64_t off; int cnt; int64_t nodes = 0; };  // one launch: level L, or a run of
+                                                                         // cnt levels (tier B: of `nodes` nodes)
         std::vector<std::vector<AItem>> a_items;        // per step, in level order
         MemoARunLevel *d_runlv = nullptr;               // the runs' levels, all steps
         std::vector<std::vector<AItem>> b_items;        // per step: tier-B launches (a level, or a run of cnt levels)
@@ -2152,6 +2198,13 @@ extern "C" qkc_status qkc_ctx_create(int device, qkc_ctx **out) {
         c->memoB_blocks_per_sm < 1) {
         cudaGetLastError();
         c->memoB_blocks_per_sm = 4;
+    }
+    // tier-B runs stage up to MEMO_RUN_NODES nodes and MEMO_RUN_LV levels in dynamic shared memory
+    if (cudaFuncSetAttribute(memoB_run_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)run_smem_bytes(MEMO_RUN_LV, MEMO_RUN_NODES)) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return fail(QKC_ERR_CUDA, "qkc_ctx_create: cannot size the shared memory of the tier-B run kernel");
     }
     *out = c;
     return QKC_OK;
@@ -3222,11 +3275,13 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
             m->t_lvl[j][L] = th;
         }
         m->bp_cnt.push_back((int64_t)bplan.size() - m->bp_base[j]);
-        {  // tier-B launches: consecutive small levels form one run (FP32: a warp per 32-column chunk walks them)
+        {  // tier-B launches: consecutive small levels form one run (FP32: a warp per 64-column chunk walks
+           // them), of at most MEMO_RUN_LV levels and MEMO_RUN_NODES nodes
             std::vector<uint32_t> pend;
+            int64_t pend_nodes = 0;
             auto flush = [&]() {
                 if (pend.size() >= 2) {
-                    m->b_items[j].push_back({-1, (int64_t)brunlv.size(), (int)pend.size()});
+                    m->b_items[j].push_back({-1, (int64_t)brunlv.size(), (int)pend.size(), pend_nodes});
                     for (uint32_t L : pend)
                         brunlv.push_back(MemoBRunLevel{(uint32_t)m->b_lvl[j][L],
                                                        (uint32_t)(m->b_lvl[j][L + 1] - m->b_lvl[j][L]), (int32_t)L,
@@ -3235,12 +3290,15 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
                     m->b_items[j].push_back({(int)pend[0], 0, 0});
                 }
                 pend.clear();
+                pend_nodes = 0;
             };
             for (uint32_t L = 1; L < D; ++L) {
                 const int64_t cnt = m->b_lvl[j][L + 1] - m->b_lvl[j][L];
                 if (cnt == 0) continue;
                 if (a->prec == 32 && cnt <= MEMO_RUN_B) {
+                    if ((int)pend.size() == MEMO_RUN_LV || pend_nodes + cnt > MEMO_RUN_NODES) flush();
                     pend.push_back(L);
+                    pend_nodes += cnt;
                 } else {
                     flush();
                     m->b_items[j].push_back({(int)L, 0, 0});
@@ -3412,7 +3470,8 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
                 const int64_t chunks = (pitch + 63) / 64;
                 const unsigned g = (unsigned)std::min<int64_t>((chunks + TPB / 32 - 1) / (TPB / 32), (int64_t)sms * 8);
                 const int fz = (ii == 0 ? (m->fuse[j] & 1) : 0) | (ii + 1 == nit ? (m->fuse[j] & 2) : 0);
-                memoB_run_f32<<<g, TPB, 0, s>>>(m->d_brunlv + it.off, it.cnt, bd_j, a->d_desc, md_j, pitch,
+                memoB_run_f32<<<g, TPB, run_smem_bytes(it.cnt, it.nodes), s>>>(m->d_brunlv + it.off, it.cnt, bd_j,
+                                                                                a->d_desc, md_j, pitch,
                                                  (float2 *)a->d_V, a->d_S, a->d_obs, fz, m->root_row[j],
                                                  a->root_lev[j], a->d_root);
                 continue;
