@@ -101,8 +101,15 @@ enum { QKC_ORDER_AUTO = 0, QKC_ORDER_MINFILL = 1, QKC_ORDER_MINWEIGHT = 2, QKC_O
  * construction; it is this library's answer to its sampling cost.  Supported
  * by qkc_evaluate (the last root: the whole circuit) and qkc_sample only.
  *
- * `order` is one of QKC_ORDER_*; `max_nodes` bounds the AC (0 = 2^31-1), above
- * it QKC_ERR_TOO_LARGE.  On success *out_bytes is a malloc'd buffer in the
+ * `order` is one of QKC_ORDER_*; `max_nodes` bounds the node store during
+ * compilation (0 = 2^31-1; intermediate nodes the final AC drops count too),
+ * above it QKC_ERR_TOO_LARGE.  QKC_ORDER_AUTO eliminates each circuit with
+ * min-fill and with min-weight on copies of the node store and keeps the order
+ * that adds fewer nodes (their table-size estimates ignore sharing and dropped
+ * zero entries and can be off severalfold); for DENSITY_STEPS it also compiles
+ * the whole AC with min-fill and with min-weight throughout and returns the
+ * smaller of those two when it has at least 10% fewer nodes (so it costs up to
+ * about five compilations).  On success *out_bytes is a malloc'd buffer in the
  * compiled-AC format below; release it with qkc_free_bytes.
  */
 qkc_status qkc_compile(const qkc_op *ops, int32_t n_ops, int32_t n_qubits, int32_t n_angles,
@@ -111,8 +118,10 @@ qkc_status qkc_compile(const qkc_op *ops, int32_t n_ops, int32_t n_qubits, int32
 void qkc_free_bytes(uint8_t *bytes);
 
 /*
- * qkc_plan -- the elimination order qkc_compile would use, without building
- * nodes: *table_entries = sum over eliminated variables of the product of the
+ * qkc_plan -- an elimination order's estimate, without building nodes (for
+ * QKC_ORDER_AUTO: the order with the smaller estimate, which qkc_compile then
+ * checks against the other by building both): *table_entries = sum over
+ * eliminated variables of the product of the
  * cardinalities of the variable and its neighbours (about the node count), and
  * *max_log2_table = log2 of the largest such table (the order's width in bits).
  * Lets a caller reject a circuit whose AC would not fit before compiling it.
