@@ -298,3 +298,22 @@ def test_light_cone_steps_shrink_early_steps():
     sizes = [reach(roots[j]) for j in (0, 8, 14, 31)]
     assert sizes[0] < sizes[1] < sizes[2] < sizes[3]
     assert sizes[2] * 10 < sizes[3]
+
+
+def test_auto_order_takes_the_order_with_fewer_nodes():
+    """The automatic elimination order builds min-fill and min-weight and keeps the one that adds fewer
+    nodes (the table-size estimates can be off severalfold): on a 12-qubit noisy QAOA of the serving mix
+    it is never larger than either fixed order; a step AC may take either order throughout when that
+    saves at least 10%.  The AUTO AC still gives the density matrix's probabilities."""
+    from paper_2103_17226_gb300 import native as N
+    c = I.qaoa_maxcut(12, I.random_regular_graph(12, 3, seed=52), 1, I.NOISE_CFG2, name="q12")
+    size = {o: N.header(compile_ac(c, kind=1, order=o))["n_nodes"] for o in (0, 1, 2)}
+    assert size[0] <= min(size[1], size[2]), size
+    steps = {o: N.header(compile_ac(c, kind=2, order=o))["n_nodes"] for o in (0, 1, 2)}
+    assert steps[0] <= min(steps[1], steps[2]) / 0.9, steps
+    c6 = I.random_circuit(6, 24, seed=907, noise_prob=0.4)
+    ang = I.uniform_angles(1, c6.n_angles, seed=7)[0]
+    P = Q.probabilities(c6, ang)
+    r = R.ACRef(compile_ac(c6, kind=1, order=0))
+    for x in range(64):
+        assert abs(r.up(ang, outcome_ev(x, 6)) - P[x]) < 1e-13

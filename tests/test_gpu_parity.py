@@ -506,6 +506,35 @@ def test_vqe_ising_gradient(cuda_ctx):
 
 
 @pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("name", ["vqe_ising_5x5_ideal", "vqe_ising_3x3_noisy"])
+def test_memoised_step_sampler_equals_per_group_vqe(cuda_ctx, prec, name):
+    """The 2D-Ising VQE step ACs put most of tier B in runs of small levels (chains of 15-20 levels of
+    1-8 nodes per step, split into runs of at most 16 levels), with the group keys and root values
+    formed inside the runs, and (25 qubits) every step's tier A in one launch: the memoised samples
+    equal the per-group sampler's exactly, with ragged shot counts, and their probabilities agree to
+    rounding (the two paths' kernels may round products and sums differently)."""
+    c = I.workload(name)
+    b = compiled(name, N().QKC_AC_DENSITY_STEPS)
+    V, S = 6, 600
+    angs = I.uniform_angles(V, c.n_angles, seed=23)
+    seeds = t(I.vector_seeds(V, 23).astype(np.int64))
+    shots = t(np.array([S, 1, S - 11, 97, S // 2, 2], dtype=np.int32))
+    outs, probs = [], []
+    for mode in (0, 2):  # per group, memoised whenever it fits
+        ac = N().load_ac(cuda_ctx, b, precision=prec)
+        N().set_sampler(ac, mode)
+        N().set_params(ac, t(angs))
+        o, pr = N().sample_probs(ac, seeds, shots, S)
+        N().check_status(ac)
+        outs.append(o.cpu().numpy())
+        probs.append(pr.cpu().numpy())
+    sh = shots.cpu().numpy()
+    for v in range(V):
+        assert np.array_equal(outs[0][v, :sh[v]], outs[1][v, :sh[v]]), v
+        assert np.allclose(probs[1][v, :sh[v]], probs[0][v, :sh[v]], rtol=1e-12 if prec == 64 else 2e-6, atol=0), v
+
+
+@pytest.mark.parametrize("prec", [64, 32])
 @pytest.mark.parametrize("name", ["qaoa4_ring_p1", "random6", "qaoa32_3reg_p1_ideal"])
 def test_light_cone_step_sampler(cuda_ctx, prec, name):
     """A light-cone step AC (root j: the density AC of the backward light cone of qubits <= j)
