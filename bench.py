@@ -59,10 +59,11 @@ def parse():
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
     ap.add_argument("--shots", type=int, default=None, help="samples per vector (qaoa32: 10000, vqe: 1000)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["step", "uppass", "gradpass", "samplepass", "reeval"], default="step",
+    ap.add_argument("--mode", choices=["step", "uppass", "gradpass", "samplepass", "reeval", "serveacs"], default="step",
                     help="uppass: only the upward pass over --columns sampling-prefix columns; gradpass: "
                          "upward + downward pass (gradient) over --columns Z-string columns; samplepass: one "
-                         "sampling call over --vectors vectors x --shots shots (profiling cases)")
+                         "sampling call over --vectors vectors x --shots shots; serveacs: each AC of the serving "
+                         "mix alone (profiling cases)")
     ap.add_argument("--vectors", type=int, default=16, help="samplepass: parameter vectors")
     ap.add_argument("--columns", type=int, default=2048)
     ap.add_argument("--tile", type=int, default=0, help="cap the column tile (0: library default)")
@@ -873,6 +874,65 @@ def run_uppass(args):
                       "up_gbs": st["up_bytes"] / (st["up_ms"] * 1e6), "launches": st["launches"]}), flush=True)
 
 
+def serve_circuits():
+    """The serving mix: noisy QAOA p=1 on 8, 12, 16 and 20 qubits (two random 3-regular graphs at 12, 16 and
+    20; density ACs) and p=2 on 8 qubits (TRAJECTORY AC), noise as config 2."""
+    from paper_2103_17226_gb300 import inputs as I, native as N
+    circs, kinds = {}, {}
+    for n in (8, 12, 16, 20):
+        for g in ((0,) if n == 8 else (0, 1)):
+            k = f"qaoa{n}_p1_g{g}"
+            circs[k] = I.qaoa_maxcut(n, I.random_regular_graph(n, 3, seed=40 + n + 100 * g), 1, I.NOISE_CFG2, name=k)
+            kinds[k] = N.QKC_AC_DENSITY
+    circs["qaoa8_p2"] = I.qaoa_maxcut(8, I.random_regular_graph(8, 3, seed=48), 2, I.NOISE_CFG2, name="qaoa8_p2")
+    kinds["qaoa8_p2"] = N.QKC_AC_TRAJECTORY
+    return circs, kinds
+
+
+def run_serveacs(args):
+    """Profiling case for the serving mix: each AC alone, one sampling call of 32 requests x 2150 shots (the
+    mix's mean) as the serving bench makes them (FP32, 8192-column tiles, 2 GB memo budget; light-cone step
+    ACs for p=1), timed with CUDA events over three calls; one JSON line per AC with its samples/s and its
+    memoised tiers' (or per-group passes') algorithmic GB/s."""
+    import torch
+    from paper_2103_17226_gb300.build import build_library
+    build_library()
+    from paper_2103_17226_gb300 import inputs as I, native as N
+    circs, kinds = serve_circuits()
+    ctx = N.Context(0)
+    dev = torch.device("cuda", 0)
+    V, S = 32, 2150
+    for k, c in circs.items():
+        kind = N.QKC_AC_DENSITY_STEPS if kinds[k] == N.QKC_AC_DENSITY else kinds[k]
+        b = N.compile(c, kind)
+        ac = N.load_ac(ctx, b, precision=32)
+        N.set_tile_limit(ac, 8192)
+        N.set_sampler(ac, 1, 2 << 30)
+        N.set_params(ac, torch.tensor(I.uniform_angles(V, c.n_angles, seed=1), device=dev))
+        seeds = torch.tensor(I.vector_seeds(V, 3).astype(np.int64), device=dev)
+        shots = torch.full((V,), S, dtype=torch.int32, device=dev)
+        N.sample(ac, seeds, shots, S)  # warm-up: scratch, memoised metadata, graphs
+        torch.cuda.synchronize()
+        N.stats_enable(ac, True, 1 << 16)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            N.sample(ac, seeds, shots, S)
+        e1.record()
+        torch.cuda.synchronize()
+        st = N.get_stats(ac)
+        ms = e0.elapsed_time(e1) / 3
+        b_ms = st["memo_ms"] - st["memo_a_ms"]
+        print(json.dumps({"mode": "serveacs", "ac": k, "kind": "steps" if kind == N.QKC_AC_DENSITY_STEPS else "trajectory",
+                          "nodes": N.header(b)["n_nodes"], "vectors": V, "shots": S, "ms_per_call": ms,
+                          "samples_per_s": V * S / ms * 1e3,
+                          "tier_a_gbs": st["memo_a_bytes"] / (st["memo_a_ms"] * 1e6) if st["memo_a_ms"] > 0 else None,
+                          "tier_b_gbs": (st["memo_bytes"] - st["memo_a_bytes"]) / (b_ms * 1e6) if b_ms > 0 else None,
+                          "up_gbs": st["up_bytes"] / (st["up_ms"] * 1e6) if st["up_ms"] > 0 else None}), flush=True)
+        del ac
+        torch.cuda.empty_cache()
+
+
 def run_serve(args):
     """Serving: Poisson arrivals over 8 resident noisy-QAOA ACs (1q depolarising 0.001, 2q depolarising 0.01 after
     every gate): p=1 on 8, 12, 16 and 20 qubits (two random 3-regular graphs at 12, 16 and 20) as density ACs, and
@@ -887,14 +947,7 @@ def run_serve(args):
     build_library()
     from paper_2103_17226_gb300 import inputs as I, native as N
     from paper_2103_17226_gb300.serve import Server, poisson_requests
-    circs, kinds = {}, {}
-    for n in (8, 12, 16, 20):
-        for g in ((0,) if n == 8 else (0, 1)):
-            k = f"qaoa{n}_p1_g{g}"
-            circs[k] = I.qaoa_maxcut(n, I.random_regular_graph(n, 3, seed=40 + n + 100 * g), 1, I.NOISE_CFG2, name=k)
-            kinds[k] = N.QKC_AC_DENSITY
-    circs["qaoa8_p2"] = I.qaoa_maxcut(8, I.random_regular_graph(8, 3, seed=48), 2, I.NOISE_CFG2, name="qaoa8_p2")
-    kinds["qaoa8_p2"] = N.QKC_AC_TRAJECTORY
+    circs, kinds = serve_circuits()
     acs = {k: N.compile(c, kinds[k]) for k, c in circs.items()}
     # ours samples p=1 from the light-cone step ACs (--sampler lightcone, the default) or the density ACs
     ours = {k: (N.compile(c, N.QKC_AC_DENSITY_STEPS) if args.sampler == "lightcone" and kinds[k] == N.QKC_AC_DENSITY
@@ -982,6 +1035,9 @@ def main():
     args = parse()
     if args.workload == "gibbs_kl":
         run_gibbs_kl(args)
+        return
+    if args.mode == "serveacs":
+        run_serveacs(args)
         return
     if args.workload == "serve":
         run_serve(args)

@@ -74,7 +74,8 @@ constexpr int OBS_EMPTY = -1000;
 constexpr int64_t MEMO_RUN_T = 1024;           // tier-A levels with at most this many threads per vector
                                                // are walked in runs by one launch
 constexpr int64_t MEMO_ALL_T = 4096;           // every step's tier A in one launch (a block per step and
-                                               // vector) when no tier-A level is wider than this
+                                               // vector) when no tier-A level is wider than this, else
+                                               // a launch per level index
 constexpr int64_t MEMO_INLINE_SCALE_B = 4096;  // tier-B sets up to this size form level scales inline
 constexpr int64_t MEMO_RUN_B = NBB;            // FP32 tier-B levels of one node block (at most 32 nodes) are walked
                                                // in runs by one launch ...
@@ -935,6 +936,47 @@ __global__ void __launch_bounds__(TPB) memoA_all(DevAC ac, const MemoDesc *mdesc
                               vec, t);
             __syncthreads();
         }
+    }
+}
+
+// Every step's tier A at once when some tier-A level is too wide for memoA_all: a launch per level
+// index covers that level in every step that has tier-A nodes there (levels in increasing order, so a
+// slot's children are done), grid-striding over (step, vector, thread block) items like memoA_level.
+// The steps' memo descriptors are staged in shared memory.  A step's levels then no longer wait on one
+// another's launches step by step: D launches replace a launch per (step, tier-A item).
+struct MemoALvlStep {
+    int64_t node_off, grp_off, u0;  // the step's first tier-A node and group of the level, first unit
+    uint32_t T, ng;                 // threads per vector, groups
+    int32_t j, pad;                 // the step
+};
+constexpr int MEMO_LVL_STEPS = 64;  // steps per level (a memoised AC has at most 63 qubits)
+template <typename C>
+__global__ void __launch_bounds__(TPB, sizeof(C) == 8 ? 8 : 1) memoA_lvl_all(DevAC ac, const MemoDesc *mdesc,
+                                                                            const uint32_t *nodes,
+                                                                            const MemoAGroup *grp,
+                                                                            const MemoALvlStep *ls, int nls) {
+    __shared__ MemoDesc smd[MEMO_LVL_STEPS];
+    __shared__ int64_t pre[MEMO_LVL_STEPS + 1];  // block items before each step's
+    for (int i = threadIdx.x; i < nls; i += blockDim.x) smd[i] = mdesc[ls[i].j];
+    __syncthreads();
+    const int64_t V = smd[0].V;
+    if (threadIdx.x == 0) {
+        pre[0] = 0;
+        for (int i = 0; i < nls; ++i) pre[i + 1] = pre[i] + V * (int64_t)((ls[i].T + TPB - 1) / TPB);
+    }
+    __syncthreads();
+    const int64_t items = pre[nls];
+    int s = 0;
+    for (int64_t b = blockIdx.x; b < items; b += gridDim.x) {
+        while (pre[s + 1] <= b) ++s;  // items only grow along the loop
+        const MemoALvlStep L = ls[s];
+        const uint32_t nblk = (L.T + TPB - 1) / TPB;
+        const int64_t r = b - pre[s];
+        const int64_t vec = r / nblk;
+        const uint32_t t = (uint32_t)(r - vec * nblk) * TPB + threadIdx.x;
+        if (t < L.T)
+            memoA_slot<C>(ac, smd[s], static_cast<C *>(smd[s].VA), nodes + L.node_off, grp + L.grp_off, (int)L.ng,
+                          L.u0, vec, t);
     }
 }
 
@@ -2108,6 +2150,8 @@ struct qkc_ac {
         int64_t max_units = 0;
         std::vector<int64_t> unit_base{0};  // per step: its first unit when every step's slots are resident
         MemoARunLevel *d_alllv = nullptr;   // every step's tier-A levels (memoA_all)
+        MemoALvlStep *d_lvs = nullptr;      // per level, the steps with tier-A nodes there (memoA_lvl_all)
+        std::vector<int64_t> lvs_off;       // [D + 1] offsets into d_lvs
         MemoAStep *d_asteps = nullptr;      // per step: its bases and levels in d_alllv
         int32_t *d_aorder = nullptr;        // the steps by tier-A work, largest first
         int64_t all_T = 0;                  // the largest threads per vector of any tier-A level
@@ -2258,7 +2302,7 @@ extern "C" void qkc_free_ac(qkc_ac *a) {
     for (auto *m : a->memo) {
         if (!m) continue;
         cudaFree(m->d_a_nodes); cudaFree(m->d_a_grp); cudaFree(m->d_offu);
-        cudaFree(m->d_emask); cudaFree(m->d_runlv); cudaFree(m->d_brunlv); cudaFree(m->d_rst); cudaFree(m->d_alllv); cudaFree(m->d_asteps); cudaFree(m->d_aorder); cudaFree(m->d_bclo); cudaFree(m->d_bcl); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
+        cudaFree(m->d_emask); cudaFree(m->d_runlv); cudaFree(m->d_brunlv); cudaFree(m->d_rst); cudaFree(m->d_alllv); cudaFree(m->d_lvs); cudaFree(m->d_asteps); cudaFree(m->d_aorder); cudaFree(m->d_bclo); cudaFree(m->d_bcl); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
         for (auto &g : m->gA) if (g.exec) cudaGraphExecDestroy(g.exec);
         for (auto &g : m->gB) if (g.exec) cudaGraphExecDestroy(g.exec);
         delete m;
@@ -3382,6 +3426,17 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
         *st = QKC_OK;
         return nullptr;
     }
+    std::vector<MemoALvlStep> lvs;  // per level, the steps with tier-A nodes there (memoA_lvl_all)
+    m->lvs_off.assign(1, 0);
+    for (uint32_t L = 0; L < D; ++L) {
+        for (int j = 0; j < nq; ++j) {
+            if (m->a_lvl[j][L + 1] == m->a_lvl[j][L]) continue;
+            lvs.push_back(MemoALvlStep{m->a_base[j] + m->a_lvl[j][L], m->g_base[j] + m->g_lvl[j][L], m->u_lvl[j][L],
+                                       (uint32_t)m->t_lvl[j][L],
+                                       (uint32_t)(m->g_lvl[j][L + 1] - m->g_lvl[j][L]), (int32_t)j, 0});
+        }
+        m->lvs_off.push_back((int64_t)lvs.size());
+    }
     std::vector<int32_t> aorder(nq);  // steps by tier-A work, largest first (memoA_all)
     for (int j = 0; j < nq; ++j) aorder[j] = j;
     std::stable_sort(aorder.begin(), aorder.end(),
@@ -3396,6 +3451,7 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
         (*st = upload(&m->d_rst, rst.data(), rst.size(), dummy)) ||
         (*st = upload(&m->d_bclo, bclo.data(), bclo.size(), dummy)) ||
         (*st = upload(&m->d_alllv, alllv.data(), alllv.size(), dummy)) ||
+        (*st = upload(&m->d_lvs, lvs.data(), lvs.size(), dummy)) ||
         (*st = upload(&m->d_asteps, asteps.data(), asteps.size(), dummy)) ||
         (*st = upload(&m->d_aorder, aorder.data(), aorder.size(), dummy)) ||
         (*st = upload(&m->d_bcl, bcl.data(), bcl.size(), dummy)) ||
@@ -3405,7 +3461,7 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
         (*st = upload(&m->d_aplan, aplan.data(), aplan.size(), dummy)) ||
         (*st = upload(&m->d_bplan, bplan.data(), bplan.size(), dummy))) {
         cudaFree(m->d_a_nodes); cudaFree(m->d_a_grp); cudaFree(m->d_offu);
-        cudaFree(m->d_emask); cudaFree(m->d_runlv); cudaFree(m->d_brunlv); cudaFree(m->d_rst); cudaFree(m->d_alllv); cudaFree(m->d_asteps); cudaFree(m->d_aorder); cudaFree(m->d_bclo); cudaFree(m->d_bcl); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
+        cudaFree(m->d_emask); cudaFree(m->d_runlv); cudaFree(m->d_brunlv); cudaFree(m->d_rst); cudaFree(m->d_alllv); cudaFree(m->d_lvs); cudaFree(m->d_asteps); cudaFree(m->d_aorder); cudaFree(m->d_bclo); cudaFree(m->d_bcl); cudaFree(m->d_bdesc); cudaFree(m->d_brec); cudaFree(m->d_kplan); cudaFree(m->d_aplan); cudaFree(m->d_bplan);
         delete m;
         return nullptr;
     }
@@ -3561,8 +3617,9 @@ static void set_memo_step(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, int clamp
     ++a->launches;
 }
 
-// The tier-A passes of every step at once (their slots resident side by side): memoA_all, a block
-// per (step, vector), after every step's memo descriptor is set.
+// The tier-A passes of every step at once (their slots resident side by side), after every step's
+// memo descriptor is set: memoA_all (a block per step and vector) when no tier-A level is wider than
+// MEMO_ALL_T threads per vector, else memoA_lvl_all per level index.
 static qkc_status memo_tierA_all(qkc_ac *a, qkc_ac::MemoMeta *m, int clamp, int64_t n_vec, cudaStream_t s) {
     const int nq = (int)a->n_qubits;
     qkc_status st;
@@ -3576,14 +3633,29 @@ static qkc_status memo_tierA_all(qkc_ac *a, qkc_ac::MemoMeta *m, int clamp, int6
         }
     }
     const DevAC d = a->dev();
-    const unsigned g = (unsigned)std::min<int64_t>((int64_t)nq * n_vec, (int64_t)a->ctx->sm_count * 8);
-    if (a->prec == 32)
-        memoA_all<float2><<<g, TPB, 0, s>>>(d, a->d_mdesc, m->d_a_nodes, m->d_a_grp, m->d_alllv, m->d_asteps,
-                                            m->d_aorder, nq, n_vec);
-    else
-        memoA_all<double2><<<g, TPB, 0, s>>>(d, a->d_mdesc, m->d_a_nodes, m->d_a_grp, m->d_alllv, m->d_asteps,
-                                             m->d_aorder, nq, n_vec);
-    ++a->launches;
+    if (m->all_T <= MEMO_ALL_T) {
+        const unsigned g = (unsigned)std::min<int64_t>((int64_t)nq * n_vec, (int64_t)a->ctx->sm_count * 8);
+        if (a->prec == 32)
+            memoA_all<float2><<<g, TPB, 0, s>>>(d, a->d_mdesc, m->d_a_nodes, m->d_a_grp, m->d_alllv, m->d_asteps,
+                                                m->d_aorder, nq, n_vec);
+        else
+            memoA_all<double2><<<g, TPB, 0, s>>>(d, a->d_mdesc, m->d_a_nodes, m->d_a_grp, m->d_alllv, m->d_asteps,
+                                                 m->d_aorder, nq, n_vec);
+        ++a->launches;
+    } else {
+        const unsigned g = (unsigned)(a->ctx->sm_count * 16);
+        for (uint32_t L = 0; L < a->D; ++L) {
+            const int64_t o0 = m->lvs_off[L], cnt = m->lvs_off[L + 1] - o0;
+            if (cnt == 0) continue;
+            if (a->prec == 32)
+                memoA_lvl_all<float2><<<g, TPB, 0, s>>>(d, a->d_mdesc, m->d_a_nodes, m->d_a_grp, m->d_lvs + o0,
+                                                        (int)cnt);
+            else
+                memoA_lvl_all<double2><<<g, TPB, 0, s>>>(d, a->d_mdesc, m->d_a_nodes, m->d_a_grp, m->d_lvs + o0,
+                                                         (int)cnt);
+            ++a->launches;
+        }
+    }
     if ((st = rec_end(a, ra, s))) return st;
     QKC_LAUNCH_CHECK();
     return QKC_OK;
@@ -3716,10 +3788,10 @@ static qkc_status sample_impl(qkc_ac *a, const uint64_t *seeds, const int32_t *s
         }
         if (memo >= plain) meta = nullptr;
     }
-    // every step's tier-A slots at once, when they fit the budget and no tier-A level is wide: the
-    // steps' tier-A passes then run concurrently in one launch before the first step
+    // every step's tier-A slots at once, when they fit the budget: the steps' tier-A passes then run
+    // concurrently before the first step (one launch, or one per level index when a level is wide)
     bool resident = false;
-    if (meta && nq > 1 && meta->all_T <= MEMO_ALL_T) {
+    if (meta && nq > 1) {
         const int64_t need = n_vec * meta->unit_base[nq] * (int64_t)a->elem();
         if (need <= a->va_bytes) {
             resident = true;
