@@ -102,6 +102,15 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 
+// Programmatic dependent launch: a kernel of the sampling chain is launched with programmatic stream
+// serialisation, so it may be scheduled while the kernel before it in the stream finishes; its first
+// act is to wait for that kernel's completion (and memory), then to let the next one be scheduled.
+// Launched without the attribute, both instructions return at once.
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 struct DevAC {
     const uint8_t *op;
     const uint32_t *child_off;
@@ -174,7 +183,10 @@ struct PassDesc {
     int64_t pv_pitch;
     int64_t col0, ncols;  // first global column of this tile, columns in the tile (host bound)
 };
-__global__ void set_desc(PassDesc *dst, PassDesc v) { *dst = v; }
+__global__ void set_desc(PassDesc *dst, PassDesc v) {
+    pdl_begin();
+    *dst = v;
+}
 __device__ __forceinline__ int64_t desc_cols(const PassDesc &d) {
     int64_t n = d.ncols;
     if (d.es.n_active) n = min(n, (int64_t)(*d.es.n_active) - d.col0);
@@ -267,6 +279,7 @@ __global__ void bind_leaves_f64(DevAC ac, const PassDesc *pd, int64_t pitch, dou
 // reset.  Order-independent, so deterministic and per column.
 __global__ void level_scale_kernel(const uint32_t *cl_off, const uint16_t *cl, int L, int64_t pitch, int floor_zero,
                                    int *S, int *obs) {
+    pdl_begin();
     int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= pitch) return;
     int s = INT_MIN;
@@ -287,6 +300,7 @@ __global__ void level_scale_kernel(const uint32_t *cl_off, const uint16_t *cl, i
 // tier-B levels, and the level scales read the observed exponents of those levels and their child
 // levels alone.
 __global__ void obs_reset(int *obs, const int32_t *levels, int nlev, int64_t pitch) {
+    pdl_begin();
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < (int64_t)nlev * pitch) obs[(int64_t)levels[i / pitch] * pitch + i % pitch] = OBS_EMPTY;
 }
@@ -734,7 +748,10 @@ __device__ __forceinline__ uint32_t plan_key(const KeyPlan *kp, uint64_t x, bool
     }
     return (uint32_t)y;
 }
-__global__ void set_memo_desc(MemoDesc *dst, MemoDesc v) { *dst = v; }
+__global__ void set_memo_desc(MemoDesc *dst, MemoDesc v) {
+    pdl_begin();
+    *dst = v;
+}
 
 // bits of x selected by mask m, packed into the low bits in order (contiguous runs take a shift)
 __device__ __forceinline__ uint32_t extract_bits(uint64_t x, uint64_t m) {
@@ -866,6 +883,7 @@ template <typename C>
 __global__ void __launch_bounds__(TPB, sizeof(C) == 8 ? 8 : 1) memoA_level(DevAC ac, const MemoDesc *mdp,
                                                                           const uint32_t *nodes,
                                                     const MemoAGroup *grp, int ng, int64_t u0, uint32_t T) {
+    pdl_begin();
     if (T == 0 || ng <= 0) return;
     const MemoDesc md = *mdp;
     C *VA = static_cast<C *>(md.VA);
@@ -898,6 +916,7 @@ struct MemoARunLevel {
 template <typename C>
 __global__ void __launch_bounds__(TPB) memoA_run(DevAC ac, const MemoDesc *mdp, const uint32_t *nodes,
                                                   const MemoAGroup *grp, const MemoARunLevel *lv, int nlv) {
+    pdl_begin();
     const MemoDesc md = *mdp;
     C *VA = static_cast<C *>(md.VA);
     for (int64_t vec = blockIdx.x; vec < md.V; vec += gridDim.x) {
@@ -923,6 +942,7 @@ template <typename C>
 __global__ void __launch_bounds__(TPB) memoA_all(DevAC ac, const MemoDesc *mdesc, const uint32_t *nodes,
                                                   const MemoAGroup *grp, const MemoARunLevel *lv,
                                                   const MemoAStep *steps, const int32_t *order, int nq, int64_t V) {
+    pdl_begin();
     for (int64_t p = blockIdx.x; p < (int64_t)nq * V; p += gridDim.x) {
         const int j = order[p / V];
         const int64_t vec = p % V;
@@ -955,6 +975,7 @@ __global__ void __launch_bounds__(TPB, sizeof(C) == 8 ? 8 : 1) memoA_lvl_all(Dev
                                                                             const uint32_t *nodes,
                                                                             const MemoAGroup *grp,
                                                                             const MemoALvlStep *ls, int nls) {
+    pdl_begin();
     __shared__ MemoDesc smd[MEMO_LVL_STEPS];
     __shared__ int64_t pre[MEMO_LVL_STEPS + 1];  // block items before each step's
     for (int i = threadIdx.x; i < nls; i += blockDim.x) smd[i] = mdesc[ls[i].j];
@@ -984,6 +1005,7 @@ __global__ void __launch_bounds__(TPB, sizeof(C) == 8 ? 8 : 1) memoA_lvl_all(Dev
 // prefix bits on that support, packed (read by tier-B nodes for their tier-A children).  Only
 // columns below the tile's group count are written.
 __global__ void memo_keys(const PassDesc *pd, const MemoDesc *mdp) {
+    pdl_begin();
     const int64_t ncols = desc_cols(*pd);
     const int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (col >= ncols) return;
@@ -1227,6 +1249,7 @@ __global__ void __launch_bounds__(TPB, 3) memoB_level_f32(DevAC ac, LevelArgs a,
                                                         const PassDesc *pd,
                                                         const MemoDesc *mdp, float2 *__restrict__ V,
                                                         int *__restrict__ S, int *__restrict__ obs) {
+    pdl_begin();
     __shared__ uint2 sdesc[TPB / 32][NBB];
     __shared__ uint4 srec[TPB / 32][NBB][2];
     const int64_t ncols = desc_cols(*pd);
@@ -1402,6 +1425,7 @@ __global__ void __launch_bounds__(TPB, 4) memoB_run_f32(const MemoBRunLevel *lv,
                                                       float2 *__restrict__ V, int *__restrict__ S,
                                                       int *__restrict__ obs, int fuse, int64_t rrow, int Lroot,
                                                       double2 *__restrict__ out) {
+    pdl_begin();
     extern __shared__ uint4 run_smem[];
     __shared__ MemoBRunLevel slv[MEMO_RUN_LV];
     const int64_t ncols = desc_cols(*pd);
@@ -1576,6 +1600,7 @@ static size_t run_smem_bytes(int nlv, int64_t ntot) {
 __global__ void __launch_bounds__(TPB) memoB_level_f64(LevelArgs a, const uint2 *bdesc, int64_t count,
                                                         const PassDesc *pd, const MemoDesc *mdp,
                                                         double2 *__restrict__ V) {
+    pdl_begin();
     const int64_t ncols = desc_cols(*pd);
     if (ncols <= 0 || count <= 0) return;
     const MemoDesc md = *mdp;
@@ -1630,6 +1655,7 @@ __global__ void __launch_bounds__(TPB) memoB_level_f64(LevelArgs a, const uint2 
 // Root value of every active group column: from the tier-A slots or the tier-B tile.
 __global__ void memo_root(const MemoDesc *mdp, const PassDesc *pd, uint32_t root, int Lroot, int64_t rrow,
                           const void *Vb, const int *S, int64_t pitch, int prec32, double2 *out) {
+    pdl_begin();
     const int64_t ncols = desc_cols(*pd);
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= ncols) return;
@@ -1916,6 +1942,7 @@ __global__ void set_count(int32_t *dst, int32_t v) { *dst = v; }
 __global__ void sample_decide(int64_t n_vec, int64_t max_shots, const int32_t *shots, const uint64_t *seeds, int j,
                               int n_qubits, const double2 *pv, int32_t *s_group,
                               uint64_t *s_bits, int32_t *flag, const int32_t *g_count, int32_t *status) {
+    pdl_begin();
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n_vec * max_shots) return;
     int64_t v = t / max_shots, s = t % max_shots;
@@ -1935,6 +1962,7 @@ __global__ void sample_decide(int64_t n_vec, int64_t max_shots, const int32_t *s
 
 // exclusive scan of flag[0..n) into pos (block-local pass), block sums in bsum
 __global__ void scan_block(const int32_t *flag, const int32_t *n_dev, int mult, int32_t *pos, int32_t *bsum) {
+    pdl_begin();
     __shared__ int32_t sh[1024];
     const int64_t n = (int64_t)(*n_dev) * mult;
     int64_t i = blockIdx.x * 1024LL + threadIdx.x;
@@ -1951,6 +1979,7 @@ __global__ void scan_block(const int32_t *flag, const int32_t *n_dev, int mult, 
     if (threadIdx.x == 1023) bsum[blockIdx.x] = sh[1023];
 }
 __global__ void scan_sums(int32_t *bsum, int64_t nb) {
+    pdl_begin();
     // single block: exclusive scan of nb block sums
     __shared__ int32_t carry;
     __shared__ int32_t sh[1024];
@@ -1980,6 +2009,7 @@ __global__ void sample_regroup(const int32_t *g_count_old, const int32_t *flag, 
                                const double2 *pv, int32_t *g_vec_n, uint64_t *g_prefix_n,
                                double *g_P_n, int32_t *g_count_new, int64_t nflag, const int32_t *g_traj,
                                int32_t *g_traj_n) {
+    pdl_begin();
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t n = min((int64_t)(2LL * (*g_count_old)), nflag);  // only the scanned child slots
     if (k >= n) return;
@@ -1996,6 +2026,7 @@ __global__ void sample_regroup(const int32_t *g_count_old, const int32_t *flag, 
 __global__ void sample_remap(int64_t n_vec, int64_t max_shots, const int32_t *shots, const int32_t *pos,
                              const int32_t *bsum, int32_t *s_group, const uint64_t *s_bits, int64_t nflag,
                              int32_t *status) {
+    pdl_begin();
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n_vec * max_shots) return;
     int64_t v = t / max_shots, s = t % max_shots;
@@ -3469,6 +3500,23 @@ static qkc_ac::MemoMeta *memo_meta(qkc_ac *a, int cap, qkc_status *st) {
     return m;
 }
 
+// Launch a kernel of the sampling chain with programmatic stream serialisation (the kernel begins with
+// pdl_begin, so it touches memory only once the kernel before it has completed).
+template <typename... P, typename... A>
+static void launch_pdl(void (*k)(P...), unsigned grid, unsigned block, size_t smem, cudaStream_t s, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, static_cast<P>(args)...);  // a failure is left for the caller's launch check
+}
+
 // Launch sequences of a memoised pass, captured once per (cap, step) as CUDA graphs.  They
 // read the memo descriptor (vectors, step, slots) and the pass descriptor (tile columns), and
 // their grids do not depend on the number of vectors or columns.
@@ -3482,9 +3530,9 @@ static void launch_memoA_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
     for (const auto &it : m->a_items[j]) {
         if (it.cnt > 0) {
             if (a->prec == 32)
-                memoA_run<float2><<<gr, TPB, 0, s>>>(d, md_j, nodes_j, grp_j, m->d_runlv + it.off, it.cnt);
+                launch_pdl(memoA_run<float2>, gr, TPB, 0, s, d, md_j, nodes_j, grp_j, m->d_runlv + it.off, it.cnt);
             else
-                memoA_run<double2><<<gr, TPB, 0, s>>>(d, md_j, nodes_j, grp_j, m->d_runlv + it.off, it.cnt);
+                launch_pdl(memoA_run<double2>, gr, TPB, 0, s, d, md_j, nodes_j, grp_j, m->d_runlv + it.off, it.cnt);
             continue;
         }
         const uint32_t L = (uint32_t)it.L;
@@ -3494,8 +3542,8 @@ static void launch_memoA_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
         const uint32_t *nodes = nodes_j + i0;
         const MemoAGroup *gp = grp_j + m->g_lvl[j][L];
         const int ng = (int)(m->g_lvl[j][L + 1] - m->g_lvl[j][L]);
-        if (a->prec == 32) memoA_level<float2><<<g, TPB, 0, s>>>(d, md_j, nodes, gp, ng, u0, T);
-        else memoA_level<double2><<<g, TPB, 0, s>>>(d, md_j, nodes, gp, ng, u0, T);
+        if (a->prec == 32) launch_pdl(memoA_level<float2>, g, TPB, 0, s, d, md_j, nodes, gp, ng, u0, T);
+        else launch_pdl(memoA_level<double2>, g, TPB, 0, s, d, md_j, nodes, gp, ng, u0, T);
     }
 }
 static int64_t memoA_launches(const qkc_ac *a, const qkc_ac::MemoMeta *m, int j) {
@@ -3510,11 +3558,11 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
     const int64_t pitch = a->tile;
     if (m->b_lvl[j][D] > 0) {
         const unsigned gs = (unsigned)((pitch + TPB - 1) / TPB);
-        if (m->bp_cnt[j] > 0 && !(m->fuse[j] & 1)) memo_keys<<<gs, TPB, 0, s>>>(a->d_desc, md_j);
+        if (m->bp_cnt[j] > 0 && !(m->fuse[j] & 1)) launch_pdl(memo_keys, gs, TPB, 0, s, a->d_desc, md_j);
         // FP32 scales: only levels with tier-B nodes are computed, so every level's observed
         // exponent starts empty and the scale kernel runs for those levels alone
         if (a->prec == 32 && m->rst_cnt[j] > 0)
-            obs_reset<<<(unsigned)((m->rst_cnt[j] * pitch + TPB - 1) / TPB), TPB, 0, s>>>(
+            launch_pdl(obs_reset, (unsigned)((m->rst_cnt[j] * pitch + TPB - 1) / TPB), TPB, 0, s,
                 a->d_obs, m->d_rst + m->rst_base[j], (int)m->rst_cnt[j], pitch);
         const bool inline_scale = m->b_lvl[j][D] <= MEMO_INLINE_SCALE_B;
         const uint2 *bd_j = m->d_bdesc + m->b_base[j];
@@ -3526,7 +3574,7 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
                 const int64_t chunks = (pitch + 63) / 64;
                 const unsigned g = (unsigned)std::min<int64_t>((chunks + TPB / 32 - 1) / (TPB / 32), (int64_t)sms * 8);
                 const int fz = (ii == 0 ? (m->fuse[j] & 1) : 0) | (ii + 1 == nit ? (m->fuse[j] & 2) : 0);
-                memoB_run_f32<<<g, TPB, run_smem_bytes(it.cnt, it.nodes), s>>>(m->d_brunlv + it.off, it.cnt, bd_j,
+                launch_pdl(memoB_run_f32, g, TPB, run_smem_bytes(it.cnt, it.nodes), s, m->d_brunlv + it.off, it.cnt, bd_j,
                                                                                 a->d_desc, md_j, pitch,
                                                  (float2 *)a->d_V, a->d_S, a->d_obs, fz, m->root_row[j],
                                                  a->root_lev[j], a->d_root);
@@ -3535,24 +3583,24 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
             const uint32_t L = (uint32_t)it.L;
             const int64_t b0 = m->b_lvl[j][L], b1 = m->b_lvl[j][L + 1];
             if (a->prec == 32 && !inline_scale)
-                level_scale_kernel<<<gs, TPB, 0, s>>>(cl_off_j, m->d_bcl, (int)L, pitch, m->floor0[j][L], a->d_S,
+                launch_pdl(level_scale_kernel, gs, TPB, 0, s, cl_off_j, m->d_bcl, (int)L, pitch, m->floor0[j][L], a->d_S,
                                                       a->d_obs);
             // lo: the level's first tier-B row; hi: bit 0 reads tier-A values, bit 1 scale formed inline
             LevelArgs la{(uint32_t)b0, (uint32_t)m->floor0[j][L] | (inline_scale ? 2u : 0u), (int)L, pitch};
             if (a->prec == 32) {  // at most one wave of resident blocks (the kernel splits the last round)
                 const int64_t items = ((b1 - b0 + NBB - 1) / NBB) * ((pitch + 127) / 128);
                 const unsigned g = grid_for(items * 8 * 32, TPB, (int64_t)sms * a->ctx->memoB_blocks_per_sm);
-                memoB_level_f32<<<g, TPB, 0, s>>>(d, la, bd_j + b0, b1 - b0, a->d_desc, md_j, (float2 *)a->d_V,
+                launch_pdl(memoB_level_f32, g, TPB, 0, s, d, la, bd_j + b0, b1 - b0, a->d_desc, md_j, (float2 *)a->d_V,
                                                    a->d_S, a->d_obs);
             } else {  // a warp per 32 nodes x 32 columns, grid-striding
                 const int64_t items = ((b1 - b0 + NBB - 1) / NBB) * ((pitch + 31) / 32);
                 const unsigned g = grid_for(items * 32, TPB, (int64_t)sms * 8);
-                memoB_level_f64<<<g, TPB, 0, s>>>(la, bd_j + b0, b1 - b0, a->d_desc, md_j, (double2 *)a->d_V);
+                launch_pdl(memoB_level_f64, g, TPB, 0, s, la, bd_j + b0, b1 - b0, a->d_desc, md_j, (double2 *)a->d_V);
             }
         }
     }
     if (!(m->fuse[j] & 2))
-        memo_root<<<(unsigned)((pitch + TPB - 1) / TPB), TPB, 0, s>>>(md_j, a->d_desc, a->roots[j], a->root_lev[j],
+        launch_pdl(memo_root, (unsigned)((pitch + TPB - 1) / TPB), TPB, 0, s, md_j, a->d_desc, a->roots[j], a->root_lev[j],
                                                                       m->root_row[j], a->d_V, a->d_S, pitch,
                                                                       a->prec == 32, a->d_root);
 }
@@ -3613,7 +3661,7 @@ static void set_memo_step(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, int clamp
                 a->d_sigma, m->d_emask + (size_t)j * a->E, m->d_brec + m->br_base[j],
                 m->d_kplan + m->kp_base[j], m->d_aplan + m->ap_base[j], m->d_bplan + m->bp_base[j],
                 (int32_t)m->bp_cnt[j], a->d_keys, a->tile, m->d_bclo + (size_t)j * (a->D + 1), m->d_bcl};
-    set_memo_desc<<<1, 1, 0, s>>>(a->d_mdesc + j, md);
+    launch_pdl(set_memo_desc, 1, 1, 0, s, a->d_mdesc + j, md);
     ++a->launches;
 }
 
@@ -3636,10 +3684,10 @@ static qkc_status memo_tierA_all(qkc_ac *a, qkc_ac::MemoMeta *m, int clamp, int6
     if (m->all_T <= MEMO_ALL_T) {
         const unsigned g = (unsigned)std::min<int64_t>((int64_t)nq * n_vec, (int64_t)a->ctx->sm_count * 8);
         if (a->prec == 32)
-            memoA_all<float2><<<g, TPB, 0, s>>>(d, a->d_mdesc, m->d_a_nodes, m->d_a_grp, m->d_alllv, m->d_asteps,
+            launch_pdl(memoA_all<float2>, g, TPB, 0, s, d, a->d_mdesc, m->d_a_nodes, m->d_a_grp, m->d_alllv, m->d_asteps,
                                                 m->d_aorder, nq, n_vec);
         else
-            memoA_all<double2><<<g, TPB, 0, s>>>(d, a->d_mdesc, m->d_a_nodes, m->d_a_grp, m->d_alllv, m->d_asteps,
+            launch_pdl(memoA_all<double2>, g, TPB, 0, s, d, a->d_mdesc, m->d_a_nodes, m->d_a_grp, m->d_alllv, m->d_asteps,
                                                  m->d_aorder, nq, n_vec);
         ++a->launches;
     } else {
@@ -3648,10 +3696,10 @@ static qkc_status memo_tierA_all(qkc_ac *a, qkc_ac::MemoMeta *m, int clamp, int6
             const int64_t o0 = m->lvs_off[L], cnt = m->lvs_off[L + 1] - o0;
             if (cnt == 0) continue;
             if (a->prec == 32)
-                memoA_lvl_all<float2><<<g, TPB, 0, s>>>(d, a->d_mdesc, m->d_a_nodes, m->d_a_grp, m->d_lvs + o0,
+                launch_pdl(memoA_lvl_all<float2>, g, TPB, 0, s, d, a->d_mdesc, m->d_a_nodes, m->d_a_grp, m->d_lvs + o0,
                                                         (int)cnt);
             else
-                memoA_lvl_all<double2><<<g, TPB, 0, s>>>(d, a->d_mdesc, m->d_a_nodes, m->d_a_grp, m->d_lvs + o0,
+                launch_pdl(memoA_lvl_all<double2>, g, TPB, 0, s, d, a->d_mdesc, m->d_a_nodes, m->d_a_grp, m->d_lvs + o0,
                                                          (int)cnt);
             ++a->launches;
         }
@@ -3691,7 +3739,7 @@ static qkc_status memo_pass(qkc_ac *a, qkc_ac::MemoMeta *m, int j, int clamp, in
         const int64_t nc = std::min<int64_t>(pitch, bound - c0);
         EvSrc es{nullptr, a->d_g_prefix[cur], j, clamp, a->d_g_vec[cur], n_active, std::max<int64_t>(1, n_vec)};
         PassDesc desc{es, a->d_pv, a->vec_cap, c0, nc};
-        set_desc<<<1, 1, 0, s>>>(a->d_desc, desc);
+        launch_pdl(set_desc, 1, 1, 0, s, a->d_desc, desc);
         ++a->launches;
         QKC_CUDA(cudaGraphLaunch(gB, s));
         a->launches += memoB_launches(a, m, j);
@@ -3864,17 +3912,17 @@ static qkc_status sample_impl(qkc_ac *a, const uint64_t *seeds, const int32_t *s
         }
         const int64_t nflag = 2 * bound;
         QKC_CUDA(cudaMemsetAsync(a->d_flag, 0, sizeof(int32_t) * nflag, s));
-        sample_decide<<<gs, TPB, 0, s>>>(n_vec, max_shots, shots, seeds, j, nq, a->d_root, a->d_s_group,
+        launch_pdl(sample_decide, gs, TPB, 0, s, n_vec, max_shots, shots, seeds, j, nq, a->d_root, a->d_s_group,
                                          a->d_s_bits, a->d_flag, gcount, a->d_status);
         const int64_t nb = (nflag + 1023) / 1024;
-        scan_block<<<(unsigned)nb, 1024, 0, s>>>(a->d_flag, gcount, 2, a->d_pos, a->d_bsum);
-        scan_sums<<<1, 1024, 0, s>>>(a->d_bsum, nb);
+        launch_pdl(scan_block, (unsigned)nb, 1024, 0, s, a->d_flag, gcount, 2, a->d_pos, a->d_bsum);
+        launch_pdl(scan_sums, 1, 1024, 0, s, a->d_bsum, nb);
         const int nxt = cur ^ 1;
-        sample_regroup<<<(unsigned)((nflag + TPB - 1) / TPB), TPB, 0, s>>>(
+        launch_pdl(sample_regroup, (unsigned)((nflag + TPB - 1) / TPB), TPB, 0, s,
             gcount, a->d_flag, a->d_pos, a->d_bsum, a->d_g_vec[cur], a->d_g_prefix[cur], a->d_root,
             a->d_g_vec[nxt], a->d_g_prefix[nxt], a->d_g_P[nxt], a->d_gcount + nxt, nflag,
             traj ? a->d_g_traj[cur] : nullptr, traj ? a->d_g_traj[nxt] : nullptr);
-        sample_remap<<<gs, TPB, 0, s>>>(n_vec, max_shots, shots, a->d_pos, a->d_bsum, a->d_s_group, a->d_s_bits,
+        launch_pdl(sample_remap, gs, TPB, 0, s, n_vec, max_shots, shots, a->d_pos, a->d_bsum, a->d_s_group, a->d_s_bits,
                                         nflag, a->d_status);
         a->launches += 5;
         QKC_LAUNCH_CHECK();
