@@ -4,7 +4,7 @@ The bench's sampling call, exactly: the 32-qubit noise-free QAOA p=1 (seeded ran
 graph), its light-cone step AC in FP32, the default sampler (mode 1: memoised passes when
 estimated cheaper), the default column tile, 64 parameter vectors x 10000 samples.  Checked
   * index for index against the whole density AC's per-group sampler (mode 0): every
-    difference must be a decision within the FP32 tie margin, judged by the FP64 AC oracle;
+    difference must be a decision within the FP32 tie margin, as the FP64 AC oracle decides it;
   * 2000 indices (8 vectors x 250) against the FP64 AC oracle's chain rule (acref), and each
     of their probabilities P(x) as the sampler computed it;
   * p0 / P = P(x_j = 0 | x_<j) on 64 random prefixes against the oracle, relative 1e-5;
