@@ -1429,7 +1429,7 @@ __global__ void __launch_bounds__(TPB, 4) memoB_run_f32(const MemoBRunLevel *lv,
     extern __shared__ uint4 run_smem[];
     __shared__ MemoBRunLevel slv[MEMO_RUN_LV];
     const int64_t ncols = desc_cols(*pd);
-    if (ncols <= 0) return;
+    if (ncols <= 0 || ((ncols + 63) >> 6) <= (int64_t)gridDim.x) return;  // few chunks: memoB_runc_f32
     const uint4 *brec = mdp->brec;
     // the run's rows are consecutive: [base, base + ntot)
     const uint32_t base = lv[0].b0, ntot = lv[nlv - 1].b0 + lv[nlv - 1].count - base;
@@ -1589,6 +1589,187 @@ __global__ void __launch_bounds__(TPB, 4) memoB_run_f32(const MemoBRunLevel *lv,
             out[gc] = make_double2(ldexp((double)q.x, sr[0]), ldexp((double)q.y, sr[0]));
             if (w.two) out[gc + 1] = make_double2(ldexp((double)q.z, sr[1]), ldexp((double)q.w, sr[1]));
         }
+    }
+}
+// The same run when the tile has no more 64-column chunks than the launch has blocks (the early sampling
+// steps, a few groups per vector): a block per chunk, its 8 warps sharing the chunk's columns (two per
+// lane, as above) and splitting each level's nodes (warp w: nodes w, w + 8, ...), with a block barrier
+// between levels; a level's observed exponent is the largest over the warps, reduced in shared memory.
+// The chain of levels then costs a level's nodes divided by 8 instead of by 1, with the same arithmetic
+// (every warp forms the same scales), so values equal memoB_run_f32's bit for bit.  Launched beside
+// memoB_run_f32 with the same grid; exactly one of the two has work.
+__global__ void __launch_bounds__(TPB, 4) memoB_runc_f32(const MemoBRunLevel *lv, int nlv, const uint2 *bdesc,
+                                                       const PassDesc *pd, const MemoDesc *mdp, int64_t pitch,
+                                                       float2 *__restrict__ V, int *__restrict__ S,
+                                                       int *__restrict__ obs, int fuse, int64_t rrow, int Lroot,
+                                                       double2 *__restrict__ out) {
+    pdl_begin();
+    extern __shared__ uint4 run_smem[];
+    __shared__ MemoBRunLevel slv[MEMO_RUN_LV];
+    __shared__ float2 smx[2][TPB / 32][32];  // per level parity, warp and lane: the warp's largest magnitudes
+    const int64_t ncols = desc_cols(*pd);
+    const int64_t nchunks = (ncols + 63) >> 6;
+    if (ncols <= 0 || nchunks > (int64_t)gridDim.x) return;  // many chunks: memoB_run_f32
+    const uint4 *brec = mdp->brec;
+    const uint32_t base = lv[0].b0, ntot = lv[nlv - 1].b0 + lv[nlv - 1].count - base;
+    uint4 *srec = run_smem;
+    uint2 *sdesc = reinterpret_cast<uint2 *>(srec + 2 * (size_t)ntot);
+    int *se = reinterpret_cast<int *>(sdesc + ntot);
+    for (uint32_t i = threadIdx.x; i < ntot; i += blockDim.x) {
+        const uint2 d = __ldg(bdesc + base + i);
+        const uint4 r0 = __ldg(brec + d.x);
+        sdesc[i] = d;
+        srec[2 * i] = r0;
+        srec[2 * i + 1] = (d.y & 0xffffffu) >= 2u ? __ldg(brec + d.x + 1) : r0;
+    }
+    if (threadIdx.x < nlv) slv[threadIdx.x] = lv[threadIdx.x];
+    __syncthreads();
+    const int64_t col0 = pd->col0;
+    const int32_t *col_vec = pd->es.col_vec;
+    const int64_t n_vec = pd->es.n_vec;
+    const uint64_t *prefix = pd->es.prefix;
+    const uint32_t *cl_off = mdp->bcl_off;
+    const uint16_t *cl = mdp->bcl;
+    const int j = mdp->j;
+    RView w;
+    w.VA = static_cast<const float2 *>(mdp->VA);
+    w.kplan = mdp->kplan;
+    w.hp = (uint32_t)(pitch >> 1);
+    w.pitch = (uint32_t)pitch;
+    w.kpitch = (uint32_t)mdp->kpitch;
+    w.Vn = (uint32_t)mdp->V;
+    w.j = j;
+    w.narrow = j <= 32;
+    uint32_t *keys = mdp->keys;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nwarp = TPB / 32;
+    float4 *V4 = reinterpret_cast<float4 *>(V);
+    int2 *se_w = reinterpret_cast<int2 *>(se) + (size_t)wp * 32 + lane;
+    const int se_step = nwarp * 32;
+    for (int64_t chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {  // one chunk a block
+        const int64_t col = chunk * 64 + lane * 2;
+        const bool active = col < ncols;
+        w.two = col + 1 < ncols;
+        const int64_t g0 = col0 + (active ? col : 0), g1 = w.two ? g0 + 1 : g0;
+        if (fuse & 1) {  // the chunk's group keys: the warps split the tabled supports
+            const KeyPlan *bplan = mdp->bplan;
+            const uint64_t p0 = j ? __brevll(prefix[g0] << (64 - j)) : 0ull;
+            const uint64_t p1 = j ? __brevll(prefix[g1] << (64 - j)) : 0ull;
+            for (int r = wp, nbm = mdp->nbm; r < nbm && active; r += nwarp) {
+                uint32_t *kr = keys + (int64_t)r * mdp->kpitch + col;
+                kr[0] = plan_key(bplan + r, p0, w.narrow);
+                if (w.two) kr[1] = plan_key(bplan + r, p1, w.narrow);
+            }
+            __syncthreads();
+        }
+        int64_t v0 = col_vec ? (int64_t)col_vec[g0] : g0, v1 = col_vec ? (int64_t)col_vec[g1] : g1;
+        v0 = v0 < 0 ? 0 : (v0 >= n_vec ? n_vec - 1 : v0);
+        v1 = v1 < 0 ? 0 : (v1 >= n_vec ? n_vec - 1 : v1);
+        w.vec0 = (uint32_t)v0;
+        w.vec1 = (uint32_t)v1;
+        w.pre = prefix + g0;
+        w.V4c = V4 + ((active ? col : 0) >> 1);
+        w.Sc = S + (active ? col : 0);
+        w.Kc = keys + (active ? col : 0);
+        for (int l = 0; l < nlv; ++l) {
+            const MemoBRunLevel L = slv[l];
+            int s0 = INT_MIN, s1 = INT_MIN;
+            if (active) {
+                for (uint32_t k = __ldg(cl_off + L.L), k1 = __ldg(cl_off + L.L + 1); k < k1; ++k) {
+                    const int Lp = __ldg(cl + k);
+                    int r = l - 1;
+                    while (r >= 0 && slv[r].L != Lp) --r;
+                    if (r >= 0) {
+                        const int2 e = se_w[r * se_step];
+                        s0 = max(s0, e.x);
+                        s1 = max(s1, e.y);
+                    } else {
+                        const int2 o = *reinterpret_cast<const int2 *>(obs + (int64_t)Lp * pitch + col);
+                        const int2 sc = *reinterpret_cast<const int2 *>(S + (int64_t)Lp * pitch + col);
+                        if (o.x != OBS_EMPTY) s0 = max(s0, sc.x + o.x);
+                        if (o.y != OBS_EMPTY) s1 = max(s1, sc.y + o.y);
+                    }
+                }
+            }
+            if (s0 == INT_MIN) s0 = 0;
+            if (s1 == INT_MIN) s1 = 0;
+            if (L.floor0) {
+                s0 = max(s0, 0);
+                s1 = max(s1, 0);
+            }
+            if (!w.two) s1 = 0;
+            const int sl0 = s0, sl1 = s1;
+            int *sw = S + (int64_t)L.L * pitch + (active ? col : 0), *ow = obs + (int64_t)L.L * pitch + (active ? col : 0);
+            if (wp == 0 && active) {  // the level's scale, read by the next levels' warps after the barrier
+                if (w.two) *reinterpret_cast<int2 *>(sw) = make_int2(sl0, sl1);
+                else sw[0] = sl0;
+            }
+            float mx0 = 0.f, mx1 = 0.f;
+            const uint32_t r0 = L.b0 - base;
+            float4 *dst = w.V4c + (int64_t)L.b0 * w.hp;
+            const int nn = (int)L.count;
+            for (int i = wp; i < nn && active;) {  // this warp's nodes: i, i + 8, ...; two at a time
+                const int i1 = i + nwarp;
+                const uint2 d0 = sdesc[r0 + i];
+                const uint2 d1 = sdesc[r0 + (i1 < nn ? i1 : i)];
+                const uint32_t deg0 = d0.y & 0xffffffu, deg1 = d1.y & 0xffffffu;
+                const uint4 *q0r = srec + 2 * (size_t)(r0 + i);
+                RChild x0, y0;
+                y0.v = make_float4(0.f, 0.f, 0.f, 0.f);
+                y0.s = make_int2(0, 0);
+                if (i1 < nn && deg0 <= 2u && deg1 <= 2u) {
+                    const uint4 *q1r = srec + 2 * (size_t)(r0 + i1);
+                    RChild x1, y1;
+                    y1.v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    y1.s = make_int2(0, 0);
+                    rchild_issue(q0r[0], x0, w);
+                    if (deg0 == 2u) rchild_issue(q0r[1], y0, w);
+                    rchild_issue(q1r[0], x1, w);
+                    if (deg1 == 2u) rchild_issue(q1r[1], y1, w);
+                    rchild_slots(q0r[0], x0, w);
+                    if (deg0 == 2u) rchild_slots(q0r[1], y0, w);
+                    rchild_slots(q1r[0], x1, w);
+                    if (deg1 == 2u) rchild_slots(q1r[1], y1, w);
+                    const float4 q = rcombine<false>(d0, x0, y0, sl0, sl1, brec, w);
+                    const float4 p = rcombine<false>(d1, x1, y1, sl0, sl1, brec, w);
+                    dst[(int64_t)i * w.hp] = q;
+                    dst[(int64_t)i1 * w.hp] = p;
+                    mx0 = fmaxf(mx0, fmaxf(fmaxf(fabsf(q.x), fabsf(q.y)), fmaxf(fabsf(p.x), fabsf(p.y))));
+                    mx1 = fmaxf(mx1, fmaxf(fmaxf(fabsf(q.z), fabsf(q.w)), fmaxf(fabsf(p.z), fabsf(p.w))));
+                    i += 2 * nwarp;
+                } else {
+                    rchild_issue(q0r[0], x0, w);
+                    if (deg0 >= 2u) rchild_issue(q0r[1], y0, w);
+                    rchild_slots(q0r[0], x0, w);
+                    if (deg0 >= 2u) rchild_slots(q0r[1], y0, w);
+                    const float4 q = rcombine<true>(d0, x0, y0, sl0, sl1, brec, w);
+                    dst[(int64_t)i * w.hp] = q;
+                    mx0 = fmaxf(mx0, fmaxf(fabsf(q.x), fabsf(q.y)));
+                    mx1 = fmaxf(mx1, fmaxf(fabsf(q.z), fabsf(q.w)));
+                    i += nwarp;
+                }
+            }
+            smx[l & 1][wp][lane] = make_float2(mx0, mx1);
+            __syncthreads();  // the level's rows (global) and every warp's magnitudes are visible
+            for (int u = 0; u < nwarp; ++u) {
+                const float2 m = smx[l & 1][u][lane];
+                mx0 = fmaxf(mx0, m.x);
+                mx1 = fmaxf(mx1, m.y);
+            }
+            const int e0 = (__float_as_int(mx0) >> 23) - 127, e1 = (__float_as_int(mx1) >> 23) - 127;
+            se_w[l * se_step] = make_int2(sl0 + e0, sl1 + e1);
+            if (wp == 0 && active) {  // the observed exponents: read only by later launches
+                if (w.two) *reinterpret_cast<int2 *>(ow) = make_int2(e0, e1);
+                else ow[0] = e0;
+            }
+        }
+        if ((fuse & 2) && wp == 0 && active) {  // the root's value in the lane's columns, unscaled to FP64
+            const float4 q = w.V4c[rrow * (int64_t)w.hp];
+            const int *sr = S + (int64_t)Lroot * pitch + col;
+            const int64_t gc = col0 + col;
+            out[gc] = make_double2(ldexp((double)q.x, sr[0]), ldexp((double)q.y, sr[0]));
+            if (w.two) out[gc + 1] = make_double2(ldexp((double)q.z, sr[1]), ldexp((double)q.w, sr[1]));
+        }
+        __syncthreads();  // before the next chunk reuses the shared magnitudes
     }
 }
 // Dynamic shared memory of a run of nlv levels and ntot nodes.
@@ -2276,6 +2457,8 @@ extern "C" qkc_status qkc_ctx_create(int device, qkc_ctx **out) {
     }
     // tier-B runs stage up to MEMO_RUN_NODES nodes and MEMO_RUN_LV levels in dynamic shared memory
     if (cudaFuncSetAttribute(memoB_run_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)run_smem_bytes(MEMO_RUN_LV, MEMO_RUN_NODES)) != cudaSuccess ||
+        cudaFuncSetAttribute(memoB_runc_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)run_smem_bytes(MEMO_RUN_LV, MEMO_RUN_NODES)) != cudaSuccess) {
         cudaGetLastError();
         delete c;
@@ -3578,6 +3761,10 @@ static void launch_memoB_sequence(qkc_ac *a, const qkc_ac::MemoMeta *m, int j, c
                                                                                 a->d_desc, md_j, pitch,
                                                  (float2 *)a->d_V, a->d_S, a->d_obs, fz, m->root_row[j],
                                                  a->root_lev[j], a->d_root);
+                launch_pdl(memoB_runc_f32, g, TPB, run_smem_bytes(it.cnt, it.nodes), s, m->d_brunlv + it.off, it.cnt, bd_j,
+                                                                                a->d_desc, md_j, pitch,
+                                                 (float2 *)a->d_V, a->d_S, a->d_obs, fz, m->root_row[j],
+                                                 a->root_lev[j], a->d_root);
                 continue;
             }
             const uint32_t L = (uint32_t)it.L;
@@ -3610,7 +3797,7 @@ static int64_t memoB_launches(const qkc_ac *a, const qkc_ac::MemoMeta *m, int j)
         n += (a->prec == 32 && m->rst_cnt[j] > 0) ? 1 : 0;
         n += m->bp_cnt[j] > 0 && !(m->fuse[j] & 1);
         const int per = (a->prec == 32 && m->b_lvl[j][a->D] > MEMO_INLINE_SCALE_B) ? 2 : 1;
-        for (const auto &it : m->b_items[j]) n += it.cnt > 0 ? 1 : per;
+        for (const auto &it : m->b_items[j]) n += it.cnt > 0 ? 2 : per;  // a run: both run kernels
     }
     return n;
 }
