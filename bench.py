@@ -939,7 +939,8 @@ def run_serve(args):
     p=2 on 8 qubits as a TRAJECTORY AC (p=2 at 12 qubits compiles to a 5.4M-node TRAJECTORY AC, about 0.3 s of GPU
     per 2000-shot request, and at 16 and 20 qubits to elimination widths 24 and 32: out of a serving budget); one
     parameter vector and log-uniform shots in [100, 10000] per request.  Continuous batching (FP32, 2 lanes per
-    AC, light-cone step ACs for p=1 with --sampler lightcone) against the FP64 one-request-at-a-time path on the
+    AC, light-cone step ACs for p=1 with --sampler lightcone, an 8 GB memo budget per lane unless --memo-budget-gb
+    says otherwise) against the FP64 one-request-at-a-time path on the
     same stream.  Both serve every admitted request to completion (arrivals for --duration seconds, at most six
     times that in all); p50/p99 are over every admitted request."""
     import torch
@@ -956,7 +957,8 @@ def run_serve(args):
     ctx = N.Context(0)
     cap = args.duration * 6
     srv = Server(ctx, ours, precision=32, lanes=2, max_batch=32, max_shots=10000, tile_columns=8192,
-                 memoised=args.sampler != "plain")
+                 memoised=args.sampler != "plain",
+                 memo_budget_bytes=int(args.memo_budget_gb * 2 ** 30) if args.memo_budget_gb > 0 else 8 << 30)
     res, st = srv.run(reqs, time_limit=cap)
     del srv
     torch.cuda.empty_cache()
