@@ -891,8 +891,8 @@ def serve_circuits():
 
 def run_serveacs(args):
     """Profiling case for the serving mix: each AC alone, one sampling call of 32 requests x 2150 shots (the
-    mix's mean) as the serving bench makes them (FP32, 8192-column tiles, 2 GB memo budget; light-cone step
-    ACs for p=1), timed with CUDA events over three calls; one JSON line per AC with its samples/s and its
+    mix's mean) as the serving bench makes them (FP32, 8192-column tiles; light-cone step ACs for p=1) but with a
+    2 GB memo budget, timed with CUDA events over three calls; one JSON line per AC with its samples/s and its
     memoised tiers' (or per-group passes') algorithmic GB/s."""
     import torch
     from paper_2103_17226_gb300.build import build_library
