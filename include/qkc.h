@@ -345,7 +345,12 @@ qkc_status qkc_gibbs(qkc_ac *ac, const int32_t *col_vec_dev, const uint64_t *see
  * memo_budget_bytes caps the device memory of the memoised values (0: 40% of
  * the device memory and at most 60% of what is free); the sampler picks the
  * largest key width that fits, and falls back to mode 0 when none does or when
- * the memoised passes are estimated to cost more than the per-group ones.
+ * the memoised passes are estimated to cost more than the per-group ones.  When
+ * the slots of every sampling step fit the budget side by side, they are kept
+ * for the whole call and every step's per-slot tier is computed before the
+ * first step (in one launch, or one per level index); otherwise each step
+ * reuses the same slots.  The memoised values' allocation only grows, up to the
+ * budget, and lasts until the AC is freed.
  */
 qkc_status qkc_set_sampler(qkc_ac *ac, int32_t mode, int64_t memo_budget_bytes);
 
